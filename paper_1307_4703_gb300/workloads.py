@@ -1,0 +1,181 @@
+"""Seeded synthetic inputs for the coupled lattice Boltzmann step.
+
+This module builds problem descriptions only: solid masks, port tables,
+inlet velocity profiles, source/sink concentrations and valve schedules.  It
+holds none of the method's arithmetic, so both the CUDA path and the FP64
+oracle take their inputs from here.
+
+The chip topology follows the gradient generator of Tanaka & Iber (arXiv
+1307.4703, "Experimental Layout and Conditions"): two parallel channels whose
+inlet and outlet valves open alternately, joined by a chamber in which the
+gradient forms.  The exact drawing of the paper's Figure 1a is not part of
+the paper's text, so rectangular chips of the stated proportions stand in for
+it.  Every random draw uses numpy's PCG64 generator with an explicit seed.
+
+Problem dict keys: name, nx, ny, solid (ny, nx) uint8 (1 = solid), tau,
+tau_c, w0, ports (list of dicts: channel, side, x, y0, y1, kind, rho),
+edge_u / edge_C ((2, ny) float64: u_x and C_in of velocity-port nodes per
+side and row), period, states (valve words cycled every ``period`` steps),
+steps, u_max.
+"""
+import numpy as np
+
+WEST, EAST = 0, 1
+VELOCITY, PRESSURE = 0, 1
+SEED = 0x1307
+
+
+def rng(seed=SEED):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def parabolic_profile(width, u_max):
+    """Inlet u_x across a channel of ``width`` rows whose walls lie half a
+    cell outside its first and last row: u = 4 u_max s (W - s) / W^2 with
+    s = row + 1/2 (the developed Poiseuille profile the paper's channels
+    approach, section "Results")."""
+    s = np.arange(width, dtype=np.float64) + 0.5
+    return 4.0 * u_max * s * (width - s) / float(width) ** 2
+
+
+def valve_word(problem, t):
+    """Valve word of time step t under the problem's schedule."""
+    st = problem["states"]
+    return int(st[(t // int(problem["period"])) % len(st)])
+
+
+def two_channel_chip(nx, ny, ch_w, ch_len, chamber_w, tau, tau_c, u_max, period, steps,
+                     x0=0, C_top=1.0, C_bottom=0.0, w0=1.0 / 3.0, name="chip"):
+    """Two channels of ``ch_w`` rows along x (rows [0, ch_w) and
+    [ny - ch_w, ny), columns [x0, x0 + ch_len)) joined by a chamber of
+    ``chamber_w`` columns centred in the grid.  Channel 0 is the top channel
+    (largest y, fed with C_top) and opens first; channel 1 is the bottom
+    channel (C_bottom).  Each channel has a velocity inlet on its west end
+    and a pressure outlet (rho = 1) on its east end."""
+    assert 0 < ch_w and 2 * ch_w < ny and 0 <= x0 and x0 + ch_len <= nx
+    solid = np.ones((ny, nx), dtype=np.uint8)
+    solid[0:ch_w, x0:x0 + ch_len] = 0
+    solid[ny - ch_w:ny, x0:x0 + ch_len] = 0
+    cx0 = (nx - chamber_w) // 2
+    solid[ch_w:ny - ch_w, cx0:cx0 + chamber_w] = 0
+    edge_u = np.zeros((2, ny))
+    edge_C = np.zeros((2, ny))
+    prof = parabolic_profile(ch_w, u_max)
+    ports = []
+    for chan, (y0, c_in) in enumerate(((ny - ch_w, C_top), (0, C_bottom))):
+        ports.append(dict(channel=chan, side=WEST, x=x0, y0=y0, y1=y0 + ch_w, kind=VELOCITY, rho=1.0))
+        ports.append(dict(channel=chan, side=EAST, x=x0 + ch_len - 1, y0=y0, y1=y0 + ch_w,
+                          kind=PRESSURE, rho=1.0))
+        edge_u[WEST, y0:y0 + ch_w] = prof
+        edge_C[WEST, y0:y0 + ch_w] = c_in
+    return dict(name=name, nx=nx, ny=ny, solid=solid, tau=float(tau), tau_c=float(tau_c),
+                w0=float(w0), ports=ports, edge_u=edge_u, edge_C=edge_C, period=int(period),
+                states=[1, 2], steps=int(steps), u_max=float(u_max),
+                chamber=(cx0, cx0 + chamber_w, ch_w, ny - ch_w))
+
+
+def config_small():
+    """256 x 128 chip: channels rows 0-15 and 112-127 over x = 0..255, chamber
+    x = 96..159; tau = 0.8, tau_c = 0.55, u_max = 0.05, valves toggle every
+    500 steps, 2000 steps."""
+    return two_channel_chip(256, 128, 16, 256, 64, 0.8, 0.55, 0.05, 500, 2000, name="chip-256x128")
+
+
+def config_full_chip(tau_c=0.51):
+    """1024 x 768 chip at 1 um per cell: channels 100 rows wide over
+    x = 0..999 (columns 1000-1023 solid), chamber 200 columns wide spanning
+    rows 100..667; tau = 0.6, u_max = 0.04, valve period 2000 steps."""
+    return two_channel_chip(1024, 768, 100, 1000, 200, 0.6, tau_c, 0.04, 2000, 200000,
+                            name="chip-1024x768")
+
+
+def config_large_chip(nx=4096, ny=2048, tau_c=0.51, steps=50000):
+    """The 1024 x 768 chip scaled to 4096 x 2048 (x by 4, y by 8/3): channels
+    267 rows wide over x = 0..3999, chamber 800 columns wide.  Other sizes
+    keep the same proportions (used for downscaled copies)."""
+    ch_w = int(round(ny * 267 / 2048))
+    ch_len = int(round(nx * 4000 / 4096))
+    cw = int(round(nx * 800 / 4096))
+    return two_channel_chip(nx, ny, ch_w, ch_len, cw, 0.6, tau_c, 0.04, 2000, steps,
+                            name="chip-%dx%d" % (nx, ny))
+
+
+def config_adjoint_chip():
+    """1024 x 512 chip for the gradient workload: channels rows 0..99 and
+    412..511 over x = 0..999, chamber 200 wide; tau = 0.6, tau_c = 0.51,
+    u_max = 0.04, valve period 1500, 4000 steps."""
+    return two_channel_chip(1024, 512, 100, 1000, 200, 0.6, 0.51, 0.04, 1500, 4000,
+                            name="chip-1024x512")
+
+
+def has_isolated_fluid(solid):
+    """True when some fluid cell has no fluid cell among its 8 neighbours
+    inside the grid (such masks are rejected by the library)."""
+    fl = np.asarray(solid) == 0
+    ny, nx = fl.shape
+    pad = np.zeros((ny + 2, nx + 2), dtype=bool)
+    pad[1:-1, 1:-1] = fl
+    nb = np.zeros_like(fl)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dx or dy:
+                nb |= pad[1 + dy:ny + 1 + dy, 1 + dx:nx + 1 + dx]
+    return bool(np.any(fl & ~nb))
+
+
+def random_case(seed, nx, ny, solid_frac=0.2):
+    """A small lattice with every kind of node: random solid obstacles, one
+    port of each (side, kind) pair on three valve channels, random inlet
+    profiles and concentrations, and random initial fields near rest.
+
+    Returns (problem, init) where init = dict(rho, ux, uy, C) of (ny, nx)
+    arrays, and problem["states"] holds a random valve word per step
+    (period 1)."""
+    r = rng(seed)
+    assert nx >= 4 and ny >= 8
+    solid = (r.random((ny, nx)) < solid_frac).astype(np.uint8)
+    # ports: rows split into bands; each band is a port on the west or east edge
+    h = ny // 4
+    bands = [(0, h), (h, 2 * h), (2 * h, 3 * h), (3 * h, ny)]
+    ports = []
+    edge_u = np.zeros((2, ny))
+    edge_C = np.zeros((2, ny))
+    specs = [(0, WEST, VELOCITY, bands[0]), (0, EAST, PRESSURE, bands[1]),
+             (1, EAST, VELOCITY, bands[2]), (1, WEST, PRESSURE, bands[3]),
+             (2, WEST, VELOCITY, bands[2]), (2, EAST, PRESSURE, bands[0])]
+    for chan, side, kind, (y0, y1) in specs:
+        y0 = y0 + (1 if y1 - y0 > 2 else 0)
+        x = 0 if side == WEST else nx - 1
+        solid[y0:y1, x] = 0
+        solid[y0:y1, x + (1 if side == WEST else -1)] = 0
+        ports.append(dict(channel=chan, side=side, x=x, y0=y0, y1=y1, kind=kind,
+                          rho=float(1.0 + 0.01 * (r.random() - 0.5))))
+        if kind == VELOCITY:
+            sgn = 1.0 if side == WEST else -1.0
+            edge_u[side, y0:y1] = sgn * 0.04 * r.random(y1 - y0)
+            edge_C[side, y0:y1] = r.random(y1 - y0)
+    # drop isolated fluid cells (never port nodes, which have a fluid neighbour)
+    while has_isolated_fluid(solid):
+        fl = solid == 0
+        pad = np.zeros((ny + 2, nx + 2), dtype=bool)
+        pad[1:-1, 1:-1] = fl
+        nb = np.zeros_like(fl)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if dx or dy:
+                    nb |= pad[1 + dy:ny + 1 + dy, 1 + dx:nx + 1 + dx]
+        solid[fl & ~nb] = 1
+    init = dict(rho=1.0 + 0.01 * (r.random((ny, nx)) - 0.5),
+                ux=0.03 * (r.random((ny, nx)) - 0.5),
+                uy=0.03 * (r.random((ny, nx)) - 0.5),
+                C=r.random((ny, nx)))
+    states = [int(s) for s in r.integers(0, 8, size=64)]
+    prob = dict(name="random-%dx%d-s%d" % (nx, ny, seed), nx=nx, ny=ny, solid=solid,
+                tau=float(0.55 + 0.5 * r.random()), tau_c=float(0.52 + 0.5 * r.random()),
+                w0=1.0 / 3.0, ports=ports, edge_u=edge_u, edge_C=edge_C, period=1,
+                states=states, steps=len(states), u_max=0.04)
+    return prob, init
+
+
+def fluid_count(problem):
+    return int(np.count_nonzero(np.asarray(problem["solid"]) == 0))
