@@ -1,0 +1,322 @@
+"""Benchmark of the coupled D2Q9 + D2Q5 lattice Boltzmann time step on GB300.
+
+A "step" is one coupled time step of the whole chip: pull-stream of f and g,
+bounce-back walls, valve-switched Zou-He ports, moments, collision of f and
+of g with the same step's velocity, and the fused FP64 mass/flux
+diagnostics; one launch of the fused kernel.  The workload is the
+4096 x 2048 two-channel chip (3.35 M fluid nodes, 0.94 GB of FP32
+populations per copy, larger than the 129 MB L2), the configuration the HBM
+roofline is quoted on.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
+replica of the chip (no data exchange: the chips are independent) and rank 0
+reports the aggregate over ranks with the time of the slowest rank.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled D2Q9+D2Q5 GLUPS and % HBM roofline; adjoint/forward time ratio"
+UNIT = "GLUPS"
+BYTES_PER_NODE = 112  # 14 FP32 populations read + written per fluid node and step
+KERNEL_SRC = os.path.join(ROOT, "paper_1307_4703_gb300", "csrc", "lbm_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "coupled_step_chip-4096x2048.md")
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="large", choices=["large", "full", "small"])
+    p.add_argument("--skip-extras", action="store_true",
+                   help="skip the end-to-end and CPU-baseline legs (profiling runs)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def _problem(name):
+    from paper_1307_4703_gb300 import workloads as W
+    if name == "large":
+        return W.config_large_chip()
+    if name == "full":
+        return W.config_full_chip()
+    return W.config_small()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def _traffic(nodes_now):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    n = re.search(r"fluid_nodes:\s*(\d+)", text)
+    if not (h and b and n) or h.group(1) != _kernel_hash():
+        return None
+    return float(b.group(1)) * nodes_now / float(n.group(1))
+
+
+class _Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        self.out.close()
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                s = float(r[1])
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            sm.append(s)
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _cpu_baseline(seconds):
+    """The FP64 oracle as it stands, single thread, on a 512 x 256 downscaled
+    copy of the chip; runs for about `seconds` of host time."""
+    import oracle
+    from paper_1307_4703_gb300 import workloads as W
+    prob = W.config_large_chip(512, 256)
+    ref = oracle.from_problem(prob)
+    fluid = W.fluid_count(prob)
+    ref.step(1, 5)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        ref.step(W.valve_word(prob, n), 10)
+        n += 10
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return {"value": fluid * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 C oracle, 1 thread, %d steps of the 512x256 downscaled copy "
+                      "(%d fluid nodes), %.1f s" % (n, fluid, dt)}
+
+
+def _reference(args):
+    """The reference arm: the oracle, as it stands, on the host cores."""
+    import oracle
+    from paper_1307_4703_gb300 import workloads as W
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    prob = W.config_large_chip(256, 128)
+    fluid = W.fluid_count(prob)
+    ref = oracle.from_problem(prob)
+    for t in range(args.warmup):
+        ref.step(W.valve_word(prob, t))
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        ref.step(W.valve_word(prob, args.warmup + t))
+    dt = time.perf_counter() - t0
+    value = fluid * args.steps / dt / 1e9
+    sample = ("FP64 C oracle, 1 thread; each step one time step of the 256x128 downscaled copy "
+              "of the 4096x2048 chip (%d fluid nodes)" % fluid)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob["name"] + " (sample of chip-4096x2048)", "nx": prob["nx"],
+                       "ny": prob["ny"], "fluid_nodes": fluid},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _e2e(prob, steps, device):
+    """The same metric through the public C ABI with host buffers: create the
+    chip from host arrays, then every step upload the step's valve word, run
+    the step and read its diagnostics back to the host, and finally read
+    the fields back; all inside the timed region."""
+    import numpy as np
+    from paper_1307_4703_gb300 import lbm, workloads as W
+    fluid = W.fluid_count(prob)
+    nx, ny = prob["nx"], prob["ny"]
+    warm = lbm.Chip.from_problem(prob, device=device)
+    warm.step(2)
+    warm.diagnostics()
+    warm.close()
+    t0 = time.perf_counter()
+    chip = lbm.Chip.from_problem(prob, device=device)
+    for t in range(steps):
+        chip.set_valves(W.valve_word(prob, t))
+        chip.step(1)
+        chip.diagnostics()
+    fields = chip.fields()
+    chip.close()
+    dt = time.perf_counter() - t0
+    h2d_once = nx * ny + 2 * 2 * ny * 4 + len(prob["ports"]) * 32
+    d2h_once = sum(a.nbytes for a in fields)
+    return {"value": fluid * steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": 4 + h2d_once / steps,
+            "d2h_bytes_per_step": 36 + d2h_once / steps,
+            "steps": steps, "seconds": dt}
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        _reference(args)
+        return
+    import torch
+    from paper_1307_4703_gb300 import build, lbm, workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    build.build()
+    torch.cuda.set_device(local)
+    prob = _problem(args.workload)
+    fluid = W.fluid_count(prob)
+    stream = torch.cuda.Stream()
+    chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=local)
+    chip.set_valve_schedule(prob["period"], prob["states"])
+    info = chip.info()
+
+    for _ in range(max(args.warmup, 0)):
+        chip.step(1)
+    chip.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    clocks = _Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        chip.step(1)  # one launch of the fused step kernel (with diagnostics)
+    ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    d = chip.diagnostics()  # raises on a numeric error flag
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / max(args.steps, 1)
+    value = ws * fluid * args.steps / (ms / 1e3) / 1e9
+    peak, peak_src = _peak()
+    achieved = fluid * BYTES_PER_NODE / (ms_per_step / 1e3) / 1e9
+    extras = {}
+    if not args.skip_extras:
+        e2e_steps = min(args.steps, 5000)
+        e = _e2e(prob, e2e_steps, local)
+        if ws > 1:
+            t = torch.tensor([e["seconds"]], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e["value"] = ws * fluid * e2e_steps / float(t.item()) / 1e9
+        extras["e2e"] = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+        if ws == 1 and rank == 0:
+            extras["cpu_baseline"] = _cpu_baseline(args.cpu_seconds)
+    chip.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%s two-channel gradient chip, FP32 populations" % prob["name"],
+                       "nx": prob["nx"], "ny": prob["ny"], "fluid_nodes": fluid,
+                       "tau": prob["tau"], "tau_c": prob["tau_c"], "valve_period": prob["period"],
+                       "l2": "inputs larger than L2 (%.2f GB of populations per copy)"
+                             % (info["pitch"] * prob["ny"] * 14 * 4 / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "launch": {"grid": info["grid"], "block": info["block"], "tiles": info["n_tiles"]}},
+            "all_node_glups": ws * prob["nx"] * prob["ny"] * args.steps / (ms / 1e3) / 1e9,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": _traffic(fluid),
+                         "peak_source": "%s (hbm_gbs)" % peak_src,
+                         "bytes_per_launch": fluid * BYTES_PER_NODE},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "adjoint_forward_ratio": None,
+            "diagnostics": {"mass": d[0], "scalar": d[1]},
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

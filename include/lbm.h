@@ -1,0 +1,226 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) coupled lattice Boltzmann library.
+ *
+ * One handle holds one 2-D microfluidic chip: a D2Q9 BGK fluid lattice
+ * (Eq. lattice, Eq. lbequation, Eq. moments) and a scalar lattice for the
+ * compound's advection-diffusion equation (Eq. cde with R = 0, solved by the
+ * multi-distribution approach of Eq. cdeequilibrium) driven by the fluid
+ * velocity of the same node and time step.  Walls are halfway bounce-back
+ * for both lattices (zero flux).  Valve-controlled ports switch between an
+ * open inlet/outlet and a wall as the source and sink valves toggle
+ * (section "Experimental Layout and Conditions"; section "Results": closed
+ * valves are ordinary no-flux walls, an open inlet holds a prescribed
+ * concentration, an open outlet is do-nothing).
+ *
+ * Conventions
+ *   - Lattice coordinates (x, y), 0 <= x < nx along the channels, 0 <= y < ny,
+ *     +y = e_2 ("north").  Host arrays of per-node values are row-major
+ *     [y][x], nx*ny entries.
+ *   - Directions (Eq. lattice): 0 rest; 1 E, 2 N, 3 W, 4 S; 5 NE, 6 NW,
+ *     7 SW, 8 SE.  The scalar lattice uses directions 0..4.
+ *   - Scalar lattice: rest weight w0, w_{1..4} = (1 - w0)/4,
+ *     c_s^2 = (1 - w0)/2, g_eq_i = w_i C (1 + e_i.u / c_s^2),
+ *     D = c_s^2 (tau_c - 1/2).  w0 = 1/3 (default) is D2Q5; w0 = 0 is the
+ *     paper's D2Q4 lattice, g_eq = C/4 (1 + 2 e.u), D = (2 tau_c - 1)/4.
+ *   - Fluid viscosity nu = (tau - 1/2)/3 (c_s^2 = 1/3).
+ *   - Populations are FP32.  Diagnostics are accumulated in FP64.
+ *   - Every call returns lbm_status; no C++ exception crosses the ABI.  On
+ *     an error, lbm_last_error(handle) (or lbm_last_error(NULL) for
+ *     lbm_create) gives a one-line reason.  A handle is not thread-safe:
+ *     one thread at a time per handle.
+ *   - Input arrays are copied before the call returns; the caller keeps
+ *     ownership of every pointer it passes.
+ *   - Device work is issued on the handle's stream (lbm_options.stream).
+ *     Calls that read results into HOST memory synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx* lbm_handle;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,      /* invalid argument; nothing was changed */
+    LBM_ERR_CUDA = 2,     /* a CUDA runtime call failed (no device, launch error) */
+    LBM_ERR_OOM = 3,      /* device allocation failed */
+    LBM_ERR_NUMERIC = 4,  /* a fluid node had non-finite or non-positive density,
+                             or non-finite concentration (sticky until
+                             lbm_clear_error) */
+    LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+    LBM_ERR_STATE = 6     /* call not valid in the handle's current state */
+} lbm_status;
+
+enum { LBM_WEST = 0, LBM_EAST = 1 };
+enum { LBM_PORT_VELOCITY = 0, LBM_PORT_PRESSURE = 1 };
+
+/* One valve-controlled opening of the chip ("Experimental Layout and
+ * Conditions": each channel's inlet and outlet are controlled by valves).
+ *
+ * The port covers the nodes (x, y) for y0 <= y < y1 of one column.  A WEST
+ * port receives fluid from -x: at its nodes the populations with e_x = +1
+ * (1, 5, 8) come from outside; an EAST port is the mirror image (3, 6, 7).
+ * The cells on the outer side of the port, (x - 1, y) for WEST and (x + 1, y)
+ * for EAST with y0 - 1 <= y <= y1, must be solid or outside the grid.
+ *
+ * The port is open during a time step when bit `channel` (0..31) of that
+ * step's valve word is set.  Open VELOCITY port: Zou-He velocity node
+ * u = (u_x(y), 0) for the fluid and a held concentration C_in(y) for the
+ * scalar (the inlet of a flushed channel).  Open PRESSURE port: Zou-He
+ * pressure node with density `rho` and zero tangential velocity for the
+ * fluid, do-nothing for the scalar (its missing population keeps its own
+ * post-collision value of the previous step: zeroth-order extrapolation in
+ * time).  Closed port: wall, as everywhere else. */
+typedef struct {
+    int32_t channel;
+    int32_t side;   /* LBM_WEST or LBM_EAST */
+    int32_t x;
+    int32_t y0;
+    int32_t y1;
+    int32_t kind;   /* LBM_PORT_VELOCITY or LBM_PORT_PRESSURE */
+    double rho;     /* PRESSURE ports: prescribed density (> 0) */
+} lbm_port;
+
+/* Device allocator hooks.  alloc returns a device pointer (>= 256-byte
+ * aligned) or NULL; free releases it.  Both are called only from
+ * lbm_create / lbm_destroy (and lbm_init_equilibrium for a temporary). */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*lbm_free_fn)(void* ptr, size_t bytes, void* user);
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(lbm_options), set by lbm_default_options */
+    int32_t device;         /* CUDA device ordinal; -1 = the current device */
+    double w0;              /* scalar rest weight, 0 <= w0 < 1 (default 1/3) */
+    double rho0;            /* initial density (default 1) */
+    double C0;              /* initial concentration (default 0) */
+    void* stream;           /* cudaStream_t for all device work; NULL = legacy default stream */
+    lbm_alloc_fn alloc;     /* NULL = cudaMalloc */
+    lbm_free_fn free;       /* NULL = cudaFree */
+    void* alloc_user;
+    int32_t block_threads;  /* step kernel block size: 0 = default (256), else 64..256, a multiple of 32 */
+    int32_t max_blocks;     /* step kernel grid cap: 0 = one wave of resident blocks */
+} lbm_options;
+
+/* Fill *opt with the defaults listed above. */
+void lbm_default_options(lbm_options* opt);
+
+/* Create a chip.
+ *   mask      nx*ny bytes, row-major [y][x]: 0 = fluid, non-zero = solid.
+ *             Needs at least one fluid node; every fluid node needs at least
+ *             one fluid node among its 8 neighbours inside the grid.
+ *   tau       fluid relaxation time tau_f > 1/2 (Eq. lbequation).
+ *   tau_c     scalar relaxation time tau_g > 1/2.
+ *   ports     n_ports entries (0 <= n_ports <= 64), see lbm_port.  A row
+ *             holds at most one WEST and one EAST port node.
+ *   edge_u    2*ny floats, [side*ny + y]: u_x of the VELOCITY port node of
+ *             that side and row, |u_x| < 1 (a caller-built profile, e.g.
+ *             the parabolic channel profile).  Ignored elsewhere.
+ *   edge_C    2*ny floats, same layout: held concentration of VELOCITY port
+ *             nodes (the source/sink concentrations).  Both may be NULL only
+ *             when there are no VELOCITY ports.
+ *   opt       NULL = defaults.
+ * Initial state: every node at the equilibrium of rho0, u = 0, C0; step
+ * counter 0; valve word 0 (all closed); no schedule.
+ * Errors: LBM_ERR_ARG (nothing allocated), LBM_ERR_CUDA, LBM_ERR_OOM. */
+lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* mask,
+                      double tau, double tau_c, int32_t n_ports, const lbm_port* ports,
+                      const float* edge_u, const float* edge_C, const lbm_options* opt);
+
+/* Release every resource of the handle (waits for its stream).  NULL is a
+ * no-op. */
+void lbm_destroy(lbm_handle h);
+
+/* Fixed valve word for the following steps (bit k opens channel k's ports).
+ * Clears any schedule. */
+lbm_status lbm_set_valves(lbm_handle h, uint32_t open_mask);
+
+/* Valve schedule: time step t (counted from creation, see lbm_get_step)
+ * uses states[(t / period) % n].  n = 0 clears the schedule (the last fixed
+ * valve word applies again).  period >= 1, 0 <= n <= 4096. */
+lbm_status lbm_set_valve_schedule(lbm_handle h, int64_t period, int32_t n,
+                                  const uint32_t* states);
+
+/* Advance n >= 0 coupled time steps, asynchronously on the handle's stream.
+ * Each step is one launch of the fused kernel: pull-stream of f and g,
+ * bounce-back, open-port completion, moments, collision of f, collision of
+ * g with the same step's velocity.  The last step of the call also forms
+ * the diagnostics (lbm_get_diagnostics).  Returns LBM_ERR_NUMERIC (after
+ * issuing the steps) while a previous synchronising call has found the
+ * numeric error flag set and lbm_clear_error has not reset it. */
+lbm_status lbm_step(lbm_handle h, int64_t n);
+
+/* Moments of the current state (Eq. moments; C = sum of g) into HOST
+ * arrays of nx*ny floats; any may be NULL.  Solid nodes report 0.
+ * Synchronises the stream. */
+lbm_status lbm_get_fields(lbm_handle h, float* rho, float* ux, float* uy, float* C);
+
+/* Same into DEVICE arrays of nx*ny floats (row-major, pitch nx), issued on
+ * the handle's stream without synchronising; any may be NULL. */
+lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy, float* C);
+
+/* Diagnostics of the last step of the most recent lbm_step call (zeros
+ * before the first step): out[0] = sum of rho over fluid nodes, out[1] =
+ * sum of C over fluid nodes, out[2] = sum of rho u_x and out[3] = sum of
+ * C u_x over the nodes of the PRESSURE ports open during that step.
+ * Accumulated in FP64 in a fixed order (run-to-run identical).  Synchronises
+ * the stream; returns LBM_ERR_NUMERIC if a bad value was flagged. */
+lbm_status lbm_get_diagnostics(lbm_handle h, double out[4]);
+
+/* Current post-collision populations into HOST arrays: f = 9*nx*ny floats,
+ * g = 5*nx*ny floats, layout [i][y][x].  Either may be NULL.  Synchronises. */
+lbm_status lbm_get_populations(lbm_handle h, float* f, float* g);
+
+/* Replace the state's populations (same layout); values of solid nodes are
+ * ignored.  Either may be NULL (kept). */
+lbm_status lbm_set_populations(lbm_handle h, const float* f, const float* g);
+
+/* Set every fluid node to the equilibrium of the given HOST fields (nx*ny
+ * floats each; none may be NULL). */
+lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux,
+                                const float* uy, const float* C);
+
+/* Checkpoint / resume: the step counter, fixed valve word, schedule and
+ * populations.  lbm_save_state with buf == NULL stores the needed size in
+ * *bytes; otherwise *bytes must be at least that size.  lbm_load_state
+ * accepts only a buffer saved from a handle of the same nx, ny. */
+lbm_status lbm_save_state(lbm_handle h, void* buf, size_t* bytes);
+lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes);
+
+/* Time steps taken since creation (or as restored by lbm_load_state). */
+lbm_status lbm_get_step(lbm_handle h, int64_t* t);
+
+/* Block until the handle's stream is idle; reports launch errors. */
+lbm_status lbm_synchronize(lbm_handle h);
+
+/* Reset a sticky LBM_ERR_NUMERIC flag. */
+lbm_status lbm_clear_error(lbm_handle h);
+
+typedef struct {
+    int32_t nx, ny;
+    int32_t pitch;          /* floats per stored row (multiple of 128) */
+    int32_t n_tiles;        /* 128-node row segments that hold fluid */
+    int32_t grid, block;    /* step kernel launch shape */
+    int64_t fluid_nodes;
+    int64_t algorithmic_bytes_per_step;  /* fluid_nodes * 112: 14 FP32 populations read and written */
+    int64_t device_bytes;   /* device memory held by the handle */
+} lbm_info;
+
+lbm_status lbm_get_info(lbm_handle h, lbm_info* info);
+
+/* Last error message of the handle, or of the calling thread's most recent
+ * lbm_create when h is NULL.  Never NULL. */
+const char* lbm_last_error(lbm_handle h);
+
+/* Static name of a status code. */
+const char* lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

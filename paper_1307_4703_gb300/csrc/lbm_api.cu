@@ -1,0 +1,643 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// Owns the device state of one chip (see lbm_internal.h for the layout),
+// validates every argument before touching the device, builds the wall-link
+// table, the per-row port table and the list of fluid tiles, and issues the
+// kernels on the handle's stream.  No call here computes any part of the
+// time step on the host.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+constexpr uint32_t kStateMagic = 0x4C424D31u;  // "LBM1"
+constexpr int kMaxPorts = 64;
+constexpr int kMaxSchedule = 4096;
+
+struct Alloc {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, pitch = 0, segs = 0;
+    long long plane = 0;
+    double tau = 0, tau_c = 0, w0 = 0, rho0 = 1, C0 = 0;
+    float wg0 = 0, wg1 = 0, inv_cs2g = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lbm_alloc_fn alloc_fn = nullptr;
+    lbm_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+
+    std::vector<Alloc> allocs;
+    float* pop[2] = {nullptr, nullptr};
+    int cur = 0;  // buffer holding the current state
+    uint8_t* links = nullptr;
+    lbm::RowBC* rowbc = nullptr;
+    uint32_t* tiles = nullptr;
+    double* partials = nullptr;
+    unsigned int* ticket = nullptr;
+    double* diag = nullptr;
+    unsigned int* err = nullptr;
+    float* fields_tmp = nullptr;  // 4 * nx * ny floats
+
+    int n_tiles = 0;
+    int grid = 0, block = 256, grid_cap = 0;
+    long long fluid = 0;
+    long long device_bytes = 0;
+
+    int64_t step = 0;
+    uint32_t fixed_mask = 0;
+    int64_t period = 0;
+    std::vector<uint32_t> schedule;
+    bool numeric = false;  // the device error word was found set
+
+    std::string last_error = "no error";
+
+    uint32_t mask_at(int64_t t) const
+    {
+        if (!schedule.empty())
+            return schedule[size_t((t / period) % int64_t(schedule.size()))];
+        return fixed_mask;
+    }
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* h, lbm_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->last_error = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(h, call)                                       \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+void* dev_alloc(lbm_ctx* h, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (h->alloc_fn) {
+        p = h->alloc_fn(bytes, h->alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        h->allocs.push_back({p, bytes});
+        h->device_bytes += (long long)bytes;
+    }
+    return p;
+}
+
+void free_all(lbm_ctx* h)
+{
+    for (auto& a : h->allocs) {
+        if (h->free_fn) h->free_fn(a.ptr, a.bytes, h->alloc_user);
+        else cudaFree(a.ptr);
+    }
+    h->allocs.clear();
+}
+
+bool is_fluid(const uint8_t* mask, int nx, int ny, int x, int y)
+{
+    return x >= 0 && x < nx && y >= 0 && y < ny && mask[size_t(y) * nx + x] == 0;
+}
+
+// Eq. lattice directions 1..8 (index 0 is the rest direction).
+constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+lbm_status check_ctx(lbm_ctx* h)
+{
+    if (!h) return LBM_ERR_ARG;
+    return LBM_OK;
+}
+
+lbm_status pending_numeric(lbm_ctx* h)
+{
+    return h->numeric ? LBM_ERR_NUMERIC : LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_options(lbm_options* opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->struct_size = sizeof(lbm_options);
+    opt->device = -1;
+    opt->w0 = 1.0 / 3.0;
+    opt->rho0 = 1.0;
+    opt->C0 = 0.0;
+}
+
+const char* lbm_status_string(lbm_status s)
+{
+    switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_ERR_ARG: return "LBM_ERR_ARG";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+    case LBM_ERR_OOM: return "LBM_ERR_OOM";
+    case LBM_ERR_NUMERIC: return "LBM_ERR_NUMERIC";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+    case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    }
+    return "LBM_ERR_UNKNOWN";
+}
+
+const char* lbm_last_error(lbm_handle h)
+{
+    return h ? h->last_error.c_str() : g_create_error.c_str();
+}
+
+lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* mask, double tau,
+                      double tau_c, int32_t n_ports, const lbm_port* ports, const float* edge_u,
+                      const float* edge_C, const lbm_options* opt_in)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    lbm_options opt;
+    lbm_default_options(&opt);
+    if (opt_in) {
+        if (opt_in->struct_size != sizeof(lbm_options))
+            return fail(nullptr, LBM_ERR_ARG, "lbm_options.struct_size is %u, expected %zu",
+                        opt_in->struct_size, sizeof(lbm_options));
+        opt = *opt_in;
+    }
+    // ---- argument checks (no device call before they pass) ----
+    if (nx < 1 || ny < 1) return fail(nullptr, LBM_ERR_ARG, "grid %d x %d is empty", nx, ny);
+    if (ny >= (1 << 19) || nx > (1 << lbm::kSegBits) * lbm::kTileNodes - lbm::kTileNodes)
+        return fail(nullptr, LBM_ERR_ARG, "grid %d x %d is too large", nx, ny);
+    if (!mask) return fail(nullptr, LBM_ERR_ARG, "mask is NULL");
+    if (!(tau > 0.5) || !std::isfinite(tau))
+        return fail(nullptr, LBM_ERR_ARG, "tau = %g: the fluid relaxation time must exceed 1/2", tau);
+    if (!(tau_c > 0.5) || !std::isfinite(tau_c))
+        return fail(nullptr, LBM_ERR_ARG, "tau_c = %g: the scalar relaxation time must exceed 1/2", tau_c);
+    if (!(opt.w0 >= 0.0 && opt.w0 < 1.0))
+        return fail(nullptr, LBM_ERR_ARG, "w0 = %g outside [0, 1)", opt.w0);
+    if (!(opt.rho0 > 0.0) || !std::isfinite(opt.rho0) || !std::isfinite(opt.C0))
+        return fail(nullptr, LBM_ERR_ARG, "initial rho0 = %g, C0 = %g invalid", opt.rho0, opt.C0);
+    if (opt.block_threads != 0 &&
+        (opt.block_threads < 64 || opt.block_threads > 256 || opt.block_threads % 32 != 0))
+        return fail(nullptr, LBM_ERR_ARG, "block_threads = %d: use 0 or a multiple of 32 in [64, 256]",
+                    opt.block_threads);
+    if (opt.max_blocks < 0) return fail(nullptr, LBM_ERR_ARG, "max_blocks = %d < 0", opt.max_blocks);
+    if ((opt.alloc == nullptr) != (opt.free == nullptr))
+        return fail(nullptr, LBM_ERR_ARG, "alloc and free hooks must be given together");
+    if (n_ports < 0 || n_ports > kMaxPorts)
+        return fail(nullptr, LBM_ERR_ARG, "n_ports = %d outside [0, %d]", n_ports, kMaxPorts);
+    if (n_ports > 0 && !ports) return fail(nullptr, LBM_ERR_ARG, "ports is NULL");
+
+    long long fluid = 0;
+    for (long long k = 0; k < (long long)nx * ny; ++k) fluid += mask[k] == 0;
+    if (fluid == 0) return fail(nullptr, LBM_ERR_ARG, "the mask has no fluid node");
+
+    std::vector<lbm::RowBC> rowbc(size_t(2) * ny, lbm::RowBC{-1, 0, 0.f, 0.f});
+    bool any_velocity = false;
+    for (int p = 0; p < n_ports; ++p) {
+        const lbm_port& P = ports[p];
+        if (P.channel < 0 || P.channel > 31)
+            return fail(nullptr, LBM_ERR_ARG, "port %d: channel %d outside [0, 31]", p, P.channel);
+        if (P.side != LBM_WEST && P.side != LBM_EAST)
+            return fail(nullptr, LBM_ERR_ARG, "port %d: side %d invalid", p, P.side);
+        if (P.kind != LBM_PORT_VELOCITY && P.kind != LBM_PORT_PRESSURE)
+            return fail(nullptr, LBM_ERR_ARG, "port %d: kind %d invalid", p, P.kind);
+        if (P.x < 0 || P.x >= nx || P.y0 < 0 || P.y1 > ny || P.y0 >= P.y1)
+            return fail(nullptr, LBM_ERR_ARG, "port %d: column %d rows [%d, %d) outside the grid", p,
+                        P.x, P.y0, P.y1);
+        if (P.kind == LBM_PORT_PRESSURE && !(P.rho > 0.0 && std::isfinite(P.rho)))
+            return fail(nullptr, LBM_ERR_ARG, "port %d: pressure density %g invalid", p, P.rho);
+        const int s = P.side == LBM_WEST ? 1 : -1;
+        for (int y = P.y0; y < P.y1; ++y) {
+            if (!is_fluid(mask, nx, ny, P.x, y))
+                return fail(nullptr, LBM_ERR_ARG, "port %d: node (%d, %d) is solid", p, P.x, y);
+            lbm::RowBC& b = rowbc[size_t(P.side) * ny + y];
+            if (b.x >= 0) return fail(nullptr, LBM_ERR_ARG, "port %d: row %d already has a port on that side", p, y);
+            const lbm::RowBC& o = rowbc[size_t(1 - P.side) * ny + y];
+            if (o.x == P.x)
+                return fail(nullptr, LBM_ERR_ARG, "port %d: node (%d, %d) is also a port of the other side", p, P.x, y);
+            b.x = P.x;
+            b.chan_kind = P.channel | (P.kind << 8);
+            b.a = P.kind == LBM_PORT_PRESSURE ? float(P.rho) : 0.f;
+        }
+        for (int y = P.y0 - 1; y <= P.y1; ++y)
+            if (is_fluid(mask, nx, ny, P.x - s, y))
+                return fail(nullptr, LBM_ERR_ARG, "port %d: cell (%d, %d) outside the port is fluid", p,
+                            P.x - s, y);
+        any_velocity |= P.kind == LBM_PORT_VELOCITY;
+    }
+    if (any_velocity && (!edge_u || !edge_C))
+        return fail(nullptr, LBM_ERR_ARG, "velocity ports need edge_u and edge_C");
+    for (int side = 0; side < 2; ++side)
+        for (int y = 0; y < ny; ++y) {
+            lbm::RowBC& b = rowbc[size_t(side) * ny + y];
+            if (b.x < 0 || (b.chan_kind >> 8) != LBM_PORT_VELOCITY) continue;
+            const float u = edge_u[size_t(side) * ny + y], c = edge_C[size_t(side) * ny + y];
+            if (!(std::fabs(u) < 1.f) || !std::isfinite(c))
+                return fail(nullptr, LBM_ERR_ARG, "velocity port row %d: u_x = %g, C = %g invalid", y, u, c);
+            b.a = u;
+            b.c = c;
+        }
+
+    // wall-link table; every fluid node needs a fluid neighbour
+    const int pitch = (nx + lbm::kTileNodes - 1) / lbm::kTileNodes * lbm::kTileNodes;
+    const int segs = pitch / lbm::kTileNodes;
+    std::vector<uint8_t> links(size_t(pitch) * ny, lbm::kSolid);
+    std::vector<uint32_t> tiles;
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            if (!is_fluid(mask, nx, ny, x, y)) continue;
+            uint8_t lb = 0;
+            for (int i = 1; i <= 8; ++i)
+                if (!is_fluid(mask, nx, ny, x - kEx[i], y - kEy[i])) lb |= uint8_t(1u << (i - 1));
+            if (lb == lbm::kSolid)
+                return fail(nullptr, LBM_ERR_ARG, "fluid node (%d, %d) has no fluid neighbour", x, y);
+            links[size_t(y) * pitch + x] = lb;
+        }
+        for (int s = 0; s < segs; ++s) {
+            bool any = false;
+            for (int x = s * lbm::kTileNodes; x < std::min(nx, (s + 1) * lbm::kTileNodes) && !any; ++x)
+                any = mask[size_t(y) * nx + x] == 0;
+            if (any) tiles.push_back((uint32_t(y) << lbm::kSegBits) | uint32_t(s));
+        }
+    }
+
+    // ---- device set-up ----
+    lbm_ctx* h = new (std::nothrow) lbm_ctx();
+    if (!h) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->pitch = pitch;
+    h->segs = segs;
+    h->plane = (long long)ny * pitch;
+    h->tau = tau;
+    h->tau_c = tau_c;
+    h->w0 = opt.w0;
+    h->rho0 = opt.rho0;
+    h->C0 = opt.C0;
+    h->wg0 = float(opt.w0);
+    h->wg1 = float(0.25 * (1.0 - opt.w0));
+    h->inv_cs2g = float(2.0 / (1.0 - opt.w0));
+    h->stream = static_cast<cudaStream_t>(opt.stream);
+    h->alloc_fn = opt.alloc;
+    h->free_fn = opt.free;
+    h->alloc_user = opt.alloc_user;
+    h->n_tiles = int(tiles.size());
+    h->fluid = fluid;
+    h->block = opt.block_threads ? opt.block_threads : 256;
+    h->grid_cap = opt.max_blocks;
+
+    auto bail = [&](lbm_status s) {
+        g_create_error = h->last_error;
+        free_all(h);
+        delete h;
+        return s;
+    };
+    cudaError_t e;
+    if (opt.device >= 0) {
+        e = cudaSetDevice(opt.device);
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaSetDevice"));
+    }
+    e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
+    e = lbm::step_kernel_occupancy(h->block, true, &per_sm);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
+    {
+        int per_sm_nodiag = 0;
+        e = lbm::step_kernel_occupancy(h->block, false, &per_sm_nodiag);
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
+        per_sm = std::max(1, std::min(per_sm, per_sm_nodiag));
+    }
+    const int wpb = h->block / 32;
+    const int need = (h->n_tiles + wpb - 1) / wpb;
+    h->grid = std::max(1, std::min(need, per_sm * sms));
+    if (h->grid_cap > 0) h->grid = std::min(h->grid, h->grid_cap);
+
+    const size_t pop_bytes = size_t(h->plane) * lbm::kPlanes * sizeof(float);
+    h->pop[0] = static_cast<float*>(dev_alloc(h, pop_bytes));
+    h->pop[1] = static_cast<float*>(dev_alloc(h, pop_bytes));
+    h->links = static_cast<uint8_t*>(dev_alloc(h, links.size()));
+    h->rowbc = static_cast<lbm::RowBC*>(dev_alloc(h, rowbc.size() * sizeof(lbm::RowBC)));
+    h->tiles = static_cast<uint32_t*>(dev_alloc(h, std::max<size_t>(1, tiles.size()) * 4));
+    h->partials = static_cast<double*>(dev_alloc(h, size_t(h->grid) * 4 * sizeof(double)));
+    h->ticket = static_cast<unsigned*>(dev_alloc(h, 2 * sizeof(unsigned)));
+    h->diag = static_cast<double*>(dev_alloc(h, 4 * sizeof(double)));
+    h->fields_tmp = static_cast<float*>(dev_alloc(h, size_t(4) * nx * ny * sizeof(float)));
+    if (!h->pop[0] || !h->pop[1] || !h->links || !h->rowbc || !h->tiles || !h->partials ||
+        !h->ticket || !h->diag || !h->fields_tmp)
+        return bail(fail(h, LBM_ERR_OOM, "device allocation of %zu bytes failed", 2 * pop_bytes));
+    h->err = h->ticket + 1;
+
+    cudaStream_t st = h->stream;
+    e = cudaMemcpyAsync(h->links, links.data(), links.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->rowbc, rowbc.data(), rowbc.size() * sizeof(lbm::RowBC),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->diag, 0, 4 * sizeof(double), st);
+    if (e == cudaSuccess)
+        e = lbm::launch_init_rest(h->pop[0], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0), st);
+    if (e == cudaSuccess)
+        e = lbm::launch_init_rest(h->pop[1], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0), st);
+    // the host tables above are pageable: wait so they may go out of scope
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "device initialisation"));
+    *out = h;
+    g_create_error = "no error";
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+lbm_status lbm_set_valves(lbm_handle h, uint32_t open_mask)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    h->fixed_mask = open_mask;
+    h->schedule.clear();
+    h->period = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_valve_schedule(lbm_handle h, int64_t period, int32_t n, const uint32_t* states)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (n == 0) {
+        h->schedule.clear();
+        h->period = 0;
+        return LBM_OK;
+    }
+    if (n < 0 || n > kMaxSchedule) return fail(h, LBM_ERR_ARG, "schedule length %d outside [0, %d]", n, kMaxSchedule);
+    if (period < 1) return fail(h, LBM_ERR_ARG, "schedule period %lld < 1", (long long)period);
+    if (!states) return fail(h, LBM_ERR_ARG, "states is NULL");
+    h->schedule.assign(states, states + n);
+    h->period = period;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle h, int64_t n)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
+    lbm::StepArgs a{};
+    a.links = h->links;
+    a.rowbc = h->rowbc;
+    a.tiles = h->tiles;
+    a.n_tiles = h->n_tiles;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.omega_f = float(1.0 / h->tau);
+    a.omega_g = float(1.0 / h->tau_c);
+    a.wg0 = h->wg0;
+    a.wg1 = h->wg1;
+    a.inv_cs2g = h->inv_cs2g;
+    a.partials = h->partials;
+    a.ticket = h->ticket;
+    a.diag = h->diag;
+    a.err = h->err;
+    for (int64_t k = 0; k < n; ++k) {
+        a.src = h->pop[h->cur];
+        a.dst = h->pop[1 - h->cur];
+        a.open_mask = h->mask_at(h->step);
+        cudaError_t e = lbm::launch_step(a, h->grid, h->block, k == n - 1, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+        h->cur = 1 - h->cur;
+        ++h->step;
+    }
+    return pending_numeric(h);
+}
+
+lbm_status lbm_synchronize(lbm_handle h)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    LBM_CUDA(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+static lbm_status read_err_word(lbm_handle h)
+{
+    unsigned err = 0;
+    LBM_CUDA(h, cudaMemcpyAsync(&err, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (err) h->numeric = true;
+    if (err) return fail(h, LBM_ERR_NUMERIC, "numeric: a fluid node reached a non-finite or non-positive density or a non-finite concentration");
+    return pending_numeric(h);
+}
+
+lbm_status lbm_clear_error(lbm_handle h)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    LBM_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->numeric = false;
+    h->last_error = "no error";
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy, float* C)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    cudaError_t e = lbm::launch_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, rho, ux, uy, C, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_handle h, float* rho, float* ux, float* uy, float* C)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    const size_t n = size_t(h->nx) * h->ny;
+    float* t = h->fields_tmp;
+    lbm_status s = lbm_get_fields_device(h, rho ? t : nullptr, ux ? t + n : nullptr,
+                                         uy ? t + 2 * n : nullptr, C ? t + 3 * n : nullptr);
+    if (s != LBM_OK) return s;
+    float* outs[4] = {rho, ux, uy, C};
+    for (int q = 0; q < 4; ++q)
+        if (outs[q])
+            LBM_CUDA(h, cudaMemcpyAsync(outs[q], t + q * n, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_diagnostics(lbm_handle h, double out[4])
+{
+    if (check_ctx(h) || !out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    LBM_CUDA(h, cudaMemcpyAsync(out, h->diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return read_err_word(h);
+}
+
+lbm_status lbm_get_populations(lbm_handle h, float* f, float* g)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    const float* src = h->pop[h->cur];
+    const size_t row = size_t(h->nx) * sizeof(float), pitch = size_t(h->pitch) * sizeof(float);
+    if (f)
+        LBM_CUDA(h, cudaMemcpy2DAsync(f, row, src, pitch, row, size_t(9) * h->ny, cudaMemcpyDeviceToHost, h->stream));
+    if (g)
+        LBM_CUDA(h, cudaMemcpy2DAsync(g, row, src + 9 * h->plane, pitch, row, size_t(5) * h->ny,
+                                      cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_handle h, const float* f, const float* g)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    float* dst = h->pop[h->cur];
+    const size_t row = size_t(h->nx) * sizeof(float), pitch = size_t(h->pitch) * sizeof(float);
+    if (f)
+        LBM_CUDA(h, cudaMemcpy2DAsync(dst, pitch, f, row, row, size_t(9) * h->ny, cudaMemcpyHostToDevice, h->stream));
+    if (g)
+        LBM_CUDA(h, cudaMemcpy2DAsync(dst + 9 * h->plane, pitch, g, row, row, size_t(5) * h->ny,
+                                      cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux, const float* uy,
+                                const float* C)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (!rho || !ux || !uy || !C) return fail(h, LBM_ERR_ARG, "a field pointer is NULL");
+    const size_t n = size_t(h->nx) * h->ny;
+    float* t = h->fields_tmp;
+    const float* ins[4] = {rho, ux, uy, C};
+    for (int q = 0; q < 4; ++q)
+        LBM_CUDA(h, cudaMemcpyAsync(t + q * n, ins[q], n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    cudaError_t e = lbm::launch_init_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, t, t + n,
+                                            t + 2 * n, t + 3 * n, h->wg0, h->wg1, h->inv_cs2g, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium kernel launch");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+namespace {
+struct StateHeader {
+    uint32_t magic;
+    int32_t nx, ny;
+    int32_t n_sched;
+    int64_t step;
+    int64_t period;
+    uint32_t fixed_mask;
+    uint32_t reserved;
+};
+}  // namespace
+
+lbm_status lbm_save_state(lbm_handle h, void* buf, size_t* bytes)
+{
+    if (check_ctx(h) || !bytes) return fail(h, LBM_ERR_ARG, "bytes is NULL");
+    const size_t pop = size_t(h->nx) * h->ny * lbm::kPlanes * sizeof(float);
+    const size_t need = sizeof(StateHeader) + h->schedule.size() * 4 + pop;
+    if (!buf) {
+        *bytes = need;
+        return LBM_OK;
+    }
+    if (*bytes < need) return fail(h, LBM_ERR_ARG, "state buffer of %zu bytes, need %zu", *bytes, need);
+    StateHeader hd{kStateMagic, h->nx, h->ny, int32_t(h->schedule.size()), h->step, h->period, h->fixed_mask, 0};
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    if (!h->schedule.empty()) std::memcpy(p, h->schedule.data(), h->schedule.size() * 4);
+    p += h->schedule.size() * 4;
+    float* f = reinterpret_cast<float*>(p);
+    const size_t n = size_t(h->nx) * h->ny;
+    lbm_status s = lbm_get_populations(h, f, f + 9 * n);
+    if (s != LBM_OK) return s;
+    *bytes = need;
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes)
+{
+    if (check_ctx(h) || !buf) return fail(h, LBM_ERR_ARG, "buf is NULL");
+    StateHeader hd;
+    if (bytes < sizeof(hd)) return fail(h, LBM_ERR_ARG, "state buffer too short");
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.nx != h->nx || hd.ny != h->ny || hd.n_sched < 0 ||
+        hd.n_sched > kMaxSchedule || (hd.n_sched > 0 && hd.period < 1))
+        return fail(h, LBM_ERR_ARG, "state buffer does not match this chip");
+    const size_t n = size_t(h->nx) * h->ny;
+    const size_t need = sizeof(hd) + size_t(hd.n_sched) * 4 + n * lbm::kPlanes * sizeof(float);
+    if (bytes < need) return fail(h, LBM_ERR_ARG, "state buffer of %zu bytes, need %zu", bytes, need);
+    const char* p = static_cast<const char*>(buf) + sizeof(hd);
+    std::vector<uint32_t> sched(size_t(hd.n_sched));
+    if (hd.n_sched) std::memcpy(sched.data(), p, sched.size() * 4);
+    p += sched.size() * 4;
+    // the populations may not be 4-byte aligned inside a caller's buffer
+    std::vector<float> pop(n * lbm::kPlanes);
+    std::memcpy(pop.data(), p, pop.size() * sizeof(float));
+    lbm_status s = lbm_set_populations(h, pop.data(), pop.data() + 9 * n);
+    if (s != LBM_OK) return s;
+    h->step = hd.step;
+    h->period = hd.period;
+    h->fixed_mask = hd.fixed_mask;
+    h->schedule = std::move(sched);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_step(lbm_handle h, int64_t* t)
+{
+    if (check_ctx(h) || !t) return fail(h, LBM_ERR_ARG, "t is NULL");
+    *t = h->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_handle h, lbm_info* info)
+{
+    if (check_ctx(h) || !info) return fail(h, LBM_ERR_ARG, "info is NULL");
+    info->nx = h->nx;
+    info->ny = h->ny;
+    info->pitch = h->pitch;
+    info->n_tiles = h->n_tiles;
+    info->grid = h->grid;
+    info->block = h->block;
+    info->fluid_nodes = h->fluid;
+    info->algorithmic_bytes_per_step = h->fluid * 112;
+    info->device_bytes = h->device_bytes;
+    return LBM_OK;
+}
+
+}  // extern "C"

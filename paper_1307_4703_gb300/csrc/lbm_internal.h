@@ -1,0 +1,78 @@
+// lbm_internal.h -- device data layout and kernel launchers shared by the
+// host ABI (lbm_api.cu) and the kernels (lbm_kernels.cu).
+//
+// Layout in device memory (one chip):
+//   populations  two buffers (ping-pong), each kPlanes planes of ny rows of
+//                `pitch` floats: planes 0..8 hold f_0..f_8, planes 9..13 hold
+//                g_0..g_4.  pitch is a multiple of kTileNodes, so every row
+//                starts on a 512-byte boundary and a warp tile never leaves
+//                its row.  The stored values are POST-collision populations.
+//   links        ny*pitch bytes: bit (i-1) set when the pull source x - e_i
+//                of direction i = 1..8 is not a fluid node (solid, outside the
+//                grid, or outside a port).  0xFF marks a solid node.
+//   rowbc        2*ny entries (west side then east side): the port node of
+//                that side and row, if any.
+//   tiles        list of the 128-node row segments that hold fluid,
+//                (y << 12) | segment.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+constexpr int kTileNodes = 128;  // nodes per warp tile: 32 lanes x 4 nodes
+constexpr int kPlanes = 14;      // f_0..f_8, g_0..g_4
+constexpr int kSegBits = 12;     // tile encoding: segment in the low 12 bits
+constexpr uint8_t kSolid = 0xFF;
+
+struct RowBC {
+    int32_t x;          // port node column, -1 = no port on this side and row
+    int32_t chan_kind;  // valve channel | (kind << 8); kind 0 velocity, 1 pressure
+    float a;            // velocity port: u_x; pressure port: rho
+    float c;            // velocity port: held concentration
+};
+
+struct StepArgs {
+    const float* src;       // post-collision populations at time t
+    float* dst;             // post-collision populations at time t + 1
+    const uint8_t* links;
+    const RowBC* rowbc;
+    const uint32_t* tiles;
+    int n_tiles;
+    int ny;
+    int pitch;
+    long long plane;        // ny * pitch
+    float omega_f;          // 1 / tau_f
+    float omega_g;          // 1 / tau_g
+    float wg0;              // scalar rest weight
+    float wg1;              // scalar axis weight (1 - wg0) / 4
+    float inv_cs2g;         // 1 / c_s^2 of the scalar lattice
+    uint32_t open_mask;     // valve word of this step
+    // diagnostics (only read by the diagnostics variant)
+    double* partials;       // 4 per block
+    unsigned int* ticket;   // zero between launches
+    double* diag;           // 4 results
+    unsigned int* err;      // sticky numeric error word
+};
+
+cudaError_t launch_step(const StepArgs& a, int grid, int block, bool diag, cudaStream_t s);
+cudaError_t step_kernel_occupancy(int block, bool diag, int* blocks_per_sm);
+
+// Every node (fluid and solid, padding included) to the rest equilibrium
+// of rho0 and C0.
+cudaError_t launch_init_rest(float* pop, int ny, int pitch, float rho0, float wg0, float wg1,
+                             float C0, cudaStream_t s);
+
+// Fluid nodes to the equilibrium of fields given row-major [y][x] (nx per row).
+cudaError_t launch_init_fields(float* pop, const uint8_t* links, int nx, int ny, int pitch,
+                               const float* rho, const float* ux, const float* uy, const float* C,
+                               float wg0, float wg1, float inv_cs2g, cudaStream_t s);
+
+// Moments of the stored populations into row-major [y][x] arrays (any may be
+// null); solid nodes give 0.
+cudaError_t launch_fields(const float* pop, const uint8_t* links, int nx, int ny, int pitch,
+                          float* rho, float* ux, float* uy, float* C, cudaStream_t s);
+
+}  // namespace lbm

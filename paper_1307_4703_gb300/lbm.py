@@ -1,0 +1,284 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h``.
+
+Argument marshalling only: every step of the time step runs in the CUDA
+library ``_lib/liblbm_gb300.so``.  PyTorch, when given, supplies the CUDA
+stream and the device memory (through its caching allocator); it computes
+nothing.  If the library is missing, ``load()`` raises: there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+WEST, EAST = 0, 1
+VELOCITY, PRESSURE = 0, 1
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NUMERIC, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(7)
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbm_gb300.so")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_CUDA", 3: "LBM_ERR_OOM",
+                 4: "LBM_ERR_NUMERIC", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+
+
+class lbm_port(ctypes.Structure):
+    _fields_ = [("channel", ctypes.c_int32), ("side", ctypes.c_int32), ("x", ctypes.c_int32),
+                ("y0", ctypes.c_int32), ("y1", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("rho", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class lbm_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("w0", ctypes.c_double), ("rho0", ctypes.c_double), ("C0", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p), ("block_threads", ctypes.c_int32),
+                ("max_blocks", ctypes.c_int32)]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("n_tiles", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("fluid_nodes", ctypes.c_int64), ("algorithmic_bytes_per_step", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_P = ctypes.POINTER
+_f32p = _P(ctypes.c_float)
+_f64p = _P(ctypes.c_double)
+_u8p = _P(ctypes.c_uint8)
+_u32p = _P(ctypes.c_uint32)
+
+# name -> (restype, argtypes); the same names and order as include/lbm.h
+SIGNATURES = {
+    "lbm_default_options": (None, [_P(lbm_options)]),
+    "lbm_create": (ctypes.c_int, [_P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, _u8p,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int32, _P(lbm_port),
+                                  _f32p, _f32p, _P(lbm_options)]),
+    "lbm_destroy": (None, [ctypes.c_void_p]),
+    "lbm_set_valves": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "lbm_set_valve_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, _u32p]),
+    "lbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "lbm_get_fields": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p, _f32p, _f32p]),
+    "lbm_get_fields_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_get_diagnostics": (ctypes.c_int, [ctypes.c_void_p, _f64p]),
+    "lbm_get_populations": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p]),
+    "lbm_set_populations": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p]),
+    "lbm_init_equilibrium": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p, _f32p, _f32p]),
+    "lbm_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _P(ctypes.c_size_t)]),
+    "lbm_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "lbm_get_step": (ctypes.c_int, [ctypes.c_void_p, _P(ctypes.c_int64)]),
+    "lbm_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbm_clear_error": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbm_get_info": (ctypes.c_int, [ctypes.c_void_p, _P(lbm_info)]),
+    "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load(path=None):
+    """Load the CUDA library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("the CUDA library %s is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _fp(a):
+    return a.ctypes.data_as(_f32p)
+
+
+def _torch_hooks(device_index):
+    """Allocator hooks that hand out memory from PyTorch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=device_index)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+class Chip:
+    """One chip on one GPU: the handle of ``lbm_create`` and its calls.
+
+    ``solid`` (ny, nx): non-zero = solid.  ``ports``: dicts with channel,
+    side, x, y0, y1, kind, rho.  ``edge_u`` / ``edge_C``: (2, ny) per side
+    and row.  ``stream``: a ``torch.cuda.Stream`` (or raw cudaStream_t int);
+    ``torch_alloc``: take device memory from PyTorch's caching allocator.
+    """
+
+    def __init__(self, solid, tau, tau_c, ports=(), edge_u=None, edge_C=None, w0=1.0 / 3.0,
+                 rho0=1.0, C0=0.0, stream=None, torch_alloc=False, device=-1, block_threads=0,
+                 max_blocks=0):
+        self._lib = load()
+        solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
+        self.ny, self.nx = solid.shape
+        ports = list(ports)
+        parr = (lbm_port * max(1, len(ports)))()
+        for k, p in enumerate(ports):
+            parr[k] = lbm_port(int(p["channel"]), int(p["side"]), int(p["x"]), int(p["y0"]),
+                               int(p["y1"]), int(p["kind"]), float(p.get("rho", 1.0)))
+        eu = _f32(np.zeros((2, self.ny)) if edge_u is None else edge_u, (2, self.ny))
+        ec = _f32(np.zeros((2, self.ny)) if edge_C is None else edge_C, (2, self.ny))
+        opt = lbm_options()
+        self._lib.lbm_default_options(ctypes.byref(opt))
+        opt.device = int(device)
+        opt.w0, opt.rho0, opt.C0 = float(w0), float(rho0), float(C0)
+        opt.block_threads = int(block_threads)
+        opt.max_blocks = int(max_blocks)
+        self.stream = stream
+        if stream is not None:
+            opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        self._hooks = None
+        if torch_alloc:
+            import torch
+            dev = torch.cuda.current_device() if device < 0 else int(device)
+            self._hooks = _torch_hooks(dev)
+            opt.alloc, opt.free = self._hooks
+        h = ctypes.c_void_p()
+        st = self._lib.lbm_create(ctypes.byref(h), self.nx, self.ny, solid.ctypes.data_as(_u8p),
+                                  float(tau), float(tau_c), len(ports), parr, _fp(eu), _fp(ec),
+                                  ctypes.byref(opt))
+        if st != LBM_OK:
+            raise LbmError(st, self._lib.lbm_last_error(None).decode())
+        self._h = h
+        self.solid = solid.astype(bool)
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(prob["solid"], prob["tau"], prob["tau_c"], ports=prob["ports"],
+                   edge_u=prob["edge_u"], edge_C=prob["edge_C"], w0=prob.get("w0", 1.0 / 3.0), **kw)
+
+    # -- plumbing ------------------------------------------------------------
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, self._lib.lbm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- the ABI calls -------------------------------------------------------
+    def set_valves(self, open_mask):
+        self._check(self._lib.lbm_set_valves(self._h, int(open_mask) & 0xFFFFFFFF))
+
+    def set_valve_schedule(self, period, states):
+        arr = np.ascontiguousarray(states, dtype=np.uint32)
+        self._check(self._lib.lbm_set_valve_schedule(self._h, int(period), len(arr),
+                                                     arr.ctypes.data_as(_u32p)))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_step(self._h, int(n)))
+
+    def fields(self):
+        out = [np.empty((self.ny, self.nx), np.float32) for _ in range(4)]
+        self._check(self._lib.lbm_get_fields(self._h, *[_fp(a) for a in out]))
+        return tuple(out)  # rho, ux, uy, C
+
+    def fields_device(self, rho=None, ux=None, uy=None, C=None):
+        """Moments into device buffers (torch tensors or raw pointers)."""
+        ptrs = [ctypes.c_void_p(0 if a is None else int(getattr(a, "data_ptr", lambda: a)()))
+                for a in (rho, ux, uy, C)]
+        self._check(self._lib.lbm_get_fields_device(self._h, *ptrs))
+
+    def diagnostics(self):
+        out = np.zeros(4)
+        self._check(self._lib.lbm_get_diagnostics(self._h, out.ctypes.data_as(_f64p)))
+        return out
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx), np.float32)
+        g = np.empty((5, self.ny, self.nx), np.float32)
+        self._check(self._lib.lbm_get_populations(self._h, _fp(f), _fp(g)))
+        return f, g
+
+    def set_populations(self, f=None, g=None):
+        fa = None if f is None else _f32(f, (9, self.ny, self.nx))
+        ga = None if g is None else _f32(g, (5, self.ny, self.nx))
+        self._check(self._lib.lbm_set_populations(self._h, None if fa is None else _fp(fa),
+                                                  None if ga is None else _fp(ga)))
+
+    def init_equilibrium(self, rho, ux, uy, C):
+        a = [_f32(np.broadcast_to(v, (self.ny, self.nx))) for v in (rho, ux, uy, C)]
+        self._check(self._lib.lbm_init_equilibrium(self._h, *[_fp(v) for v in a]))
+
+    def save_state(self):
+        n = ctypes.c_size_t(0)
+        self._check(self._lib.lbm_save_state(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._lib.lbm_save_state(self._h, buf, ctypes.byref(n)))
+        return buf.raw[:n.value]
+
+    def load_state(self, data):
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        self._check(self._lib.lbm_load_state(self._h, buf, len(data)))
+
+    def step_count(self):
+        t = ctypes.c_int64()
+        self._check(self._lib.lbm_get_step(self._h, ctypes.byref(t)))
+        return t.value
+
+    def synchronize(self):
+        self._check(self._lib.lbm_synchronize(self._h))
+
+    def clear_error(self):
+        self._check(self._lib.lbm_clear_error(self._h))
+
+    def info(self):
+        i = lbm_info()
+        self._check(self._lib.lbm_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in lbm_info._fields_}
