@@ -250,7 +250,7 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
                 return fail(nullptr, LBM_ERR_ARG, "port %d: node (%d, %d) is also a port of the other side", p, P.x, y);
             b.x = P.x;
             b.chan_kind = P.channel | (P.kind << 8);
-            b.a = P.kind == LBM_PORT_PRESSURE ? float(P.rho) : 0.f;
+            b.a = P.kind == LBM_PORT_PRESSURE ? float(P.rho - 1.0) : 0.f;
         }
         for (int y = P.y0 - 1; y <= P.y1; ++y)
             if (is_fluid(mask, nx, ny, P.x - s, y))
@@ -509,9 +509,17 @@ lbm_status lbm_get_diagnostics(lbm_handle h, double out[4])
     return read_err_word(h);
 }
 
-lbm_status lbm_get_populations(lbm_handle h, float* f, float* g)
+}  // extern "C"
+
+namespace {
+
+// D2Q9 weights: the device stores f_i - w_i (see lbm_internal.h).
+constexpr float kW9[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
+                          1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
+
+// Copies of the stored representation, [plane][y][x] on the host.
+lbm_status raw_out(lbm_ctx* h, float* f, float* g)
 {
-    if (check_ctx(h)) return LBM_ERR_ARG;
     const float* src = h->pop[h->cur];
     const size_t row = size_t(h->nx) * sizeof(float), pitch = size_t(h->pitch) * sizeof(float);
     if (f)
@@ -523,9 +531,8 @@ lbm_status lbm_get_populations(lbm_handle h, float* f, float* g)
     return LBM_OK;
 }
 
-lbm_status lbm_set_populations(lbm_handle h, const float* f, const float* g)
+lbm_status raw_in(lbm_ctx* h, const float* f, const float* g)
 {
-    if (check_ctx(h)) return LBM_ERR_ARG;
     float* dst = h->pop[h->cur];
     const size_t row = size_t(h->nx) * sizeof(float), pitch = size_t(h->pitch) * sizeof(float);
     if (f)
@@ -535,6 +542,34 @@ lbm_status lbm_set_populations(lbm_handle h, const float* f, const float* g)
                                       cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_get_populations(lbm_handle h, float* f, float* g)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    lbm_status s = raw_out(h, f, g);
+    if (s != LBM_OK || !f) return s;
+    const size_t n = size_t(h->nx) * h->ny;
+    for (int i = 0; i < 9; ++i)
+        for (size_t k = 0; k < n; ++k) f[i * n + k] += kW9[i];
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_handle h, const float* f, const float* g)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    std::vector<float> fd;
+    if (f) {
+        const size_t n = size_t(h->nx) * h->ny;
+        fd.assign(f, f + 9 * n);
+        for (int i = 0; i < 9; ++i)
+            for (size_t k = 0; k < n; ++k) fd[i * n + k] -= kW9[i];
+    }
+    return raw_in(h, f ? fd.data() : nullptr, g);
 }
 
 lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux, const float* uy,
@@ -582,10 +617,12 @@ lbm_status lbm_save_state(lbm_handle h, void* buf, size_t* bytes)
     p += sizeof(hd);
     if (!h->schedule.empty()) std::memcpy(p, h->schedule.data(), h->schedule.size() * 4);
     p += h->schedule.size() * 4;
-    float* f = reinterpret_cast<float*>(p);
+    // the stored representation, bit for bit (the buffer may be unaligned)
     const size_t n = size_t(h->nx) * h->ny;
-    lbm_status s = lbm_get_populations(h, f, f + 9 * n);
+    std::vector<float> stored(n * lbm::kPlanes);
+    lbm_status s = raw_out(h, stored.data(), stored.data() + 9 * n);
     if (s != LBM_OK) return s;
+    std::memcpy(p, stored.data(), stored.size() * sizeof(float));
     *bytes = need;
     return LBM_OK;
 }
@@ -609,7 +646,7 @@ lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes)
     // the populations may not be 4-byte aligned inside a caller's buffer
     std::vector<float> pop(n * lbm::kPlanes);
     std::memcpy(pop.data(), p, pop.size() * sizeof(float));
-    lbm_status s = lbm_set_populations(h, pop.data(), pop.data() + 9 * n);
+    lbm_status s = raw_in(h, pop.data(), pop.data() + 9 * n);
     if (s != LBM_OK) return s;
     h->step = hd.step;
     h->period = hd.period;

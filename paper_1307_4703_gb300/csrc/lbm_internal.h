@@ -6,7 +6,11 @@
 //                `pitch` floats: planes 0..8 hold f_0..f_8, planes 9..13 hold
 //                g_0..g_4.  pitch is a multiple of kTileNodes, so every row
 //                starts on a 512-byte boundary and a warp tile never leaves
-//                its row.  The stored values are POST-collision populations.
+//                its row.  The stored values are POST-collision populations;
+//                the fluid planes hold the deviation f_i - w_i from the rest
+//                state rho = 1 (the bits of an FP32 word then resolve the
+//                small pressure differences that drive the flow), the
+//                scalar planes hold g_i itself.
 //   links        ny*pitch bytes: bit (i-1) set when the pull source x - e_i
 //                of direction i = 1..8 is not a fluid node (solid, outside the
 //                grid, or outside a port).  0xFF marks a solid node.
@@ -30,7 +34,7 @@ constexpr uint8_t kSolid = 0xFF;
 struct RowBC {
     int32_t x;          // port node column, -1 = no port on this side and row
     int32_t chan_kind;  // valve channel | (kind << 8); kind 0 velocity, 1 pressure
-    float a;            // velocity port: u_x; pressure port: rho
+    float a;            // velocity port: u_x; pressure port: rho - 1
     float c;            // velocity port: held concentration
 };
 

@@ -19,7 +19,8 @@
 // pull move between lanes by warp shuffle; lane 0 / lane 31 fetch the one
 // value that comes from the neighbouring segment.  Only segments that hold
 // fluid are listed in the tile table, and lanes whose four nodes are all
-// solid issue no memory traffic.  The grid is persistent (one wave of
+// solid load only the shifted planes a fluid neighbour lane needs and store
+// nothing.  The grid is persistent (one wave of
 // resident blocks) and strides over the tile table.
 #include <cmath>
 
@@ -107,13 +108,21 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
         const int halo_e = x0 + 4 < a.pitch ? 4 : 3;
         const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
         const bool act = lk != 0xFFFFFFFFu;  // some node of this lane is fluid
+        // A shifted plane's edge value also feeds the neighbouring lane (its
+        // pull source may be fluid in row y -+ 1 even where this lane's own
+        // nodes are all solid), so a lane loads it when it or that
+        // neighbour is active.
+        const unsigned ball = __ballot_sync(kFull, act);
+        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;  // feeds lane + 1
+        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;  // feeds lane - 1
 
         // ---- free flight (pull): v[p] component k = plane p at (x0+k) - e ----
         float4 v[kPlanes];
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) {
             const long long o = p * P + (src_row(p) == 0 ? oC : src_row(p) == 1 ? oS : oN);
-            float4 r = act ? ldg4(S + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool ld = src_col(p) == 0 ? act : src_col(p) == 1 ? ld_w : ld_e;
+            float4 r = ld ? ldg4(S + o) : make_float4(0.f, 0.f, 0.f, 0.f);
             if (src_col(p) == 1) {  // from column x - 1
                 float h = 0.f;
                 if (act && lane == 0) h = __ldg(S + o + halo_w);
@@ -160,7 +169,8 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
         const bool open_w = bw.x >= 0 && ((a.open_mask >> (bw.chan_kind & 31)) & 1u);
         const bool open_e = be.x >= 0 && ((a.open_mask >> (be.chan_kind & 31)) & 1u);
 
-        float t_m = 0.f, t_c = 0.f;
+        float t_m = 0.f, t_c = 0.f;  // sum of rho - 1 and of C over the fluid nodes
+        int t_n = 0;                 // fluid nodes
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const unsigned lb = (lk >> (8 * k)) & 0xFFu;
@@ -170,11 +180,11 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
             for (int i = 0; i < 9; ++i) f[i] = at(v[i], k);
 #pragma unroll
             for (int i = 0; i < 5; ++i) g[i] = at(v[9 + i], k);
-            if (!fluid) {  // solid node: park it at the rest state
-                f[0] = kWr;
-                f[1] = f[2] = f[3] = f[4] = kWa;
-                f[5] = f[6] = f[7] = f[8] = kWd;
-                g[0] = g[1] = g[2] = g[3] = g[4] = 0.f;
+            if (!fluid) {  // solid node: park it at the rest state rho = 1, C = 0
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = 0.f;
+#pragma unroll
+                for (int i = 0; i < 5; ++i) g[i] = 0.f;
             }
 
             // ---- open valve ports (Zou-He; held concentration / do-nothing) ----
@@ -190,16 +200,15 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
                 const float fo_ax = pw ? f[3] : f[1];
                 const float fo_dn = pw ? f[7] : f[8];
                 const float fo_up = pw ? f[6] : f[5];
-                const float K = f[0] + f[2] + f[4] + 2.f * (fo_ax + fo_dn + fo_up);
-                float rho_b, ux_b;
+                // rho (1 - s u_x) = f0 + f2 + f4 + 2 (leaving) = 1 + Kd in deviations
+                // (the weights of those populations add up to one)
+                const float Kd = f[0] + f[2] + f[4] + 2.f * (fo_ax + fo_dn + fo_up);
+                float jx;  // rho u_x of the node
                 if (velocity) {
-                    ux_b = b.a;
-                    rho_b = K / (1.f - s * ux_b);
+                    jx = (1.f + Kd) * b.a / (1.f - s * b.a);
                 } else {
-                    rho_b = b.a;
-                    ux_b = s * (1.f - K / rho_b);
+                    jx = s * (b.a - Kd);  // b.a = prescribed rho - 1
                 }
-                const float jx = rho_b * ux_b;
                 const float ht = 0.5f * (f[2] - f[4]);
                 const float fi_ax = fo_ax + s * (2.f / 3.f) * jx;
                 const float fi_up = fo_dn - ht + s * (1.f / 6.f) * jx;  // e = (s, +1)
@@ -224,8 +233,10 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
                 }
             }
 
-            // ---- moments (Eq. moments) and BGK collision of f ----
-            const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            // ---- moments (Eq. moments) and BGK collision of f, in deviations
+            //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
+            const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            const float rho = 1.f + rd;
             const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
             const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
             const float inv = 1.f / rho;
@@ -233,24 +244,29 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
             const float usq = 1.5f * (ux * ux + uy * uy);
             const float wo = a.omega_f;
             {
-                const float r0 = kWr * rho, ra = kWa * rho, rd = kWd * rho;
-                f[0] += wo * (r0 * (1.f - usq) - f[0]);
+                // f_eq_i - w_i = w_i [rho - 1 + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]
                 const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
-                f[1] += wo * (ra * (1.f + 3.f * e1 + 4.5f * e1 * e1 - usq) - f[1]);
-                f[3] += wo * (ra * (1.f - 3.f * e1 + 4.5f * e1 * e1 - usq) - f[3]);
-                f[2] += wo * (ra * (1.f + 3.f * e2 + 4.5f * e2 * e2 - usq) - f[2]);
-                f[4] += wo * (ra * (1.f - 3.f * e2 + 4.5f * e2 * e2 - usq) - f[4]);
-                f[5] += wo * (rd * (1.f + 3.f * e5 + 4.5f * e5 * e5 - usq) - f[5]);
-                f[7] += wo * (rd * (1.f - 3.f * e5 + 4.5f * e5 * e5 - usq) - f[7]);
-                f[6] += wo * (rd * (1.f + 3.f * e6 + 4.5f * e6 * e6 - usq) - f[6]);
-                f[8] += wo * (rd * (1.f - 3.f * e6 + 4.5f * e6 * e6 - usq) - f[8]);
+                const float q1 = rho * (4.5f * e1 * e1 - usq), q2 = rho * (4.5f * e2 * e2 - usq);
+                const float q5 = rho * (4.5f * e5 * e5 - usq), q6 = rho * (4.5f * e6 * e6 - usq);
+                const float t1 = 3.f * jx, t2 = 3.f * jy, t5 = t1 + t2, t6 = t2 - t1;
+                f[0] += wo * (kWr * (rd - rho * usq) - f[0]);
+                f[1] += wo * (kWa * (rd + t1 + q1) - f[1]);
+                f[3] += wo * (kWa * (rd - t1 + q1) - f[3]);
+                f[2] += wo * (kWa * (rd + t2 + q2) - f[2]);
+                f[4] += wo * (kWa * (rd - t2 + q2) - f[4]);
+                f[5] += wo * (kWd * (rd + t5 + q5) - f[5]);
+                f[7] += wo * (kWd * (rd - t5 + q5) - f[7]);
+                f[6] += wo * (kWd * (rd + t6 + q6) - f[6]);
+                f[8] += wo * (kWd * (rd - t6 + q6) - f[8]);
             }
             // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
             const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
             {
                 const float wg = a.omega_g;
                 const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
-                g[0] += wg * (a.wg0 * C - g[0]);
+                // rest equilibrium w0 C formed as the remainder, so that the five
+                // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)
+                g[0] += wg * ((C - 4.f * c1) - g[0]);
                 g[1] += wg * ((c1 + cx) - g[1]);
                 g[3] += wg * ((c1 - cx) - g[3]);
                 g[2] += wg * ((c1 + cy) - g[2]);
@@ -264,8 +280,9 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
             if (fluid) {
                 bad |= !(rho > 0.f && rho < INFINITY) || !(fabsf(C) < INFINITY);
                 if (kDiag) {
-                    t_m += rho;
+                    t_m += rd;
                     t_c += C;
+                    ++t_n;
                     if (pressure_node) {
                         acc2 += double(rho) * double(ux);
                         acc3 += double(C) * double(ux);
@@ -274,7 +291,7 @@ __global__ void __launch_bounds__(256) coupled_step(const StepArgs a)
             }
         }
         if (kDiag) {
-            acc0 += double(t_m);
+            acc0 += double(t_n) + double(t_m);
             acc1 += double(t_c);
         }
         if (act) {
@@ -346,8 +363,8 @@ __global__ void init_rest(float* pop, long long plane, float rho0, float wg0, fl
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
         const int p = int(e / plane);
-        float w;
-        if (p < 9) w = (p == 0 ? kWr : p <= 4 ? kWa : kWd) * rho0;
+        float w;  // f is stored as f_i - w_i
+        if (p < 9) w = (p == 0 ? kWr : p <= 4 ? kWa : kWd) * (rho0 - 1.f);
         else w = (p == 9 ? wg0 : wg1) * C0;
         pop[e] = w;
     }
@@ -368,9 +385,9 @@ __global__ void init_fields(float* pop, const uint8_t* links, int nx, int ny, in
         const float usq = 1.5f * (ux * ux + uy * uy);
         const float e[9] = {0.f, ux, uy, -ux, -uy, ux + uy, uy - ux, -ux - uy, ux - uy};
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
+        for (int i = 0; i < 9; ++i) {  // f_eq_i - w_i
             const float w = i == 0 ? kWr : i <= 4 ? kWa : kWd;
-            pop[i * P + o] = w * rho * (1.f + 3.f * e[i] + 4.5f * e[i] * e[i] - usq);
+            pop[i * P + o] = w * ((rho - 1.f) + rho * (3.f * e[i] + 4.5f * e[i] * e[i] - usq));
         }
         pop[9 * P + o] = wg0 * C;
 #pragma unroll
@@ -391,7 +408,7 @@ __global__ void fields_kernel(const float* pop, const uint8_t* links, int nx, in
             float f[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) f[i] = pop[i * P + o];
-            r = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            r = 1.f + (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]);
             const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
             const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
             vx = jx / r;
