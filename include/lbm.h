@@ -53,7 +53,9 @@ typedef enum {
     LBM_ERR_NUMERIC = 4,  /* a fluid node had non-finite or non-positive density,
                              or non-finite concentration (sticky until
                              lbm_clear_error) */
-    LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+    LBM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up (about one second); the
+                             step's results are invalid (sticky until
+                             lbm_clear_error) */
     LBM_ERR_STATE = 6     /* call not valid in the handle's current state */
 } lbm_status;
 
@@ -103,8 +105,13 @@ typedef struct {
     lbm_alloc_fn alloc;     /* NULL = cudaMalloc */
     lbm_free_fn free;       /* NULL = cudaFree */
     void* alloc_user;
-    int32_t block_threads;  /* step kernel block size: 0 = default (256), else 64..256, a multiple of 32 */
+    int32_t block_threads;  /* register variant: block size, 0 = default (256), else 64..256, a multiple of 32 */
     int32_t max_blocks;     /* step kernel grid cap: 0 = one wave of resident blocks */
+    int32_t variant;        /* step kernel: 0 = default (2), 1 = registers and warp shuffles,
+                               2 = bulk-copy pipeline through shared memory */
+    int32_t pipeline_stages;/* variant 2: shared-memory stages per computing warp, 0 = default (1);
+                               computing warps x stages <= 24 */
+    int32_t consumer_warps; /* variant 2: computing warps per block, 0 = default (3), else 1..7 */
 } lbm_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -149,8 +156,8 @@ lbm_status lbm_set_valve_schedule(lbm_handle h, int64_t period, int32_t n,
 /* Advance n >= 0 coupled time steps, asynchronously on the handle's stream.
  * Each step is one launch of the fused kernel: pull-stream of f and g,
  * bounce-back, open-port completion, moments, collision of f, collision of
- * g with the same step's velocity.  The last step of the call also forms
- * the diagnostics (lbm_get_diagnostics).  Returns LBM_ERR_NUMERIC (after
+ * g with the same step's velocity, and per-block partial sums of the
+ * diagnostics (lbm_get_diagnostics adds them up).  Returns LBM_ERR_NUMERIC (after
  * issuing the steps) while a previous synchronising call has found the
  * numeric error flag set and lbm_clear_error has not reset it. */
 lbm_status lbm_step(lbm_handle h, int64_t n);
@@ -164,12 +171,14 @@ lbm_status lbm_get_fields(lbm_handle h, float* rho, float* ux, float* uy, float*
  * the handle's stream without synchronising; any may be NULL. */
 lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy, float* C);
 
-/* Diagnostics of the last step of the most recent lbm_step call (zeros
- * before the first step): out[0] = sum of rho over fluid nodes, out[1] =
- * sum of C over fluid nodes, out[2] = sum of rho u_x and out[3] = sum of
- * C u_x over the nodes of the PRESSURE ports open during that step.
- * Accumulated in FP64 in a fixed order (run-to-run identical).  Synchronises
- * the stream; returns LBM_ERR_NUMERIC if a bad value was flagged. */
+/* Diagnostics of the most recent time step (zeros before the first step):
+ * out[0] = sum of rho over fluid nodes, out[1] = sum of C over fluid nodes,
+ * out[2] = sum of rho u_x and out[3] = sum of C u_x over the nodes of the
+ * PRESSURE ports open during that step.  Each lane of the step kernel sums
+ * its nodes in compensated FP32; lanes and blocks are combined in FP64 in a
+ * fixed order (run-to-run identical for a given launch shape).  Launches a
+ * small reduction kernel and synchronises the stream; returns
+ * LBM_ERR_NUMERIC / LBM_ERR_TIMEOUT if the error word is set. */
 lbm_status lbm_get_diagnostics(lbm_handle h, double out[4]);
 
 /* Current post-collision populations into HOST arrays: f = 9*nx*ny floats,
@@ -198,7 +207,7 @@ lbm_status lbm_get_step(lbm_handle h, int64_t* t);
 /* Block until the handle's stream is idle; reports launch errors. */
 lbm_status lbm_synchronize(lbm_handle h);
 
-/* Reset a sticky LBM_ERR_NUMERIC flag. */
+/* Reset a sticky LBM_ERR_NUMERIC or LBM_ERR_TIMEOUT flag. */
 lbm_status lbm_clear_error(lbm_handle h);
 
 typedef struct {
@@ -206,6 +215,8 @@ typedef struct {
     int32_t pitch;          /* floats per stored row (multiple of 128) */
     int32_t n_tiles;        /* 128-node row segments that hold fluid */
     int32_t grid, block;    /* step kernel launch shape */
+    int32_t variant;        /* 1 registers, 2 bulk-copy pipeline */
+    int32_t stages;         /* shared-memory stages per block (variant 2), 0 otherwise */
     int64_t fluid_nodes;
     int64_t algorithmic_bytes_per_step;  /* fluid_nodes * 112: 14 FP32 populations read and written */
     int64_t device_bytes;   /* device memory held by the handle */

@@ -24,6 +24,10 @@ thread_local std::string g_create_error = "no error";
 constexpr uint32_t kStateMagic = 0x4C424D31u;  // "LBM1"
 constexpr int kMaxPorts = 64;
 constexpr int kMaxSchedule = 4096;
+// Bulk-copy pipeline shape measured fastest on GB300 for the 4096 x 2048 chip:
+// three computing warps with one stage each, four blocks per SM.
+constexpr int kDefaultConsumers = 3;
+constexpr int kDefaultStagesPerConsumer = 1;
 
 struct Alloc {
     void* ptr = nullptr;
@@ -48,15 +52,14 @@ struct lbm_ctx {
     int cur = 0;  // buffer holding the current state
     uint8_t* links = nullptr;
     lbm::RowBC* rowbc = nullptr;
-    uint32_t* tiles = nullptr;
+    uint2* tiles = nullptr;
     double* partials = nullptr;
-    unsigned int* ticket = nullptr;
-    double* diag = nullptr;
+    double* diag = nullptr;       // 4 totals formed by lbm_get_diagnostics
     unsigned int* err = nullptr;
     float* fields_tmp = nullptr;  // 4 * nx * ny floats
 
     int n_tiles = 0;
-    int grid = 0, block = 256, grid_cap = 0;
+    lbm::StepLaunch launch{lbm::kVariantBulk, 0, 0, 0};
     long long fluid = 0;
     long long device_bytes = 0;
 
@@ -64,7 +67,8 @@ struct lbm_ctx {
     uint32_t fixed_mask = 0;
     int64_t period = 0;
     std::vector<uint32_t> schedule;
-    bool numeric = false;  // the device error word was found set
+    bool numeric = false;  // the device error word was found set (bit 0)
+    bool timeout = false;  // a bounded device wait gave up (bit 1)
 
     std::string last_error = "no error";
 
@@ -145,7 +149,7 @@ lbm_status check_ctx(lbm_ctx* h)
 
 lbm_status pending_numeric(lbm_ctx* h)
 {
-    return h->numeric ? LBM_ERR_NUMERIC : LBM_OK;
+    return h->timeout ? LBM_ERR_TIMEOUT : h->numeric ? LBM_ERR_NUMERIC : LBM_OK;
 }
 
 }  // namespace
@@ -214,6 +218,18 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
         return fail(nullptr, LBM_ERR_ARG, "block_threads = %d: use 0 or a multiple of 32 in [64, 256]",
                     opt.block_threads);
     if (opt.max_blocks < 0) return fail(nullptr, LBM_ERR_ARG, "max_blocks = %d < 0", opt.max_blocks);
+    if (opt.variant < 0 || opt.variant > 2)
+        return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1 or 2", opt.variant);
+    if (opt.consumer_warps < 0 || opt.consumer_warps > 7)
+        return fail(nullptr, LBM_ERR_ARG, "consumer_warps = %d: use 0 or 1..7", opt.consumer_warps);
+    {
+        const int nc = opt.consumer_warps ? opt.consumer_warps : kDefaultConsumers;
+        const int per = opt.pipeline_stages ? opt.pipeline_stages : kDefaultStagesPerConsumer;
+        if (opt.pipeline_stages < 0 || nc * per > lbm::kMaxStages)
+            return fail(nullptr, LBM_ERR_ARG,
+                        "pipeline_stages = %d per consumer warp with %d consumer warps: the ring holds at most %d stages",
+                        opt.pipeline_stages, nc, lbm::kMaxStages);
+    }
     if ((opt.alloc == nullptr) != (opt.free == nullptr))
         return fail(nullptr, LBM_ERR_ARG, "alloc and free hooks must be given together");
     if (n_ports < 0 || n_ports > kMaxPorts)
@@ -275,7 +291,7 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     const int pitch = (nx + lbm::kTileNodes - 1) / lbm::kTileNodes * lbm::kTileNodes;
     const int segs = pitch / lbm::kTileNodes;
     std::vector<uint8_t> links(size_t(pitch) * ny, lbm::kSolid);
-    std::vector<uint32_t> tiles;
+    std::vector<uint2> tiles;
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
             if (!is_fluid(mask, nx, ny, x, y)) continue;
@@ -287,10 +303,16 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
             links[size_t(y) * pitch + x] = lb;
         }
         for (int s = 0; s < segs; ++s) {
-            bool any = false;
-            for (int x = s * lbm::kTileNodes; x < std::min(nx, (s + 1) * lbm::kTileNodes) && !any; ++x)
-                any = mask[size_t(y) * nx + x] == 0;
-            if (any) tiles.push_back((uint32_t(y) << lbm::kSegBits) | uint32_t(s));
+            int q0 = -1, q1 = -1;  // first and last quad of the segment holding fluid
+            for (int x = s * lbm::kTileNodes; x < std::min(nx, (s + 1) * lbm::kTileNodes); ++x)
+                if (mask[size_t(y) * nx + x] == 0) {
+                    const int q = (x - s * lbm::kTileNodes) / 4;
+                    if (q0 < 0) q0 = q;
+                    q1 = q;
+                }
+            if (q0 >= 0)
+                tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s),
+                                           uint32_t(q0) | (uint32_t(q1) << 8)));
         }
     }
 
@@ -316,8 +338,6 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     h->alloc_user = opt.alloc_user;
     h->n_tiles = int(tiles.size());
     h->fluid = fluid;
-    h->block = opt.block_threads ? opt.block_threads : 256;
-    h->grid_cap = opt.max_blocks;
 
     auto bail = [&](lbm_status s) {
         g_create_error = h->last_error;
@@ -335,33 +355,40 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
-    e = lbm::step_kernel_occupancy(h->block, true, &per_sm);
-    if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
-    {
-        int per_sm_nodiag = 0;
-        e = lbm::step_kernel_occupancy(h->block, false, &per_sm_nodiag);
-        if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
-        per_sm = std::max(1, std::min(per_sm, per_sm_nodiag));
+    lbm::StepLaunch& L = h->launch;
+    L.variant = opt.variant == 1 ? lbm::kVariantRegs : lbm::kVariantBulk;
+    if (L.variant == lbm::kVariantBulk) {
+        const int nc = opt.consumer_warps ? opt.consumer_warps : kDefaultConsumers;
+        L.stages = nc * (opt.pipeline_stages ? opt.pipeline_stages : kDefaultStagesPerConsumer);
+        L.block = 32 * (nc + 1);
+        e = lbm::prepare_step_kernels();
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "shared-memory attribute"));
+    } else {
+        L.stages = 0;
+        L.block = opt.block_threads ? opt.block_threads : 256;
     }
-    const int wpb = h->block / 32;
-    const int need = (h->n_tiles + wpb - 1) / wpb;
-    h->grid = std::max(1, std::min(need, per_sm * sms));
-    if (h->grid_cap > 0) h->grid = std::min(h->grid, h->grid_cap);
+    e = lbm::step_kernel_occupancy(L, &per_sm);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
+    if (per_sm < 1) return bail(fail(h, LBM_ERR_ARG, "the step kernel cannot run with this launch shape"));
+    // one wave of resident blocks, which then stride over the tile table
+    const int tiles_per_block = L.variant == lbm::kVariantBulk ? 1 : L.block / 32;
+    const int need = (h->n_tiles + tiles_per_block - 1) / tiles_per_block;
+    L.grid = std::max(1, std::min(need, per_sm * sms));
+    if (opt.max_blocks > 0) L.grid = std::min(L.grid, opt.max_blocks);
 
     const size_t pop_bytes = size_t(h->plane) * lbm::kPlanes * sizeof(float);
     h->pop[0] = static_cast<float*>(dev_alloc(h, pop_bytes));
     h->pop[1] = static_cast<float*>(dev_alloc(h, pop_bytes));
     h->links = static_cast<uint8_t*>(dev_alloc(h, links.size()));
     h->rowbc = static_cast<lbm::RowBC*>(dev_alloc(h, rowbc.size() * sizeof(lbm::RowBC)));
-    h->tiles = static_cast<uint32_t*>(dev_alloc(h, std::max<size_t>(1, tiles.size()) * 4));
-    h->partials = static_cast<double*>(dev_alloc(h, size_t(h->grid) * 4 * sizeof(double)));
-    h->ticket = static_cast<unsigned*>(dev_alloc(h, 2 * sizeof(unsigned)));
+    h->tiles = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, tiles.size()) * sizeof(uint2)));
+    h->partials = static_cast<double*>(dev_alloc(h, size_t(h->launch.grid) * 4 * sizeof(double)));
+    h->err = static_cast<unsigned*>(dev_alloc(h, sizeof(unsigned)));
     h->diag = static_cast<double*>(dev_alloc(h, 4 * sizeof(double)));
     h->fields_tmp = static_cast<float*>(dev_alloc(h, size_t(4) * nx * ny * sizeof(float)));
     if (!h->pop[0] || !h->pop[1] || !h->links || !h->rowbc || !h->tiles || !h->partials ||
-        !h->ticket || !h->diag || !h->fields_tmp)
+        !h->err || !h->diag || !h->fields_tmp)
         return bail(fail(h, LBM_ERR_OOM, "device allocation of %zu bytes failed", 2 * pop_bytes));
-    h->err = h->ticket + 1;
 
     cudaStream_t st = h->stream;
     e = cudaMemcpyAsync(h->links, links.data(), links.size(), cudaMemcpyHostToDevice, st);
@@ -369,9 +396,10 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
         e = cudaMemcpyAsync(h->rowbc, rowbc.data(), rowbc.size() * sizeof(lbm::RowBC),
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !tiles.empty())
-        e = cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, 2 * sizeof(unsigned), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->diag, 0, 4 * sizeof(double), st);
+        e = cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->partials, 0, size_t(h->launch.grid) * 4 * sizeof(double), st);
     if (e == cudaSuccess)
         e = lbm::launch_init_rest(h->pop[0], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0), st);
     if (e == cudaSuccess)
@@ -435,14 +463,12 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
     a.partials = h->partials;
-    a.ticket = h->ticket;
-    a.diag = h->diag;
     a.err = h->err;
     for (int64_t k = 0; k < n; ++k) {
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
         a.open_mask = h->mask_at(h->step);
-        cudaError_t e = lbm::launch_step(a, h->grid, h->block, k == n - 1, h->stream);
+        cudaError_t e = lbm::launch_step(a, h->launch, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
         ++h->step;
@@ -463,8 +489,12 @@ static lbm_status read_err_word(lbm_handle h)
     unsigned err = 0;
     LBM_CUDA(h, cudaMemcpyAsync(&err, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (err) h->numeric = true;
-    if (err) return fail(h, LBM_ERR_NUMERIC, "numeric: a fluid node reached a non-finite or non-positive density or a non-finite concentration");
+    if (err & 2u) h->timeout = true;
+    if (err & 1u) h->numeric = true;
+    if (err & 2u)
+        return fail(h, LBM_ERR_TIMEOUT, "timeout: a bounded wait of the step kernel gave up; results are invalid");
+    if (err & 1u)
+        return fail(h, LBM_ERR_NUMERIC, "numeric: a fluid node reached a non-finite or non-positive density or a non-finite concentration");
     return pending_numeric(h);
 }
 
@@ -474,6 +504,7 @@ lbm_status lbm_clear_error(lbm_handle h)
     LBM_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->numeric = false;
+    h->timeout = false;
     h->last_error = "no error";
     return LBM_OK;
 }
@@ -505,6 +536,8 @@ lbm_status lbm_get_fields(lbm_handle h, float* rho, float* ux, float* uy, float*
 lbm_status lbm_get_diagnostics(lbm_handle h, double out[4])
 {
     if (check_ctx(h) || !out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    cudaError_t e = lbm::launch_diag_finish(h->partials, h->launch.grid, h->diag, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics reduction launch");
     LBM_CUDA(h, cudaMemcpyAsync(out, h->diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return read_err_word(h);
 }
@@ -669,8 +702,10 @@ lbm_status lbm_get_info(lbm_handle h, lbm_info* info)
     info->ny = h->ny;
     info->pitch = h->pitch;
     info->n_tiles = h->n_tiles;
-    info->grid = h->grid;
-    info->block = h->block;
+    info->grid = h->launch.grid;
+    info->block = h->launch.block;
+    info->variant = h->launch.variant;
+    info->stages = h->launch.stages;
     info->fluid_nodes = h->fluid;
     info->algorithmic_bytes_per_step = h->fluid * 112;
     info->device_bytes = h->device_bytes;

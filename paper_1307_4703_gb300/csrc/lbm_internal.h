@@ -16,8 +16,9 @@
 //                grid, or outside a port).  0xFF marks a solid node.
 //   rowbc        2*ny entries (west side then east side): the port node of
 //                that side and row, if any.
-//   tiles        list of the 128-node row segments that hold fluid,
-//                (y << 12) | segment.
+//   tiles        list of the 128-node row segments that hold fluid:
+//                x = (y << 12) | segment, y = first | (last << 8), the first
+//                and last lane (4-node quad) of the segment holding fluid.
 #pragma once
 
 #include <cstdint>
@@ -30,6 +31,18 @@ constexpr int kTileNodes = 128;  // nodes per warp tile: 32 lanes x 4 nodes
 constexpr int kPlanes = 14;      // f_0..f_8, g_0..g_4
 constexpr int kSegBits = 12;     // tile encoding: segment in the low 12 bits
 constexpr uint8_t kSolid = 0xFF;
+constexpr int kRowFloats = kTileNodes + 8;  // staged plane row: 4-float halo on each side
+constexpr int kBulkMaxThreads = 256;        // bulk variant: at most 7 consumer warps + 1 producer
+constexpr int kMaxStages = 24;              // bulk variant: largest shared-memory ring
+
+enum StepVariant { kVariantRegs = 1, kVariantBulk = 2 };
+
+struct StepLaunch {
+    int variant;  // kVariantRegs or kVariantBulk
+    int grid;
+    int block;
+    int stages;   // bulk variant: shared-memory stages per block (consumer warps x stages per warp)
+};
 
 struct RowBC {
     int32_t x;          // port node column, -1 = no port on this side and row
@@ -43,7 +56,7 @@ struct StepArgs {
     float* dst;             // post-collision populations at time t + 1
     const uint8_t* links;
     const RowBC* rowbc;
-    const uint32_t* tiles;
+    const uint2* tiles;
     int n_tiles;
     int ny;
     int pitch;
@@ -54,15 +67,18 @@ struct StepArgs {
     float wg1;              // scalar axis weight (1 - wg0) / 4
     float inv_cs2g;         // 1 / c_s^2 of the scalar lattice
     uint32_t open_mask;     // valve word of this step
-    // diagnostics (only read by the diagnostics variant)
-    double* partials;       // 4 per block
-    unsigned int* ticket;   // zero between launches
-    double* diag;           // 4 results
-    unsigned int* err;      // sticky numeric error word
+    double* partials;       // 4 diagnostics partial sums per block (scratch)
+    unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
 };
 
-cudaError_t launch_step(const StepArgs& a, int grid, int block, bool diag, cudaStream_t s);
-cudaError_t step_kernel_occupancy(int block, bool diag, int* blocks_per_sm);
+// Dynamic shared memory of the bulk variant, and the attribute it needs.
+size_t bulk_smem_bytes(int stages);
+int bulk_stage_bytes();
+cudaError_t prepare_step_kernels();
+cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s);
+// out[0..3] = sum of the n_blocks x 4 block partials, in a fixed order.
+cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s);
+cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm);
 
 // Every node (fluid and solid, padding included) to the rest equilibrium
 // of rho0 and C0.

@@ -45,13 +45,14 @@ class lbm_options(ctypes.Structure):
                 ("w0", ctypes.c_double), ("rho0", ctypes.c_double), ("C0", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("block_threads", ctypes.c_int32),
-                ("max_blocks", ctypes.c_int32)]
+                ("max_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("pipeline_stages", ctypes.c_int32), ("consumer_warps", ctypes.c_int32)]
 
 
 class lbm_info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("pitch", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("fluid_nodes", ctypes.c_int64), ("algorithmic_bytes_per_step", ctypes.c_int64),
+                ("variant", ctypes.c_int32), ("stages", ctypes.c_int32), ("fluid_nodes", ctypes.c_int64), ("algorithmic_bytes_per_step", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64)]
 
 
@@ -146,7 +147,7 @@ class Chip:
 
     def __init__(self, solid, tau, tau_c, ports=(), edge_u=None, edge_C=None, w0=1.0 / 3.0,
                  rho0=1.0, C0=0.0, stream=None, torch_alloc=False, device=-1, block_threads=0,
-                 max_blocks=0):
+                 max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0):
         self._lib = load()
         solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
         self.ny, self.nx = solid.shape
@@ -163,6 +164,9 @@ class Chip:
         opt.w0, opt.rho0, opt.C0 = float(w0), float(rho0), float(C0)
         opt.block_threads = int(block_threads)
         opt.max_blocks = int(max_blocks)
+        opt.variant = int(variant)
+        opt.pipeline_stages = int(pipeline_stages)
+        opt.consumer_warps = int(consumer_warps)
         self.stream = stream
         if stream is not None:
             opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
