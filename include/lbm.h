@@ -224,6 +224,82 @@ typedef struct {
 
 lbm_status lbm_get_info(lbm_handle h, lbm_info* info);
 
+/* ---- One step on caller-owned buffers, allocating nothing ----
+ *
+ * The paper has no counterpart to this call.  It serves callers that cannot
+ * allocate device memory themselves through the library: code that runs
+ * inside another framework's memory pool or arena, or under a rule that no
+ * component may call cudaMalloc once start-up is over, and so cannot use
+ * lbm_create.  Such a caller owns every buffer below and passes device
+ * pointers to them; this call runs one coupled time step (the same kernel
+ * and arithmetic as lbm_step) and calls no cudaMalloc, cudaFree or other
+ * allocating routine, on the device or on the host.
+ *
+ * The step kernel's only scratch memory, its per-block partial sums of the
+ * diagnostics, lives in a fixed array inside the library of
+ * LBM_NOALLOC_MAX_BLOCKS x 4 doubles (64 KiB), which every GPU that loads the
+ * library holds until the process exits.  The first call on a device sets
+ * that device up (looks up the array's device address and the launch
+ * shape); make that first call before capturing the stream into a CUDA
+ * graph.  All calls share the one array: calls whose kernels overlap on the
+ * GPU (different streams, no ordering between them) race on it and get
+ * wrong diagnostics.  Every entry the diagnostics read is written earlier in
+ * the same call, so nothing needs clearing between calls.
+ *
+ * Buffer formats (all device memory, owned by the caller):
+ *   src, dst  14 planes of ny rows of `pitch` floats (pitch a multiple of
+ *             128, >= nx; 16-byte aligned): planes 0..8 hold f_i - w_i with
+ *             w = 4/9, 1/9 (i = 1..4), 1/36 (i = 5..8); planes 9..13 hold
+ *             g_0..g_4.  Post-collision values; src holds time t and dst
+ *             receives time t + 1.  The two must not overlap.
+ *   links     ny rows of `pitch` bytes: for a fluid node, bit (i - 1) is set
+ *             when the pull source x - e_i of direction i = 1..8 is not a
+ *             fluid node (solid, outside the grid, or beyond a port); 0xFF
+ *             marks a solid node and every padding column x >= nx.
+ *   ports     2 * ny lbm_row_port entries, west side then east side.
+ *   tiles     n_tiles lbm_tile entries: every 128-node row segment that
+ *             holds fluid, exactly once.
+ * Malformed tables or buffers that are too small are not detected and lead
+ * to out-of-bounds device accesses. */
+#define LBM_NOALLOC_MAX_BLOCKS 2048
+
+typedef struct {
+    int32_t x;             /* port node column of this side and row, -1 = none */
+    int32_t channel_kind;  /* valve channel | (LBM_PORT_VELOCITY or LBM_PORT_PRESSURE) << 8 */
+    float a;               /* velocity port: u_x; pressure port: rho - 1 */
+    float c;               /* velocity port: held concentration */
+} lbm_row_port;
+
+typedef struct {
+    uint32_t row_segment;  /* (y << 12) | s: nodes [128 s, 128 s + 128) of row y */
+    uint32_t quads;        /* q0 | (q1 << 8): first and last 4-node group holding fluid */
+} lbm_tile;
+
+typedef struct {
+    uint32_t struct_size;  /* sizeof(lbm_noalloc_step) */
+    int32_t nx, ny, pitch;
+    const float* src;
+    float* dst;
+    const uint8_t* links;
+    const lbm_row_port* ports;
+    const lbm_tile* tiles;
+    int32_t n_tiles;
+    int32_t max_blocks;    /* 0 = one wave of resident blocks; at most LBM_NOALLOC_MAX_BLOCKS */
+    double tau, tau_c, w0; /* as for lbm_create and lbm_options.w0 */
+    uint32_t open_mask;    /* valve word of this step */
+    double* diag;          /* device, 4 doubles: the step's diagnostics as lbm_get_diagnostics; NULL = skip */
+    uint32_t* err;         /* device word the kernel ORs its flags into: bit 0 numeric, bit 1 timeout */
+    void* stream;          /* cudaStream_t; NULL = legacy default stream */
+    char* message;         /* optional caller buffer for a one-line error reason */
+    int32_t message_len;
+} lbm_noalloc_step;
+
+/* Run one coupled time step on the buffers described by *s, on the current
+ * CUDA device, asynchronously on s->stream.  Errors: LBM_ERR_ARG (invalid
+ * descriptor, max_blocks above LBM_NOALLOC_MAX_BLOCKS; nothing launched),
+ * LBM_ERR_CUDA. */
+lbm_status lbm_step_noalloc(const lbm_noalloc_step* s);
+
 /* Last error message of the handle, or of the calling thread's most recent
  * lbm_create when h is NULL.  Never NULL. */
 const char* lbm_last_error(lbm_handle h);

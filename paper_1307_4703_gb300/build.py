@@ -1,7 +1,7 @@
 """Build the sm_103a CUDA library ``_lib/liblbm_gb300.so`` in-tree.
 
-Two translation units (the kernels and the host ABI) are compiled in
-parallel with nvcc for ``sm_103a`` only and linked into one shared library
+The translation units (kernels, host ABI, the allocation-free entry point)
+are compiled in parallel with nvcc for ``sm_103a`` only and linked into one shared library
 with the CUDA runtime linked statically, so the library needs nothing but
 the NVIDIA driver at run time.
 """
@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
-SOURCES = ["lbm_kernels.cu", "lbm_api.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -56,6 +56,25 @@ class lbm_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class lbm_row_port(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int32), ("channel_kind", ctypes.c_int32), ("a", ctypes.c_float),
+                ("c", ctypes.c_float)]
+
+
+class lbm_tile(ctypes.Structure):
+    _fields_ = [("row_segment", ctypes.c_uint32), ("quads", ctypes.c_uint32)]
+
+
+class lbm_noalloc_step(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("pitch", ctypes.c_int32), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("links", ctypes.c_void_p), ("ports", ctypes.c_void_p), ("tiles", ctypes.c_void_p),
+                ("n_tiles", ctypes.c_int32), ("max_blocks", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("tau_c", ctypes.c_double), ("w0", ctypes.c_double), ("open_mask", ctypes.c_uint32),
+                ("diag", ctypes.c_void_p), ("err", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("message", ctypes.c_char_p), ("message_len", ctypes.c_int32)]
+
+
 _lib = None
 _P = ctypes.POINTER
 _f32p = _P(ctypes.c_float)
@@ -86,6 +105,7 @@ SIGNATURES = {
     "lbm_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
     "lbm_clear_error": (ctypes.c_int, [ctypes.c_void_p]),
     "lbm_get_info": (ctypes.c_int, [ctypes.c_void_p, _P(lbm_info)]),
+    "lbm_step_noalloc": (ctypes.c_int, [_P(lbm_noalloc_step)]),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
