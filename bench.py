@@ -45,6 +45,8 @@ def _args():
     p.add_argument("--skip-extras", action="store_true",
                    help="skip the end-to-end and CPU-baseline legs (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
+                   help="step kernel: 0 library default, 1 registers, 2 bulk-copy pipeline")
     return p.parse_args()
 
 
@@ -225,6 +227,25 @@ def _e2e(prob, steps, device):
             "steps": steps, "seconds": dt}
 
 
+def reduce_max(value, world_size):
+    """Largest value over the ranks (the slowest rank's time); the value
+    itself on a single process.  Works on the NCCL and on the gloo backend."""
+    if world_size <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_glups(per_rank_units, seconds, world_size):
+    """Whole-job throughput: the units every rank processed over the time
+    of the slowest rank (weak scaling: each rank advances its own chip)."""
+    return world_size * per_rank_units / reduce_max(seconds, world_size) / 1e9
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -242,7 +263,7 @@ def main():
     prob = _problem(args.workload)
     fluid = W.fluid_count(prob)
     stream = torch.cuda.Stream()
-    chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=local)
+    chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=local, variant=args.variant)
     chip.set_valve_schedule(prob["period"], prob["states"])
     info = chip.info()
 
@@ -270,22 +291,16 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     d = chip.diagnostics()  # raises on a numeric error flag
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    value = aggregate_glups(fluid * args.steps, ms / 1e3, ws)
+    ms = reduce_max(ms, ws)
     ms_per_step = ms / max(args.steps, 1)
-    value = ws * fluid * args.steps / (ms / 1e3) / 1e9
     peak, peak_src = _peak()
     achieved = fluid * BYTES_PER_NODE / (ms_per_step / 1e3) / 1e9
     extras = {}
     if not args.skip_extras:
         e2e_steps = min(args.steps, 5000)
         e = _e2e(prob, e2e_steps, local)
-        if ws > 1:
-            t = torch.tensor([e["seconds"]], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e["value"] = ws * fluid * e2e_steps / float(t.item()) / 1e9
+        e["value"] = aggregate_glups(fluid * e2e_steps, e["seconds"], ws)
         extras["e2e"] = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
         if ws == 1 and rank == 0:
             extras["cpu_baseline"] = _cpu_baseline(args.cpu_seconds)
@@ -301,7 +316,9 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB of populations per copy)"
                              % (info["pitch"] * prob["ny"] * 14 * 4 / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "launch": {"grid": info["grid"], "block": info["block"], "tiles": info["n_tiles"]}},
+                       "launch": {"variant": {1: "registers", 2: "bulk-copy pipeline"}[info["variant"]],
+                                  "grid": info["grid"], "block": info["block"],
+                                  "stages": info["stages"], "tiles": info["n_tiles"]}},
             "all_node_glups": ws * prob["nx"] * prob["ny"] * args.steps / (ms / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": _traffic(fluid),

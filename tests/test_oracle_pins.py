@@ -285,6 +285,22 @@ def test_do_nothing_outlet_lets_scalar_leave_with_the_flow():
     assert C.max() < 1.0 + 1e-9
 
 
+def test_outlet_fluxes_balance_inlet_in_steady_flow():
+    """Mass and scalar conservation: in a steady channel the outlet
+    diagnostics (sum of rho u_x and of C u_x over the open pressure-port
+    nodes) carry what the inlet nodes inject, within 0.1% (mass) and 1%
+    (scalar, whose inlet also has a small diffusive part); the totals are
+    the plain sums of the fields."""
+    L = _channel(48, 8, 0.8, 0.8, W.parabolic_profile(8, 0.01), C_in=1.0)
+    L.step(1, 20000)
+    d = L.diagnostics(1)
+    rho, ux, _, C = L.fields()
+    assert abs(d[2] / (rho[:, 0] * ux[:, 0]).sum() - 1) < 1e-3
+    assert abs(d[3] / (C[:, 0] * ux[:, 0]).sum() - 1) < 1e-2
+    assert abs(d[0] - rho.sum()) < 1e-9 and abs(d[1] - C.sum()) < 1e-9
+    assert L.diagnostics(0)[2] == 0.0
+
+
 def test_closed_valve_is_a_wall():
     """Closing both valves of a channel stops the through-flow: the velocity
     decays by more than a thousandfold (what is left is a slowly damped
