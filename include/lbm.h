@@ -108,10 +108,12 @@ typedef struct {
     int32_t block_threads;  /* register variant: block size, 0 = default (256), else 64..256, a multiple of 32 */
     int32_t max_blocks;     /* step kernel grid cap: 0 = one wave of resident blocks */
     int32_t variant;        /* step kernel: 0 = default (2), 1 = registers and warp shuffles,
-                               2 = bulk-copy pipeline through shared memory */
-    int32_t pipeline_stages;/* variant 2: shared-memory stages per computing warp, 0 = default (1);
+                               2 = bulk-copy pipeline through shared memory with a producer warp,
+                               3 = bulk-copy pipeline in which every warp refills its own stages */
+    int32_t pipeline_stages;/* variants 2, 3: shared-memory stages per computing warp, 0 = default (1);
                                computing warps x stages <= 24 */
-    int32_t consumer_warps; /* variant 2: computing warps per block, 0 = default (3), else 1..7 */
+    int32_t consumer_warps; /* variants 2, 3: computing warps per block, 0 = default (2: 3, 3: 4),
+                               else 1..7 (variant 2) or 1..8 (variant 3) */
 } lbm_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -215,8 +217,8 @@ typedef struct {
     int32_t pitch;          /* floats per stored row (multiple of 128) */
     int32_t n_tiles;        /* 128-node row segments that hold fluid */
     int32_t grid, block;    /* step kernel launch shape */
-    int32_t variant;        /* 1 registers, 2 bulk-copy pipeline */
-    int32_t stages;         /* shared-memory stages per block (variant 2), 0 otherwise */
+    int32_t variant;        /* 1 registers, 2 bulk-copy pipeline with producer warp, 3 self-refilling warps */
+    int32_t stages;         /* shared-memory stages per block (variants 2, 3), 0 otherwise */
     int64_t fluid_nodes;
     int64_t algorithmic_bytes_per_step;  /* fluid_nodes * 112: 14 FP32 populations read and written */
     int64_t device_bytes;   /* device memory held by the handle */

@@ -28,6 +28,7 @@ constexpr int kMaxSchedule = 4096;
 // three computing warps with one stage each, four blocks per SM.
 constexpr int kDefaultConsumers = 3;
 constexpr int kDefaultStagesPerConsumer = 1;
+constexpr int kDefaultPipeWarps = 4;
 
 struct Alloc {
     void* ptr = nullptr;
@@ -218,12 +219,14 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
         return fail(nullptr, LBM_ERR_ARG, "block_threads = %d: use 0 or a multiple of 32 in [64, 256]",
                     opt.block_threads);
     if (opt.max_blocks < 0) return fail(nullptr, LBM_ERR_ARG, "max_blocks = %d < 0", opt.max_blocks);
-    if (opt.variant < 0 || opt.variant > 2)
-        return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1 or 2", opt.variant);
-    if (opt.consumer_warps < 0 || opt.consumer_warps > 7)
-        return fail(nullptr, LBM_ERR_ARG, "consumer_warps = %d: use 0 or 1..7", opt.consumer_warps);
+    if (opt.variant < 0 || opt.variant > 3)
+        return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1, 2 or 3", opt.variant);
+    const int max_cw = opt.variant == 3 ? 8 : 7;
+    if (opt.consumer_warps < 0 || opt.consumer_warps > max_cw)
+        return fail(nullptr, LBM_ERR_ARG, "consumer_warps = %d: use 0 or 1..%d", opt.consumer_warps, max_cw);
     {
-        const int nc = opt.consumer_warps ? opt.consumer_warps : kDefaultConsumers;
+        const int nc = opt.consumer_warps ? opt.consumer_warps
+                                          : opt.variant == 3 ? kDefaultPipeWarps : kDefaultConsumers;
         const int per = opt.pipeline_stages ? opt.pipeline_stages : kDefaultStagesPerConsumer;
         if (opt.pipeline_stages < 0 || nc * per > lbm::kMaxStages)
             return fail(nullptr, LBM_ERR_ARG,
@@ -356,11 +359,17 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
     lbm::StepLaunch& L = h->launch;
-    L.variant = opt.variant == 1 ? lbm::kVariantRegs : lbm::kVariantBulk;
+    L.variant = opt.variant == 1 ? lbm::kVariantRegs : opt.variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
     if (L.variant == lbm::kVariantBulk) {
         const int nc = opt.consumer_warps ? opt.consumer_warps : kDefaultConsumers;
         L.stages = nc * (opt.pipeline_stages ? opt.pipeline_stages : kDefaultStagesPerConsumer);
         L.block = 32 * (nc + 1);
+        e = lbm::prepare_step_kernels();
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "shared-memory attribute"));
+    } else if (L.variant == lbm::kVariantPipe) {
+        const int nw = opt.consumer_warps ? opt.consumer_warps : kDefaultPipeWarps;
+        L.stages = nw * (opt.pipeline_stages ? opt.pipeline_stages : kDefaultStagesPerConsumer);
+        L.block = 32 * nw;
         e = lbm::prepare_step_kernels();
         if (e != cudaSuccess) return bail(cuda_fail(h, e, "shared-memory attribute"));
     } else {
@@ -371,7 +380,7 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
     if (per_sm < 1) return bail(fail(h, LBM_ERR_ARG, "the step kernel cannot run with this launch shape"));
     // one wave of resident blocks, which then stride over the tile table
-    const int tiles_per_block = L.variant == lbm::kVariantBulk ? 1 : L.block / 32;
+    const int tiles_per_block = L.variant == lbm::kVariantBulk ? 1 : L.block / 32;  // tiles in flight at once
     const int need = (h->n_tiles + tiles_per_block - 1) / tiles_per_block;
     L.grid = std::max(1, std::min(need, per_sm * sms));
     if (opt.max_blocks > 0) L.grid = std::min(L.grid, opt.max_blocks);

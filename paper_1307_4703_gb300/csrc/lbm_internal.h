@@ -35,13 +35,13 @@ constexpr int kRowFloats = kTileNodes + 8;  // staged plane row: 4-float halo on
 constexpr int kBulkMaxThreads = 256;        // bulk variant: at most 7 consumer warps + 1 producer
 constexpr int kMaxStages = 24;              // bulk variant: largest shared-memory ring
 
-enum StepVariant { kVariantRegs = 1, kVariantBulk = 2 };
+enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3 };
 
 struct StepLaunch {
-    int variant;  // kVariantRegs or kVariantBulk
+    int variant;  // kVariantRegs, kVariantBulk or kVariantPipe
     int grid;
     int block;
-    int stages;   // bulk variant: shared-memory stages per block (consumer warps x stages per warp)
+    int stages;   // shared-memory stages per block (computing warps x stages per warp)
 };
 
 struct RowBC {

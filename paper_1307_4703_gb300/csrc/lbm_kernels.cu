@@ -625,6 +625,138 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
 }
 
 // ---------------------------------------------------------------------------
+// Variant 3: every warp streams its own tiles
+// ---------------------------------------------------------------------------
+// Proxy fence: the warp's generic reads of a stage are ordered before the
+// asynchronous (bulk-copy) writes that refill it.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Refill `sg` with `tile`: lane 0 arms the barrier with the byte count, then
+// lanes 0..16 each issue one bulk copy (the 14 plane rows, the wall-link
+// bytes and the two port entries), so one warp instruction starts them all.
+__device__ __forceinline__ void issue_tile(const StepArgs& a, uint2 tile, Stage& sg, uint64_t* bar, int lane)
+{
+    const int y = int(tile.x >> kSegBits);
+    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
+    const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
+    // columns of the lanes that hold fluid, and one quad more on each side
+    // for the planes that pull from x -+ 1
+    const int us = x0 + 4 * q0, ue = x0 + 4 * q1 + 4;
+    const int ss = us - 4 > 0 ? us - 4 : 0;
+    const int se = ue + 4 < a.pitch ? ue + 4 : a.pitch;
+    if (lane == 0) {
+        sg.tile = tile;
+        const uint32_t bytes = uint32_t(6 * (ue - us) + 8 * (se - ss)) * 4u + kTileNodes + 2 * sizeof(RowBC);
+        mbar_arrive_expect_tx(bar, bytes);
+    }
+    __syncwarp();
+    const long long rC = (long long)y * a.pitch;
+    if (lane < kPlanes) {
+        const int p = lane;
+        const long long r = src_row(p) == 0 ? rC
+                            : src_row(p) == 1 ? (long long)(y > 0 ? y - 1 : y) * a.pitch
+                                              : (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch;
+        const int b = src_col(p) == 0 ? us : ss;
+        const int e = src_col(p) == 0 ? ue : se;
+        bulk_g2s(&sg.pl[p][b - x0 + 4], a.src + p * a.plane + r + b, uint32_t(e - b) * 4u, bar);
+    } else if (lane == kPlanes) {
+        bulk_g2s(sg.links, a.links + rC + x0, kTileNodes, bar);
+    } else if (lane == kPlanes + 1) {
+        bulk_g2s(&sg.bc[0], a.rowbc + y, sizeof(RowBC), bar);
+    } else if (lane == kPlanes + 2) {
+        bulk_g2s(&sg.bc[1], a.rowbc + a.ny + y, sizeof(RowBC), bar);
+    }
+}
+
+// Warp w of the grid takes tiles w, w + W, w + 2W, ... (W warps in all).
+// It owns `per` stages; its k-th tile goes to stage k % per as that stage's
+// use k / per, and the warp refills a stage as soon as it has read it, so
+// `per` tiles are always on their way while it computes.
+__global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const StepArgs a, int per)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    Stage* st = reinterpret_cast<Stage*>(smem) + warp * per;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(wpb) * per * sizeof(Stage)) + warp * per;
+    const long long P = a.plane;
+    const float* __restrict__ S = a.src;
+    const int gw = int(blockIdx.x) * wpb + warp;
+    const int W = int(gridDim.x) * wpb;
+    const int n_items = gw < a.n_tiles ? (a.n_tiles - 1 - gw) / W + 1 : 0;
+
+    if (lane == 0) {
+        for (int s = 0; s < per; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+
+    LaneDiag diag;
+    bool bad = false;
+    int issued = 0;  // items whose copies were started
+    for (; issued < n_items && issued < per; ++issued)
+        issue_tile(a, a.tiles[gw + size_t(issued) * W], st[issued], &full[issued], lane);
+    uint2 pending = issued < n_items ? a.tiles[gw + size_t(issued) * W] : make_uint2(0u, 0u);
+
+    int k = 0;
+    for (; k < n_items; ++k) {
+        const int s = k % per;
+        const uint32_t use = uint32_t(k / per);
+        if (!__all_sync(kFull, mbar_wait(&full[s], use & 1u))) {
+            if (lane == 0) atomicOr(a.err, 2u);
+            break;
+        }
+        const Stage& sg = st[s];
+        const uint2 tile = sg.tile;
+        const int y = int(tile.x >> kSegBits);
+        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+        const long long oC = (long long)y * a.pitch + x0;
+        const unsigned lk = sg.links[lane];
+        const bool act = lk != 0xFFFFFFFFu;
+        const RowBC bw = sg.bc[0], be = sg.bc[1];
+        // ---- free flight (pull) from the staged rows ----
+        float4 v[kPlanes];
+        if (act) {
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) {
+                const float* row = sg.pl[p] + 4 * lane;
+                const float4 c = *reinterpret_cast<const float4*>(row + 4);
+                if (src_col(p) == 0) v[p] = c;
+                else if (src_col(p) == 1) v[p] = make_float4(row[3], c.x, c.y, c.z);
+                else v[p] = make_float4(c.y, c.z, c.w, row[8]);
+            }
+        }
+        // ---- refill the stage with the tile `per` items ahead ----
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (issued < n_items) {
+            issue_tile(a, pending, st[s], &full[s], lane);
+            ++issued;
+            if (issued < n_items) pending = a.tiles[gw + size_t(issued) * W];
+        }
+        if (act) {
+            bounce_back(v, lk, S, P, oC);
+            QuadAcc q;
+            collide_quad(v, lk, x0, bw, be, a, S, oC, q);
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) stg4(a.dst + p * P + oC, v[p]);
+            bad |= q.bad;
+            diag.add(q);
+        }
+    }
+    // after a timeout: no copy may still be writing this block's shared memory at exit
+    for (int j = k; j < issued; ++j)
+        if (!__all_sync(kFull, mbar_wait(&full[j % per], uint32_t(j / per) & 1u)) && lane == 0)
+            atomicOr(a.err, 2u);
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
+    block_partials(a, diag);
+}
+
+// ---------------------------------------------------------------------------
 // Set-up and read-out kernels
 // ---------------------------------------------------------------------------
 __global__ void init_rest(float* pop, long long plane, float rho0, float wg0, float wg1, float C0)
@@ -710,8 +842,12 @@ cudaError_t prepare_step_kernels()
 {
     // The attribute belongs to the kernel, not to a handle: allow the largest
     // ring any handle may ask for, so handles of different shapes coexist.
-    return cudaFuncSetAttribute(coupled_step_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(bulk_smem_bytes(kMaxStages)));
+    cudaError_t e = cudaFuncSetAttribute(coupled_step_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(bulk_smem_bytes(kMaxStages)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(coupled_step_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(bulk_smem_bytes(kMaxStages)));
+    return e;
 }
 
 cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
@@ -719,6 +855,9 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
     if (l.variant == kVariantBulk) {
         const int per = l.stages / (l.block / 32 - 1);
         coupled_step_bulk<<<l.grid, l.block, bulk_smem_bytes(l.stages), s>>>(a, per);
+    } else if (l.variant == kVariantPipe) {
+        const int per = l.stages / (l.block / 32);
+        coupled_step_pipe<<<l.grid, l.block, bulk_smem_bytes(l.stages), s>>>(a, per);
     } else {
         coupled_step_regs<<<l.grid, l.block, 0, s>>>(a);
     }
@@ -735,6 +874,9 @@ cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm)
 {
     if (l.variant == kVariantBulk)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk, l.block,
+                                                             bulk_smem_bytes(l.stages));
+    if (l.variant == kVariantPipe)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_pipe, l.block,
                                                              bulk_smem_bytes(l.stages));
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs, l.block, 0);
 }

@@ -51,7 +51,7 @@ def _field_errors(prob, chip, ref):
     return du, dC, dm
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("nx,ny,seed", [(8, 8, 1), (17, 9, 2), (64, 32, 3), (130, 12, 4),
                                         (300, 20, 5), (129, 16, 6), (300, 20, 7), (260, 8, 5)])
 def test_population_parity_random_lattices(nx, ny, seed, variant):
@@ -87,7 +87,9 @@ def test_population_parity_random_lattices(nx, ny, seed, variant):
 @pytest.mark.parametrize("opts", [dict(variant=1), dict(variant=2, pipeline_stages=1, consumer_warps=1),
                                   dict(variant=2, pipeline_stages=3, consumer_warps=7),
                                   dict(variant=2, pipeline_stages=1, consumer_warps=7, max_blocks=3),
-                                  dict(variant=2, pipeline_stages=5, consumer_warps=3, max_blocks=7)])
+                                  dict(variant=2, pipeline_stages=5, consumer_warps=3, max_blocks=7),
+                                  dict(variant=3), dict(variant=3, pipeline_stages=3, consumer_warps=8),
+                                  dict(variant=3, pipeline_stages=1, consumer_warps=1, max_blocks=5)])
 def test_kernel_variants_are_bit_identical(opts):
     """Both step kernels and any pipeline shape run the same arithmetic on
     the same values: identical bits after 300 steps with valve toggles and
