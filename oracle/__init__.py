@@ -47,6 +47,10 @@ def _load():
         lib.orc_post_collision.argtypes = [ctypes.c_void_p, d, d]
         lib.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_uint, d]
         lib.orc_lattice_vectors.argtypes = [P(ctypes.c_int), P(ctypes.c_int), d]
+        lib.orc_adjoint_step.argtypes = [ctypes.c_void_p, ctypes.c_uint, d, d, d, d, d, d, d]
+        lib.orc_adjoint.restype = ctypes.c_double
+        lib.orc_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_uint), ctypes.c_int,
+                                    P(ctypes.c_int), P(ctypes.c_int), d, d, d, d, d]
         _lib = lib
     return _lib
 
@@ -145,6 +149,41 @@ class OracleLattice:
         g = np.zeros((self.ny, self.nx, 5))
         self._lib.orc_post_collision(self._h, _dptr(f), _dptr(g))
         return f, g
+
+    def adjoint_step(self, open_mask, S_t, S_t1, af, ag):
+        """One reverse step: (af, ag) = dJ/dS_{t+1} -> dJ/dS_t, given the
+        pre-collision states S_t = (f, g) and S_{t+1}.  Returns (af, ag, grad)
+        with grad = [dJ/d(1/tau_g), dJ/du_in (2*ny), dJ/dC_in (2*ny)]."""
+        c = lambda a, k: np.ascontiguousarray(a, np.float64).reshape(self.ny, self.nx, k)
+        ft, gt, ft1, gt1 = c(S_t[0], 9), c(S_t[1], 5), c(S_t1[0], 9), c(S_t1[1], 5)
+        af = c(af, 9).copy()
+        ag = c(ag, 5).copy()
+        grad = np.zeros(1 + 4 * self.ny)
+        self._lib.orc_adjoint_step(self._h, ctypes.c_uint(int(open_mask) & 0xFFFFFFFF), _dptr(ft), _dptr(gt),
+                                   _dptr(ft1), _dptr(gt1), _dptr(af), _dptr(ag), _dptr(grad))
+        return af, ag, grad
+
+    def adjoint(self, n, masks, obj_x, obj_y, target, weight):
+        """n forward steps (the lattice advances) and the reverse pass of
+        J = sum weight (C(x, y) - target)^2 at the final step.  Returns
+        (J, dJ/dtau_g, dJ/du_in (2, ny), dJ/dC_in (2, ny))."""
+        masks = np.ascontiguousarray(masks, np.uint32)
+        assert len(masks) >= n
+        ox = np.ascontiguousarray(obj_x, np.int32)
+        oy = np.ascontiguousarray(obj_y, np.int32)
+        tg = np.ascontiguousarray(target, np.float64)
+        wt = np.ascontiguousarray(weight, np.float64)
+        dtau = np.zeros(1)
+        du = np.zeros((2, self.ny))
+        dc = np.zeros((2, self.ny))
+        ip = ctypes.POINTER(ctypes.c_int)
+        J = self._lib.orc_adjoint(self._h, int(n), masks.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)), len(ox),
+                                  ox.ctypes.data_as(ip), oy.ctypes.data_as(ip), _dptr(tg), _dptr(wt),
+                                  _dptr(dtau), _dptr(du), _dptr(dc))
+        if J < 0:
+            raise MemoryError("oracle adjoint: trajectory does not fit in host memory")
+        self.t += int(n)
+        return J, float(dtau[0]), du, dc
 
     def diagnostics(self, open_mask):
         out = np.zeros(4)

@@ -395,3 +395,239 @@ void orc_diagnostics(const orc_lattice* L, unsigned open_mask, double out[4])
     out[2] = q;
     out[3] = qc;
 }
+
+/* ------------------------------------------------------------------------
+ * Adjoint of one step (reverse mode).  The forward step is
+ *   S_{t+1} = B(P(K(S_t)))
+ * with K the collision at every fluid node (Eq. lbequation and its scalar
+ * counterpart), P the free flight with bounce-back (a permutation of the
+ * post-collision values), B the open-port completion (affine in the values it
+ * reads).  The adjoint applies the transposes in reverse order:
+ *   a_t = K'(S_t)^T P^T B^T a_{t+1}.
+ * ------------------------------------------------------------------------ */
+
+/* Transpose of the Zou-He completion at one node.  kn holds the node's
+ * values of S_{t+1} (the known populations are the streamed ones); a is the
+ * node's adjoint, whose three unknown entries are folded into the known ones
+ * and cleared.  Returns dJ/du_in for a velocity node (0 otherwise). */
+static double zou_he_adjoint(const double* kn, double* a, int s, int kind, double u_in, double rho_in)
+{
+    int axis_in = s > 0 ? 1 : 3;
+    int diag_in_up = s > 0 ? 5 : 6;
+    int diag_in_dn = s > 0 ? 8 : 7;
+    int axis_out = OPP[axis_in];
+    int diag_out_dn = OPP[diag_in_up];
+    int diag_out_up = OPP[diag_in_dn];
+    double a_ax = a[axis_in], a_up = a[diag_in_up], a_dn = a[diag_in_dn];
+    a[axis_in] = a[diag_in_up] = a[diag_in_dn] = 0.0;
+    /* direct terms: f_ax_in = f_ax_out + ..., f_up = f_dout_dn - (f2 - f4)/2 + ...,
+     * f_dn = f_dout_up + (f2 - f4)/2 + ... */
+    a[axis_out] += a_ax;
+    a[diag_out_dn] += a_up;
+    a[diag_out_up] += a_dn;
+    a[2] += -0.5 * a_up + 0.5 * a_dn;
+    a[4] += 0.5 * a_up - 0.5 * a_dn;
+    /* through the node's x momentum jx: dJ/djx */
+    double G = s * (2.0 / 3.0) * a_ax + s * (1.0 / 6.0) * (a_up + a_dn);
+    double K = kn[0] + kn[2] + kn[4] + 2.0 * (kn[axis_out] + kn[diag_out_dn] + kn[diag_out_up]);
+    double dK, du = 0.0;
+    if (kind == ORC_VELOCITY) {
+        double den = 1.0 - s * u_in;
+        dK = G * u_in / den;            /* jx = K u / (1 - s u) */
+        du = G * K / (den * den);
+    } else {
+        (void)rho_in;
+        dK = -s * G;                    /* jx = s (rho - K) */
+    }
+    a[0] += dK;
+    a[2] += dK;
+    a[4] += dK;
+    a[axis_out] += 2.0 * dK;
+    a[diag_out_dn] += 2.0 * dK;
+    a[diag_out_up] += 2.0 * dK;
+    return du;
+}
+
+/* Transpose of the collision at one node with pre-collision values fn, gn:
+ * on entry af/ag hold the adjoint of the post-collision values, on exit the
+ * adjoint of the pre-collision values.  Returns dJ/d(1/tau_g) of the node. */
+static double collide_adjoint(const orc_lattice* L, const double* fn, const double* gn, double* af,
+                              double* ag)
+{
+    double rho, ux, uy;
+    moments(fn, &rho, &ux, &uy);
+    double C = scalar_moment(gn);
+    double w = 1.0 / L->tau_f, omg = 1.0 / L->tau_g;
+    double cs2 = 0.5 * (1.0 - L->w0);
+    double uu = ux * ux + uy * uy;
+    /* f_eq_k = w_k [rho + 3 e.j + 9/2 (e.j)^2 / rho - 3/2 j^2 / rho], j = rho u:
+     * derivatives with respect to rho (j fixed) and to j */
+    double Ar = 0.0, Ax = 0.0, Ay = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        double eu = EX[k] * ux + EY[k] * uy;
+        Ar += af[k] * W9[k] * (1.0 - 4.5 * eu * eu + 1.5 * uu);
+        Ax += af[k] * W9[k] * (3.0 * EX[k] + 9.0 * eu * EX[k] - 3.0 * ux);
+        Ay += af[k] * W9[k] * (3.0 * EY[k] + 9.0 * eu * EY[k] - 3.0 * uy);
+    }
+    /* g_eq_k = w_k C [1 + e.j / (rho c_s^2)]: derivatives with respect to C,
+     * rho and j */
+    double Bc = 0.0, Br = 0.0, Bx = 0.0, By = 0.0, dwg = 0.0;
+    for (int k = 0; k < 5; ++k) {
+        double eu = EX[k] * ux + EY[k] * uy;
+        double wk = wg(L, k);
+        Bc += ag[k] * wk * (1.0 + eu / cs2);
+        Br += ag[k] * wk * C * (-eu / (rho * cs2));
+        Bx += ag[k] * wk * C * EX[k] / (rho * cs2);
+        By += ag[k] * wk * C * EY[k] / (rho * cs2);
+        dwg += ag[k] * (geq(L, k, C, ux, uy) - gn[k]);
+    }
+    double nf[9], ng[5];
+    for (int i = 0; i < 9; ++i)
+        nf[i] = (1.0 - w) * af[i] + w * (Ar + Ax * EX[i] + Ay * EY[i]) +
+                omg * (Br + Bx * EX[i] + By * EY[i]);
+    for (int i = 0; i < 5; ++i) ng[i] = (1.0 - omg) * ag[i] + omg * Bc;
+    for (int i = 0; i < 9; ++i) af[i] = nf[i];
+    for (int i = 0; i < 5; ++i) ag[i] = ng[i];
+    return dwg;
+}
+
+void orc_adjoint_step(const orc_lattice* L, unsigned open_mask, const double* f_t,
+                      const double* g_t, const double* f_t1, const double* g_t1,
+                      double* af, double* ag, double* grad)
+{
+    const int nx = L->nx, ny = L->ny;
+    size_t n = (size_t)nx * (size_t)ny;
+    double* bf = (double*)calloc(n * 9, sizeof(double)); /* adjoint after B^T */
+    double* dn = (double*)calloc(n, sizeof(double));     /* do-nothing terms */
+    double* pf = (double*)calloc(n * 9, sizeof(double)); /* adjoint of post-collision */
+    double* pg = (double*)calloc(n * 5, sizeof(double));
+    if (!bf || !dn || !pf || !pg) {
+        free(bf); free(dn); free(pf); free(pg);
+        return;
+    }
+    (void)g_t1;
+    /* B^T: fold the adjoint of every completed (unknown) population into the
+     * populations it was computed from */
+    for (int p = 0; p < L->n_ports; ++p) {
+        const orc_port* P = &L->ports[p];
+        if (!((open_mask >> P->channel) & 1u)) continue;
+        int s = P->side == ORC_WEST ? 1 : -1;
+        int g_in = s > 0 ? 1 : 3;
+        for (int y = P->y0; y < P->y1; ++y) {
+            int c = node(L, P->x, y);
+            double* a = af + (size_t)c * 9;
+            double* b = ag + (size_t)c * 5;
+            if (P->kind == ORC_VELOCITY) {
+                grad[1 + P->side * ny + y] +=
+                    zou_he_adjoint(f_t1 + (size_t)c * 9, a, s, ORC_VELOCITY, L->edge_u[P->side * ny + y], 0.0);
+                /* g_in = C_in - sum of the others */
+                double ain = b[g_in];
+                b[g_in] = 0.0;
+                for (int i = 0; i < 5; ++i)
+                    if (i != g_in) b[i] -= ain;
+                grad[1 + 2 * ny + P->side * ny + y] += ain;
+            } else {
+                zou_he_adjoint(f_t1 + (size_t)c * 9, a, s, ORC_PRESSURE, 0.0, P->rho);
+                /* g_in(t+1) = its own post-collision value at t */
+                dn[c] = b[g_in];
+                b[g_in] = 0.0;
+            }
+        }
+    }
+    memcpy(bf, af, n * 9 * sizeof(double));
+    /* P^T: every post-collision value went to exactly one place */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (!is_fluid(L, x, y)) continue;
+            int c = node(L, x, y);
+            for (int i = 0; i < 9; ++i) {
+                int xn = x + EX[i], yn = y + EY[i];
+                if (L->periodic) {
+                    xn = (xn + nx) % nx;
+                    yn = (yn + ny) % ny;
+                }
+                if (is_fluid(L, xn, yn)) pf[c * 9 + i] = bf[node(L, xn, yn) * 9 + i];
+                else pf[c * 9 + i] = bf[c * 9 + OPP[i]];
+            }
+            for (int i = 0; i < 5; ++i) {
+                int xn = x + EX[i], yn = y + EY[i];
+                if (L->periodic) {
+                    xn = (xn + nx) % nx;
+                    yn = (yn + ny) % ny;
+                }
+                if (is_fluid(L, xn, yn)) pg[c * 5 + i] = ag[node(L, xn, yn) * 5 + i];
+                else pg[c * 5 + i] = ag[c * 5 + OPP[i]];
+            }
+        }
+    for (int p = 0; p < L->n_ports; ++p) {
+        const orc_port* P = &L->ports[p];
+        if (P->kind != ORC_PRESSURE || !((open_mask >> P->channel) & 1u)) continue;
+        int g_in = P->side == ORC_WEST ? 1 : 3;
+        for (int y = P->y0; y < P->y1; ++y) {
+            int c = node(L, P->x, y);
+            pg[c * 5 + g_in] += dn[c];
+        }
+    }
+    /* K^T at every fluid node, with the pre-collision values of S_t */
+    memset(af, 0, n * 9 * sizeof(double));
+    memset(ag, 0, n * 5 * sizeof(double));
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (!is_fluid(L, x, y)) continue;
+            int c = node(L, x, y);
+            double* a = pf + (size_t)c * 9;
+            double* b = pg + (size_t)c * 5;
+            grad[0] += collide_adjoint(L, f_t + (size_t)c * 9, g_t + (size_t)c * 5, a, b);
+            memcpy(af + (size_t)c * 9, a, 9 * sizeof(double));
+            memcpy(ag + (size_t)c * 5, b, 5 * sizeof(double));
+        }
+    free(bf);
+    free(dn);
+    free(pf);
+    free(pg);
+}
+
+double orc_adjoint(orc_lattice* L, int n, const unsigned* masks, int n_obj,
+                   const int* obj_x, const int* obj_y, const double* target,
+                   const double* weight, double* dJ_dtau_g, double* dJ_du_in,
+                   double* dJ_dC_in)
+{
+    const int ny = L->ny;
+    size_t nodes = (size_t)L->nx * (size_t)ny;
+    double* fs = (double*)malloc((size_t)(n + 1) * nodes * 9 * sizeof(double));
+    double* gs = (double*)malloc((size_t)(n + 1) * nodes * 5 * sizeof(double));
+    double* af = (double*)calloc(nodes * 9, sizeof(double));
+    double* ag = (double*)calloc(nodes * 5, sizeof(double));
+    double* grad = (double*)calloc(1 + 4 * (size_t)ny, sizeof(double));
+    if (!fs || !gs || !af || !ag || !grad) {
+        free(fs); free(gs); free(af); free(ag); free(grad);
+        return -1.0;
+    }
+    memcpy(fs, L->f, nodes * 9 * sizeof(double));
+    memcpy(gs, L->g, nodes * 5 * sizeof(double));
+    for (int t = 0; t < n; ++t) {
+        orc_step(L, masks[t]);
+        memcpy(fs + (size_t)(t + 1) * nodes * 9, L->f, nodes * 9 * sizeof(double));
+        memcpy(gs + (size_t)(t + 1) * nodes * 5, L->g, nodes * 5 * sizeof(double));
+    }
+    /* J and its derivative with respect to S_n: C = sum of g */
+    double J = 0.0;
+    for (int k = 0; k < n_obj; ++k) {
+        int c = node(L, obj_x[k], obj_y[k]);
+        double C = scalar_moment(L->g + (size_t)c * 5);
+        double d = C - target[k];
+        J += weight[k] * d * d;
+        for (int i = 0; i < 5; ++i) ag[(size_t)c * 5 + i] += 2.0 * weight[k] * d;
+    }
+    for (int t = n - 1; t >= 0; --t)
+        orc_adjoint_step(L, masks[t], fs + (size_t)t * nodes * 9, gs + (size_t)t * nodes * 5,
+                         fs + (size_t)(t + 1) * nodes * 9, gs + (size_t)(t + 1) * nodes * 5, af, ag, grad);
+    /* d(1/tau_g)/dtau_g = -1/tau_g^2 */
+    *dJ_dtau_g = -grad[0] / (L->tau_g * L->tau_g);
+    for (int k = 0; k < 2 * ny; ++k) {
+        dJ_du_in[k] = grad[1 + k];
+        dJ_dC_in[k] = grad[1 + 2 * ny + k];
+    }
+    free(fs); free(gs); free(af); free(ag); free(grad);
+    return J;
+}

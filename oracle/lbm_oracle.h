@@ -97,6 +97,31 @@ void orc_diagnostics(const orc_lattice* L, unsigned open_mask, double out[4]);
 /* Lattice tables as the oracle uses them (for checks against Eq. lattice). */
 void orc_lattice_vectors(int ex[9], int ey[9], double w[9]);
 
+/* ---- Adjoint (reverse-mode derivative of the time step) ----
+ *
+ * The step maps the pre-collision state S_t = (f, g) to S_{t+1}; its
+ * parameters are tau_g, the inlet velocities u_in (edge_u) and the held
+ * concentrations C_in (edge_C).  orc_adjoint_step takes the adjoint of
+ * S_{t+1} (af, ag: d J / d S_{t+1}, node-major like the populations) and
+ * replaces it, in place, by the adjoint of S_t, given S_t and S_{t+1} and the
+ * step's valve word.  It adds the step's parameter derivatives to grad:
+ * grad[0] += dJ/d(1/tau_g), grad[1 + side*ny + y] += dJ/du_in(side, y),
+ * grad[1 + 2*ny + side*ny + y] += dJ/dC_in(side, y). */
+void orc_adjoint_step(const orc_lattice* L, unsigned open_mask, const double* f_t,
+                      const double* g_t, const double* f_t1, const double* g_t1,
+                      double* af, double* ag, double* grad);
+
+/* Run n steps forward from the current state with the given valve words
+ * (the lattice ends at S_n, as after n calls of orc_step), then the reverse
+ * pass for J = sum_k weight_k (C(x_k, y_k, n) - target_k)^2.  Returns J and
+ * writes dJ/dtau_g, dJ/du_in (2*ny) and dJ/dC_in (2*ny).  Keeps every state
+ * of the trajectory in host memory (test sizes).  Returns a negative value
+ * and writes nothing if memory runs out. */
+double orc_adjoint(orc_lattice* L, int n, const unsigned* masks, int n_obj,
+                   const int* obj_x, const int* obj_y, const double* target,
+                   const double* weight, double* dJ_dtau_g, double* dJ_du_in,
+                   double* dJ_dC_in);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,9 +2,9 @@
 
 Each case plants one slip in a scratch copy of the oracle's C source (a wrong
 direction index, a dropped or mis-signed term, a swapped relaxation time, a
-wrong boundary population...), rebuilds that copy and runs the pin tests
-against it in a subprocess; at least one pin must fail.  The real oracle is
-never modified.
+wrong boundary population, a wrong transpose in the adjoint...), rebuilds
+that copy and runs the forward or adjoint pin tests against it in a
+subprocess; at least one pin must fail.  The real oracle is never modified.
 """
 import os
 import shutil
@@ -64,9 +64,31 @@ MUTANTS = [
     ("diagonal weight", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 18.0};"),
 ]
 
+# slips in the adjoint, caught by tests/test_oracle_adjoint.py
+ADJOINT_MUTANTS = [
+    ("adjoint: equilibrium u^2 term", "Ar += af[k] * W9[k] * (1.0 - 4.5 * eu * eu + 1.5 * uu);",
+     "Ar += af[k] * W9[k] * (1.0 - 4.5 * eu * eu);"),
+    ("adjoint: momentum derivative", "Ax += af[k] * W9[k] * (3.0 * EX[k] + 9.0 * eu * EX[k] - 3.0 * ux);",
+     "Ax += af[k] * W9[k] * (3.0 * EX[k] + 9.0 * eu * EX[k]);"),
+    ("adjoint: scalar-to-fluid coupling dropped", "Bx += ag[k] * wk * C * EX[k] / (rho * cs2);", "(void)0;"),
+    ("adjoint: relaxation-rate derivative sign", "dwg += ag[k] * (geq(L, k, C, ux, uy) - gn[k]);",
+     "dwg += ag[k] * (gn[k] - geq(L, k, C, ux, uy));"),
+    ("adjoint: do-nothing term lost", "pg[c * 5 + g_in] += dn[c];", "(void)dn[c];"),
+    ("adjoint: Zou-He momentum weight", "double G = s * (2.0 / 3.0) * a_ax + s * (1.0 / 6.0) * (a_up + a_dn);",
+     "double G = s * (2.0 / 3.0) * a_ax + s * (1.0 / 3.0) * (a_up + a_dn);"),
+    ("adjoint: Zou-He velocity derivative", "du = G * K / (den * den);", "du = G * K / den;"),
+    ("adjoint: Dirichlet transpose sign", "if (i != g_in) b[i] -= ain;", "if (i != g_in) b[i] += ain;"),
+    ("adjoint: bounce-back transpose keeps direction", "else pf[c * 9 + i] = bf[c * 9 + OPP[i]];",
+     "else pf[c * 9 + i] = bf[c * 9 + i];"),
+]
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_a_planted_mistake_fails_a_pin(tmp_path, name, old, new):
+
+CASES = [m + ("tests/test_oracle_pins.py",) for m in MUTANTS] + \
+        [m + ("tests/test_oracle_adjoint.py",) for m in ADJOINT_MUTANTS]
+
+
+@pytest.mark.parametrize("name,old,new,pins", CASES, ids=[m[0] for m in CASES])
+def test_a_planted_mistake_fails_a_pin(tmp_path, name, old, new, pins):
     src = open(os.path.join(ROOT, "oracle", "lbm_oracle.c")).read()
     assert src.count(old) >= 1, "mutation site not found: " + name
     for sub in ("oracle", "tests"):
@@ -78,7 +100,7 @@ def test_a_planted_mistake_fails_a_pin(tmp_path, name, old, new):
         shutil.copy(os.path.join(ROOT, "paper_1307_4703_gb300", f), pkg / f)
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
     (tmp_path / "oracle" / "lbm_oracle.c").write_text(src.replace(old, new, 1))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "tests/test_oracle_pins.py"],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", pins],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "no pin caught the planted mistake '%s'" % name
     assert "failed" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
