@@ -196,6 +196,37 @@ lbm_status lbm_set_populations(lbm_handle h, const float* f, const float* g);
 lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux,
                                 const float* uy, const float* C);
 
+/* Objective of lbm_adjoint: J = sum_k weight[k] (C(x[k], y[k]) - target[k])^2
+ * over n fluid nodes, on the state after the last step (for example the
+ * chamber's concentration profile against a linear target).  Host arrays,
+ * read during the call. */
+typedef struct {
+    int32_t n;
+    const int32_t* x;
+    const int32_t* y;
+    const float* target;
+    const float* weight;
+} lbm_objective;
+
+/* Gradient of J by the adjoint (reverse-mode) method.  Advances the chip by
+ * n_steps >= 1 exactly as lbm_step would (same valve words, same final
+ * state and step counter), keeping a copy of the state every ckpt_every
+ * steps; then, segment by segment from the end, recomputes the states of the
+ * segment from its checkpoint and runs the adjoint steps backwards.  Writes
+ * J, dJ/dtau_c and, when the pointers are not NULL, dJ/du_in and dJ/dC_in:
+ * host arrays of 2*ny doubles, [side*ny + y], the derivatives with respect
+ * to the u_x and the held concentration of the velocity-port node of that
+ * side and row (0 for rows without one).  For an inlet profile
+ * u_in(y) = u_max phi(y), dJ/du_max = sum_y dJ/du_in(y) phi(y).
+ * Device memory: ceil(n_steps / ckpt_every) + ckpt_every - 1 population
+ * copies and three adjoint buffers, taken through the handle's allocator
+ * and released before returning (LBM_ERR_OOM if they do not fit).  The
+ * derivatives are accumulated in FP64; the adjoint populations are FP32.
+ * The diagnostics of lbm_get_diagnostics stay those of the last forward
+ * step.  Synchronises the stream. */
+lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n_steps, int32_t ckpt_every,
+                       double* J, double* dJ_dtau_c, double* dJ_du_in, double* dJ_dC_in);
+
 /* Checkpoint / resume: the step counter, fixed valve word, schedule and
  * populations.  lbm_save_state with buf == NULL stores the needed size in
  * *bytes; otherwise *bytes must be at least that size.  lbm_load_state

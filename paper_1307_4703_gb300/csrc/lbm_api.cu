@@ -72,6 +72,7 @@ struct lbm_ctx {
     bool timeout = false;  // a bounded device wait gave up (bit 1)
 
     std::string last_error = "no error";
+    std::vector<uint8_t> solid;  // host copy of the mask (non-zero = solid)
 
     uint32_t mask_at(int64_t t) const
     {
@@ -340,6 +341,7 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     h->free_fn = opt.free;
     h->alloc_user = opt.alloc_user;
     h->n_tiles = int(tiles.size());
+    h->solid.assign(mask, mask + size_t(nx) * ny);
     h->fluid = fluid;
 
     auto bail = [&](lbm_status s) {
@@ -695,6 +697,187 @@ lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes)
     h->fixed_mask = hd.fixed_mask;
     h->schedule = std::move(sched);
     return LBM_OK;
+}
+
+namespace {
+// Device temporaries of one call, released in reverse order on every exit.
+struct Scratch {
+    lbm_ctx* h;
+    std::vector<Alloc> items;
+    explicit Scratch(lbm_ctx* ctx) : h(ctx) {}
+    void* get(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        void* p = nullptr;
+        if (h->alloc_fn) {
+            p = h->alloc_fn(bytes, h->alloc_user);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) items.push_back({p, bytes});
+        return p;
+    }
+    ~Scratch()
+    {
+        cudaStreamSynchronize(h->stream);
+        for (auto it = items.rbegin(); it != items.rend(); ++it) {
+            if (h->free_fn) h->free_fn(it->ptr, it->bytes, h->alloc_user);
+            else cudaFree(it->ptr);
+        }
+    }
+};
+}  // namespace
+
+lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_t K, double* J,
+                       double* dJ_dtau_c, double* dJ_du_in, double* dJ_dC_in)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (!obj || !J || !dJ_dtau_c) return fail(h, LBM_ERR_ARG, "objective, J or dJ_dtau_c is NULL");
+    if (n < 1 || K < 1) return fail(h, LBM_ERR_ARG, "n_steps = %lld and ckpt_every = %d must be >= 1", (long long)n, K);
+    if (obj->n < 1 || !obj->x || !obj->y || !obj->target || !obj->weight)
+        return fail(h, LBM_ERR_ARG, "the objective needs n >= 1 nodes and all four arrays");
+    for (int k = 0; k < obj->n; ++k) {
+        const int x = obj->x[k], y = obj->y[k];
+        if (x < 0 || x >= h->nx || y < 0 || y >= h->ny || h->solid[size_t(y) * h->nx + x])
+            return fail(h, LBM_ERR_ARG, "objective node %d at (%d, %d) is not a fluid node", k, x, y);
+        if (!std::isfinite(obj->target[k]) || !std::isfinite(obj->weight[k]))
+            return fail(h, LBM_ERR_ARG, "objective node %d has a non-finite target or weight", k);
+    }
+    const long long n_ck = (n + K - 1) / K;
+    const int seg_slots = int(std::min<int64_t>(K, n)) - 1;
+    const size_t S = size_t(h->plane) * lbm::kPlanes * sizeof(float);
+    cudaStream_t st = h->stream;
+
+    int sms = 0, per_sm = 0;
+    LBM_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int ablock = 256;
+    LBM_CUDA(h, lbm::adjoint_occupancy(ablock, &per_sm));
+    const int agrid = std::max(1, std::min((h->n_tiles + ablock / 32 - 1) / (ablock / 32), std::max(1, per_sm) * sms));
+
+    Scratch tmp(h);
+    char* ckpt = static_cast<char*>(tmp.get(size_t(n_ck) * S));
+    char* seg = seg_slots > 0 ? static_cast<char*>(tmp.get(size_t(seg_slots) * S)) : nullptr;
+    float* adj[3] = {static_cast<float*>(tmp.get(S)), static_cast<float*>(tmp.get(S)), static_cast<float*>(tmp.get(S))};
+    float* dn = static_cast<float*>(tmp.get(size_t(2) * h->ny * sizeof(float)));
+    double* gw = static_cast<double*>(tmp.get(size_t(agrid) * sizeof(double)));
+    double* gu = static_cast<double*>(tmp.get(size_t(2) * h->ny * sizeof(double)));
+    double* gc = static_cast<double*>(tmp.get(size_t(2) * h->ny * sizeof(double)));
+    double* dJ = static_cast<double*>(tmp.get(2 * sizeof(double)));
+    double* rp = static_cast<double*>(tmp.get(size_t(h->launch.grid) * 4 * sizeof(double)));
+    int* ox = static_cast<int*>(tmp.get(size_t(obj->n) * sizeof(int)));
+    int* oy = static_cast<int*>(tmp.get(size_t(obj->n) * sizeof(int)));
+    float* ot = static_cast<float*>(tmp.get(size_t(obj->n) * sizeof(float)));
+    float* ow = static_cast<float*>(tmp.get(size_t(obj->n) * sizeof(float)));
+    if (!ckpt || (seg_slots > 0 && !seg) || !adj[0] || !adj[1] || !adj[2] || !dn || !gw || !gu || !gc || !dJ ||
+        !rp || !ox || !oy || !ot || !ow)
+        return fail(h, LBM_ERR_OOM, "adjoint: device memory for %lld checkpoints and %d recomputed states not available",
+                    n_ck, seg_slots);
+
+    // forward sweep with checkpoints (the handle advances as in lbm_step)
+    lbm::StepArgs a{};
+    a.links = h->links;
+    a.rowbc = h->rowbc;
+    a.tiles = h->tiles;
+    a.n_tiles = h->n_tiles;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.omega_f = float(1.0 / h->tau);
+    a.omega_g = float(1.0 / h->tau_c);
+    a.wg0 = h->wg0;
+    a.wg1 = h->wg1;
+    a.inv_cs2g = h->inv_cs2g;
+    a.partials = h->partials;
+    a.err = h->err;
+    const int64_t t0 = h->step;
+    for (int64_t t = 0; t < n; ++t) {
+        if (t % K == 0)
+            LBM_CUDA(h, cudaMemcpyAsync(ckpt + size_t(t / K) * S, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
+        a.src = h->pop[h->cur];
+        a.dst = h->pop[1 - h->cur];
+        a.open_mask = h->mask_at(t0 + t);
+        cudaError_t e = lbm::launch_step(a, h->launch, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+        h->cur = 1 - h->cur;
+        ++h->step;
+    }
+
+    // J and dJ/dP(n)
+    std::vector<int> hx(obj->x, obj->x + obj->n), hy(obj->y, obj->y + obj->n);
+    LBM_CUDA(h, cudaMemcpyAsync(ox, hx.data(), hx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    LBM_CUDA(h, cudaMemcpyAsync(oy, hy.data(), hy.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    LBM_CUDA(h, cudaMemcpyAsync(ot, obj->target, size_t(obj->n) * sizeof(float), cudaMemcpyHostToDevice, st));
+    LBM_CUDA(h, cudaMemcpyAsync(ow, obj->weight, size_t(obj->n) * sizeof(float), cudaMemcpyHostToDevice, st));
+    LBM_CUDA(h, cudaMemsetAsync(adj[0], 0, S, st));
+    LBM_CUDA(h, cudaMemsetAsync(adj[2], 0, S, st));
+    LBM_CUDA(h, cudaMemsetAsync(gw, 0, size_t(agrid) * sizeof(double), st));
+    LBM_CUDA(h, cudaMemsetAsync(gu, 0, size_t(2) * h->ny * sizeof(double), st));
+    LBM_CUDA(h, cudaMemsetAsync(gc, 0, size_t(2) * h->ny * sizeof(double), st));
+    LBM_CUDA(h, cudaMemsetAsync(dn, 0, size_t(2) * h->ny * sizeof(float), st));
+    {
+        cudaError_t e = lbm::launch_adjoint_seed(h->pop[h->cur], h->plane, h->pitch, ox, oy, ot, ow, obj->n, adj[0],
+                                                 dJ, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "adjoint seed launch");
+    }
+
+    // backward, segment by segment
+    lbm::AdjointArgs A{};
+    A.links = h->links;
+    A.rowbc = h->rowbc;
+    A.tiles = h->tiles;
+    A.n_tiles = h->n_tiles;
+    A.ny = h->ny;
+    A.pitch = h->pitch;
+    A.plane = h->plane;
+    A.omega_f = a.omega_f;
+    A.omega_g = a.omega_g;
+    A.wg0 = h->wg0;
+    A.wg1 = h->wg1;
+    A.inv_cs2g = h->inv_cs2g;
+    A.dn = dn;
+    A.grad_w = gw;
+    A.grad_u = gu;
+    A.grad_c = gc;
+    A.adj_mid = adj[2];
+    lbm::StepArgs r = a;
+    r.partials = rp;  // keep the diagnostics of the last forward step
+    int cur = 0;      // adj[cur] holds A(t+1)
+    for (long long sg = n_ck - 1; sg >= 0; --sg) {
+        const int64_t s0 = sg * K;
+        const int len = int(std::min<int64_t>(K, n - s0));
+        auto state = [&](int j) -> float* {
+            return reinterpret_cast<float*>(j == 0 ? ckpt + size_t(sg) * S : seg + size_t(j - 1) * S);
+        };
+        for (int j = 1; j < len; ++j) {
+            r.src = state(j - 1);
+            r.dst = state(j);
+            r.open_mask = h->mask_at(t0 + s0 + j - 1);
+            cudaError_t e = lbm::launch_step(r, h->launch, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "recompute step launch");
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            A.state = state(j);
+            A.adj_next = adj[cur];
+            A.adj_out = adj[1 - cur];
+            A.open_mask = h->mask_at(t0 + s0 + j);
+            cudaError_t e = lbm::launch_adjoint_step(A, agrid, ablock, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
+            cur = 1 - cur;
+        }
+    }
+    {
+        cudaError_t e = lbm::launch_sum_doubles(gw, agrid, dJ + 1, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "gradient reduction launch");
+    }
+    double host[2];
+    LBM_CUDA(h, cudaMemcpyAsync(host, dJ, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (dJ_du_in) LBM_CUDA(h, cudaMemcpyAsync(dJ_du_in, gu, size_t(2) * h->ny * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (dJ_dC_in) LBM_CUDA(h, cudaMemcpyAsync(dJ_dC_in, gc, size_t(2) * h->ny * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LBM_CUDA(h, cudaStreamSynchronize(st));
+    *J = host[0];
+    *dJ_dtau_c = -host[1] / (h->tau_c * h->tau_c);  // d(1/tau_c)/dtau_c = -1/tau_c^2
+    return read_err_word(h);
 }
 
 lbm_status lbm_get_step(lbm_handle h, int64_t* t)

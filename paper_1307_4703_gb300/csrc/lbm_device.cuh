@@ -1,0 +1,400 @@
+// lbm_device.cuh -- device code shared by the step kernels (lbm_kernels.cu)
+// and the adjoint kernels (lbm_adjoint.cu): lattice tables, the inline-PTX
+// bulk-copy and mbarrier helpers, and the per-node arithmetic of the coupled
+// step (Tanaka & Iber, arXiv 1307.4703, "Numerical Methods" and "Boundary
+// Conditions").  Everything here has internal linkage.
+#pragma once
+
+#include <cmath>
+#include <cstddef>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// D2Q9 weights of the equilibrium (Eq. lbequation / the w_i equation).
+constexpr float kWr = 4.0f / 9.0f;   // rest
+constexpr float kWa = 1.0f / 9.0f;   // axis
+constexpr float kWd = 1.0f / 36.0f;  // diagonal
+
+// A bounded wait gives up after this many SM cycles (about one second).
+constexpr long long kWaitCycles = 1ll << 31;
+
+// Eq. lattice: e_1 = E, e_2 = N, e_3 = W, e_4 = S, e_5 = NE, e_6 = NW,
+// e_7 = SW, e_8 = SE.  The opposite of direction i.
+__device__ __forceinline__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5;
+}
+
+// Pull source of plane p relative to the node: row 0 = same row, 1 = row
+// y - 1 (directions with e_y = +1), 2 = row y + 1 (e_y = -1); column
+// 0 = same, 1 = x - 1 (e_x = +1), 2 = x + 1 (e_x = -1).  Planes 9..13 are
+// the scalar directions 0..4.
+__device__ __forceinline__ constexpr int src_row(int p)
+{
+    const int i = p < 9 ? p : p - 9;
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? 2 : 0;
+}
+__device__ __forceinline__ constexpr int src_col(int p)
+{
+    const int i = p < 9 ? p : p - 9;
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? 2 : 0;
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p)
+{
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ void stg4(float* p, const float4& v)
+{
+    *reinterpret_cast<float4*>(p) = v;
+}
+__device__ __forceinline__ float& at(float4& v, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ float at(const float4& v, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// sm_90+ asynchronous bulk copies and mbarriers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase of the given parity to complete; false after about one
+// second (the caller then records LBM_ERR_TIMEOUT and stops).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+// Global -> shared bulk copy completing on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Per-node arithmetic shared by both variants
+// ---------------------------------------------------------------------------
+struct QuadAcc {
+    float m = 0.f;      // sum of rho - 1 over the quad's fluid nodes
+    float c = 0.f;      // sum of C over the quad's fluid nodes
+    int n = 0;          // fluid nodes of the quad
+    float q = 0.f;      // sum of rho u_x at open pressure-port nodes
+    float qc = 0.f;     // sum of C u_x at open pressure-port nodes
+    bool bad = false;   // a non-finite or non-positive density / non-finite C
+};
+
+// Compensated (Kahan) FP32 running sum of one lane.  GB300 has a narrow FP64
+// pipe, so a lane sums its tiles in FP32 with compensation and FP64 is used
+// only when the block combines its lanes.
+struct KahanF {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - e;
+        const float t = s + y;
+        e = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) - double(e); }
+};
+
+// The lane totals of the four diagnostics.
+struct LaneDiag {
+    KahanF m, c, q, qc;
+    int n = 0;
+    __device__ __forceinline__ void add(const QuadAcc& a)
+    {
+        m.add(a.m);
+        c.add(a.c);
+        if (a.q != 0.f || a.qc != 0.f) {
+            q.add(a.q);
+            qc.add(a.qc);
+        }
+        n += a.n;
+    }
+};
+
+// Halfway bounce-back: a link from a wall returns the node's own
+// post-collision population of the opposite direction (row y of the source
+// buffer).  Only lanes next to a wall load anything here.
+__device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, const float* S, long long P,
+                                            long long oC)
+{
+    unsigned wall = 0;  // union of the wall links of the fluid nodes
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned lb = (lk >> (8 * k)) & 0xFFu;
+        if (lb != kSolid) wall |= lb;
+    }
+    if (!wall) return;
+#pragma unroll
+    for (int i = 1; i <= 8; ++i) {
+        if (wall & (1u << (i - 1))) {
+            const float4 own = ldg4(S + opp(i) * P + oC);
+            const float4 ownc = i <= 4 ? ldg4(S + (9 + opp(i)) * P + oC) : own;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if ((lk >> (8 * k + i - 1)) & 1u) {
+                    at(v[i], k) = at(own, k);
+                    if (i <= 4) at(v[9 + i], k) = at(ownc, k);
+                }
+            }
+        }
+    }
+}
+
+// Completion of an open port node (fluid populations as deviations
+// f_i - w_i).  west: the port receives from -x, so the populations with
+// e_x = +1 are unknown (s = +1); otherwise e_x = -1 (s = -1).  Velocity port:
+// Zou-He with u = (u_x, 0) and the held concentration C_in for the scalar's
+// unknown population.  Pressure port: Zou-He with the prescribed density and
+// zero tangential velocity; the scalar's unknown population keeps its own
+// post-collision value of the previous step (read from the source buffer at
+// index own).  Returns true for a pressure node.
+__device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool west, const RowBC& b,
+                                              const float* S, long long P, long long own)
+{
+    const float s = west ? 1.f : -1.f;
+    const bool velocity = ((b.chan_kind >> 8) & 0xFF) == 0;
+    // populations leaving through the port: e = (-s, 0), (-s, -1), (-s, +1)
+    const float fo_ax = west ? f[3] : f[1];
+    const float fo_dn = west ? f[7] : f[8];
+    const float fo_up = west ? f[6] : f[5];
+    // rho (1 - s u_x) = f0 + f2 + f4 + 2 (leaving) = 1 + Kd in deviations
+    // (the weights of those populations add up to one)
+    const float Kd = f[0] + f[2] + f[4] + 2.f * (fo_ax + fo_dn + fo_up);
+    float jx;  // rho u_x of the node
+    if (velocity) jx = (1.f + Kd) * b.a / (1.f - s * b.a);
+    else jx = s * (b.a - Kd);  // b.a = prescribed rho - 1
+    const float ht = 0.5f * (f[2] - f[4]);
+    const float fi_ax = fo_ax + s * (2.f / 3.f) * jx;
+    const float fi_up = fo_dn - ht + s * (1.f / 6.f) * jx;  // e = (s, +1)
+    const float fi_dn = fo_up + ht + s * (1.f / 6.f) * jx;  // e = (s, -1)
+    if (west) {
+        f[1] = fi_ax;
+        f[5] = fi_up;
+        f[8] = fi_dn;
+    } else {
+        f[3] = fi_ax;
+        f[6] = fi_up;
+        f[7] = fi_dn;
+    }
+    if (velocity) {
+        if (west) g[1] = b.c - (g[0] + g[2] + g[3] + g[4]);
+        else g[3] = b.c - (g[0] + g[1] + g[2] + g[4]);
+        return false;
+    }
+    // do-nothing: the node keeps its own post-collision value
+    if (west) g[1] = __ldg(S + 10 * P + own);
+    else g[3] = __ldg(S + 12 * P + own);
+    return true;
+}
+
+// Free flight (pull) of one lane's four nodes x0..x0+3 with 128-bit loads:
+// v[p] component k = plane p at (x0 + k) - e_i.  The +-1 column shifts move
+// between lanes by shuffle; lane 0 / lane 31 load the one value that comes
+// from the neighbouring segment.  act: this lane holds fluid; ld_w / ld_e:
+// this lane's edge value feeds a fluid neighbour lane.  reverse: pull from
+// (x0 + k) + e_i instead (the transposed free flight of the adjoint).
+template <bool kReverse>
+__device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const float* __restrict__ S, long long P,
+                                          long long oC, long long oS, long long oN, int halo_w, int halo_e,
+                                          bool act, bool ld_w, bool ld_e, int lane)
+{
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int sr = kReverse ? (src_row(p) == 0 ? 0 : 3 - src_row(p)) : src_row(p);
+        const int sc = kReverse ? (src_col(p) == 0 ? 0 : 3 - src_col(p)) : src_col(p);
+        const long long o = p * P + (sr == 0 ? oC : sr == 1 ? oS : oN);
+        const bool ld = sc == 0 ? act : sc == 1 ? ld_w : ld_e;
+        float4 r = ld ? ldg4(S + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sc == 1) {  // from column x - 1
+            float h = 0.f;
+            if (act && lane == 0) h = __ldg(S + o + halo_w);
+            float w = __shfl_up_sync(kFull, r.w, 1);
+            if (lane == 0) w = h;
+            r = make_float4(w, r.x, r.y, r.z);
+        } else if (sc == 2) {  // from column x + 1
+            float h = 0.f;
+            if (act && lane == 31) h = __ldg(S + o + halo_e);
+            float e = __shfl_down_sync(kFull, r.x, 1);
+            if (lane == 31) e = h;
+            r = make_float4(r.y, r.z, r.w, e);
+        }
+        v[p] = r;
+    }
+}
+
+// Open ports, moments and both collisions for the four nodes x0..x0+3 of a
+// row whose port entries are bw (west) and be (east); v holds the streamed
+// populations on entry and the post-collision populations on exit (fluid
+// planes as deviations f_i - w_i).
+__device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, int x0, const RowBC& bw,
+                                             const RowBC& be, const StepArgs& a, const float* S, long long oC,
+                                             QuadAcc& acc)
+{
+    const long long P = a.plane;
+    const bool open_w = bw.x >= 0 && ((a.open_mask >> (bw.chan_kind & 31)) & 1u);
+    const bool open_e = be.x >= 0 && ((a.open_mask >> (be.chan_kind & 31)) & 1u);
+
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned lb = (lk >> (8 * k)) & 0xFFu;
+        const bool fluid = lb != kSolid;
+        float f[9], g[5];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = at(v[i], k);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = at(v[9 + i], k);
+        if (!fluid) {  // solid node: park it at the rest state rho = 1, C = 0
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) g[i] = 0.f;
+        }
+
+        // ---- open valve ports (Zou-He; held concentration / do-nothing) ----
+        const int xk = x0 + k;
+        const bool pw = open_w && bw.x == xk;
+        const bool pe = !pw && open_e && be.x == xk;
+        bool pressure_node = false;
+        if (pw || pe) pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k);
+
+        // ---- moments (Eq. moments) and BGK collision of f, in deviations
+        //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
+        const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const float rho = 1.f + rd;
+        const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        const float inv = 1.f / rho;
+        const float ux = jx * inv, uy = jy * inv;
+        const float usq = 1.5f * (ux * ux + uy * uy);
+        const float wo = a.omega_f;
+        {
+            // f_eq_i - w_i = w_i [rho - 1 + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]
+            const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
+            const float q1 = rho * (4.5f * e1 * e1 - usq), q2 = rho * (4.5f * e2 * e2 - usq);
+            const float q5 = rho * (4.5f * e5 * e5 - usq), q6 = rho * (4.5f * e6 * e6 - usq);
+            const float t1 = 3.f * jx, t2 = 3.f * jy, t5 = t1 + t2, t6 = t2 - t1;
+            f[0] += wo * (kWr * (rd - rho * usq) - f[0]);
+            f[1] += wo * (kWa * (rd + t1 + q1) - f[1]);
+            f[3] += wo * (kWa * (rd - t1 + q1) - f[3]);
+            f[2] += wo * (kWa * (rd + t2 + q2) - f[2]);
+            f[4] += wo * (kWa * (rd - t2 + q2) - f[4]);
+            f[5] += wo * (kWd * (rd + t5 + q5) - f[5]);
+            f[7] += wo * (kWd * (rd - t5 + q5) - f[7]);
+            f[6] += wo * (kWd * (rd + t6 + q6) - f[6]);
+            f[8] += wo * (kWd * (rd - t6 + q6) - f[8]);
+        }
+        // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
+        const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+        {
+            const float wg = a.omega_g;
+            const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
+            // rest equilibrium w0 C formed as the remainder, so that the five
+            // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)
+            g[0] += wg * ((C - 4.f * c1) - g[0]);
+            g[1] += wg * ((c1 + cx) - g[1]);
+            g[3] += wg * ((c1 - cx) - g[3]);
+            g[2] += wg * ((c1 + cy) - g[2]);
+            g[4] += wg * ((c1 - cy) - g[4]);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) at(v[i], k) = f[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) at(v[9 + i], k) = g[i];
+
+        if (fluid) {
+            acc.bad |= !(rho > 0.f && rho < INFINITY) || !(fabsf(C) < INFINITY);
+            acc.m += rd;
+            acc.c += C;
+            ++acc.n;
+            if (pressure_node) {
+                acc.q += jx;  // rho u_x
+                acc.qc += C * ux;
+            }
+        }
+    }
+}
+
+// The block's partial sums of the four diagnostics (FP64 from here on).
+// The cross-block total is formed on demand by diag_finish.
+__device__ __forceinline__ void block_partials(const StepArgs& a, const LaneDiag& d)
+{
+    __shared__ double red[32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    double s0 = warp_sum(double(d.n) + d.m.value());
+    double s1 = warp_sum(d.c.value());
+    double s2 = warp_sum(d.q.value());
+    double s3 = warp_sum(d.qc.value());
+    if (lane == 0) {
+        red[warp][0] = s0;
+        red[warp][1] = s1;
+        red[warp][2] = s2;
+        red[warp][3] = s3;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < wpb; ++w) s += red[w][threadIdx.x];
+        a.partials[blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+}  // namespace
+}  // namespace lbm

@@ -71,6 +71,34 @@ struct StepArgs {
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
 };
 
+// One adjoint step (lbm_adjoint.cu): A(t) from A(t+1) and the state P(t).
+struct AdjointArgs {
+    const float* state;     // P(t), post-collision populations (fluid planes as deviations)
+    const float* adj_next;  // A(t+1) = dJ/dP(t+1), same layout
+    float* adj_mid;         // scratch: adjoint of the completed pre-collision values
+    float* adj_out;         // A(t)
+    const uint8_t* links;
+    const RowBC* rowbc;
+    const uint2* tiles;
+    int n_tiles;
+    int ny;
+    int pitch;
+    long long plane;
+    float omega_f, omega_g, wg0, wg1, inv_cs2g;
+    uint32_t open_mask;     // valve word of step t
+    float* dn;              // 2*ny: do-nothing terms passed from the first launch to the second
+    double* grad_w;         // one running sum of dJ/d(1/tau_g) per block of adjoint_collide
+    double* grad_u;         // 2*ny running sums of dJ/du_in
+    double* grad_c;         // 2*ny running sums of dJ/dC_in
+};
+
+cudaError_t adjoint_occupancy(int block, int* blocks_per_sm);
+cudaError_t launch_adjoint_step(const AdjointArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_adjoint_seed(const float* state, long long plane, int pitch, const int* ox, const int* oy,
+                                const float* target, const float* weight, int n, float* adj, double* J,
+                                cudaStream_t s);
+cudaError_t launch_sum_doubles(const double* v, int n, double* out, cudaStream_t s);
+
 // Dynamic shared memory of the bulk variant, and the attribute it needs.
 size_t bulk_smem_bytes(int stages);
 int bulk_stage_bytes();

@@ -56,6 +56,11 @@ class lbm_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class lbm_objective(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("target", ctypes.c_void_p), ("weight", ctypes.c_void_p)]
+
+
 class lbm_row_port(ctypes.Structure):
     _fields_ = [("x", ctypes.c_int32), ("channel_kind", ctypes.c_int32), ("a", ctypes.c_float),
                 ("c", ctypes.c_float)]
@@ -106,6 +111,8 @@ SIGNATURES = {
     "lbm_clear_error": (ctypes.c_int, [ctypes.c_void_p]),
     "lbm_get_info": (ctypes.c_int, [ctypes.c_void_p, _P(lbm_info)]),
     "lbm_step_noalloc": (ctypes.c_int, [_P(lbm_noalloc_step)]),
+    "lbm_adjoint": (ctypes.c_int, [ctypes.c_void_p, _P(lbm_objective), ctypes.c_int64, ctypes.c_int32,
+                                   _f64p, _f64p, _f64p, _f64p]),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -301,6 +308,24 @@ class Chip:
 
     def clear_error(self):
         self._check(self._lib.lbm_clear_error(self._h))
+
+    def adjoint(self, n_steps, obj_x, obj_y, target, weight=None, ckpt_every=250):
+        """Gradient of J = sum weight (C(x, y) - target)^2 after n_steps
+        (the chip advances by n_steps).  Returns (J, dJ/dtau_c,
+        dJ/du_in (2, ny), dJ/dC_in (2, ny))."""
+        ox = np.ascontiguousarray(obj_x, np.int32)
+        oy = np.ascontiguousarray(obj_y, np.int32)
+        tg = np.ascontiguousarray(target, np.float32)
+        wt = np.ascontiguousarray(np.ones(len(ox)) if weight is None else weight, np.float32)
+        o = lbm_objective(len(ox), ox.ctypes.data, oy.ctypes.data, tg.ctypes.data, wt.ctypes.data)
+        J = ctypes.c_double()
+        dtau = ctypes.c_double()
+        du = np.zeros((2, self.ny))
+        dc = np.zeros((2, self.ny))
+        self._check(self._lib.lbm_adjoint(self._h, ctypes.byref(o), int(n_steps), int(ckpt_every),
+                                          ctypes.byref(J), ctypes.byref(dtau), du.ctypes.data_as(_f64p),
+                                          dc.ctypes.data_as(_f64p)))
+        return J.value, dtau.value, du, dc
 
     def info(self):
         i = lbm_info()
