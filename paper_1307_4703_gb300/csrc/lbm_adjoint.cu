@@ -19,35 +19,36 @@ namespace lbm {
 namespace {
 
 // Transpose of the collision and of the port completion for the four nodes
-// of one lane.  x holds X (fluid planes as deviations), a holds A(t+1) on
-// entry and A* on exit.
-__device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes], float4 (&a)[kPlanes], unsigned lk,
-                                                     int x0, int y, const RowBC& bw, const RowBC& be,
+// of one lane.  x holds X (fluid planes as deviations); A(t+1) is read and
+// A* written one node at a time (fewer live registers than whole quads).
+__device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes], unsigned lk, int x0, int y,
+                                                     long long oC, const RowBC& bw, const RowBC& be,
                                                      const AdjointArgs& A, KahanF& dwg)
 {
+    const long long P = A.plane;
     const bool open_w = bw.x >= 0 && ((A.open_mask >> (bw.chan_kind & 31)) & 1u);
     const bool open_e = be.x >= 0 && ((A.open_mask >> (be.chan_kind & 31)) & 1u);
     const float w = A.omega_f, wgr = A.omega_g;
-    const float cs2 = 1.f / A.inv_cs2g;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const unsigned lb = (lk >> (8 * k)) & 0xFFu;
         float af[9], ag[5];
+        const long long o = oC + k;
         if (lb == kSolid) {
 #pragma unroll
-            for (int i = 0; i < kPlanes; ++i) at(a[i], k) = 0.f;
+            for (int i = 0; i < kPlanes; ++i) A.adj_mid[i * P + o] = 0.f;
             continue;
         }
         float f[9], g[5];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             f[i] = at(x[i], k);
-            af[i] = at(a[i], k);
+            af[i] = __ldg(A.adj_next + i * P + o);
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             g[i] = at(x[9 + i], k);
-            ag[i] = at(a[9 + i], k);
+            ag[i] = __ldg(A.adj_next + (9 + i) * P + o);
         }
         const int xk = x0 + k;
         const bool pw = open_w && bw.x == xk;
@@ -96,7 +97,6 @@ __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes],
                 dw += ag[q] * (c1 * (1.f + eu * A.inv_cs2g) - g[q]);
             }
         }
-        (void)cs2;
         dwg.add(dw);
         float nf[9], ng[5];
 #pragma unroll
@@ -151,9 +151,9 @@ __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes],
             }
         }
 #pragma unroll
-        for (int q = 0; q < 9; ++q) at(a[q], k) = nf[q];
+        for (int q = 0; q < 9; ++q) A.adj_mid[q * P + o] = nf[q];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) at(a[9 + q], k) = ng[q];
+        for (int q = 0; q < 5; ++q) A.adj_mid[(9 + q) * P + o] = ng[q];
     }
 }
 
@@ -222,12 +222,7 @@ __global__ void __launch_bounds__(256) adjoint_collide(const AdjointArgs A)
                 }
             }
         }
-        float4 a[kPlanes];
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) a[p] = ldg4(A.adj_next + p * P + oC);
-        collide_adjoint_quad(x, a, lk, x0, y, bw, be, A, dwg);
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) stg4(A.adj_mid + p * P + oC, a[p]);
+        collide_adjoint_quad(x, lk, x0, y, oC, bw, be, A, dwg);
     }
     block_add(A.grad_w, dwg.value());
 }
