@@ -230,6 +230,31 @@ def _adjoint_ratio(device):
             "definition": "(adjoint call - forward steps) / forward steps"}
 
 
+def _frozen_scalar(chip, prob, steps, stream, peak):
+    """The scalar-only step on stored velocity fields (the paper's own
+    workflow): 48 bytes per fluid node and step (5 populations read and
+    written, 2 velocity components read).  Device time over `steps` steps."""
+    import torch
+    from paper_1307_4703_gb300 import workloads as W
+    fluid = W.fluid_count(prob)
+    for w in sorted(set(prob["states"])):
+        chip.store_velocity(w)  # the current flow field stands in for each valve state
+    chip.scalar_step(10, 2.0)
+    chip.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        chip.scalar_step(1, 2.0)
+    e1.record(stream)
+    stream.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    achieved = fluid * 48 * steps / s / 1e9
+    return {"value": fluid * steps / s / 1e9, "unit": UNIT, "steps": steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "bytes_per_launch": fluid * 48}}
+
+
 def _e2e(prob, steps, device):
     """The same metric through the public C ABI with host buffers: create the
     chip from host arrays, then every step upload the step's valve word, run
@@ -331,6 +356,7 @@ def main():
     achieved = fluid * BYTES_PER_NODE / (ms_per_step / 1e3) / 1e9
     extras = {}
     if not args.skip_extras:
+        extras["frozen_scalar_step"] = _frozen_scalar(chip, prob, min(args.steps, 2000), stream, peak)
         e2e_steps = min(args.steps, 5000)
         e = _e2e(prob, e2e_steps, local)
         e["value"] = aggregate_glups(fluid * e2e_steps, e["seconds"], ws)

@@ -196,6 +196,35 @@ lbm_status lbm_set_populations(lbm_handle h, const float* f, const float* g);
 lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux,
                                 const float* uy, const float* C);
 
+/* ---- Scalar-only steps on stored velocity fields ----
+ *
+ * The paper's workflow (section "Results"): the flow reaches its steady
+ * state quickly and the compound does not act on it, so the stationary
+ * velocity field of each valve state is computed once and the
+ * advection-diffusion solver reads it, with a larger time step for the
+ * scalar; the stored field is multiplied by the ratio of the time steps.
+ * Up to LBM_MAX_FIELDS fields, one per valve word. */
+#define LBM_MAX_FIELDS 8
+
+/* Store the fluid velocity of the current state as the field of valve word
+ * open_mask (replacing an earlier field of that word).  Device memory for a
+ * new field (2 x ny x pitch floats) comes from the handle's allocator. */
+lbm_status lbm_store_velocity(lbm_handle h, uint32_t open_mask);
+
+/* Store a caller's field for valve word open_mask: HOST arrays of nx*ny
+ * floats, row-major; values at solid nodes are ignored. */
+lbm_status lbm_set_velocity_field(lbm_handle h, uint32_t open_mask, const float* ux, const float* uy);
+
+/* Advance only the scalar lattice by n >= 0 steps: step t reads the field
+ * stored for its valve word (lbm_set_valves / lbm_set_valve_schedule)
+ * multiplied by u_scale, with the same scalar ports and walls as lbm_step
+ * (held concentration, do-nothing, no-flux).  The fluid populations do not
+ * change; the step counter advances.  LBM_ERR_STATE (nothing launched) if a
+ * valve word the steps use has no stored field.  Diagnostics: out[1] and
+ * out[3] of lbm_get_diagnostics come from the last scalar step, out[0] and
+ * out[2] stay those of the last coupled step. */
+lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale);
+
 /* Objective of lbm_adjoint: J = sum_k weight[k] (C(x[k], y[k]) - target[k])^2
  * over n fluid nodes, on the state after the last step (for example the
  * chamber's concentration profile against a linear target).  Host arrays,

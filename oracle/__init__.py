@@ -48,6 +48,7 @@ def _load():
         lib.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_uint, d]
         lib.orc_lattice_vectors.argtypes = [P(ctypes.c_int), P(ctypes.c_int), d]
         lib.orc_adjoint_step.argtypes = [ctypes.c_void_p, ctypes.c_uint, d, d, d, d, d, d, d]
+        lib.orc_scalar_step.argtypes = [ctypes.c_void_p, ctypes.c_uint, d, d]
         lib.orc_adjoint.restype = ctypes.c_double
         lib.orc_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_uint), ctypes.c_int,
                                     P(ctypes.c_int), P(ctypes.c_int), d, d, d, d, d]
@@ -149,6 +150,14 @@ class OracleLattice:
         g = np.zeros((self.ny, self.nx, 5))
         self._lib.orc_post_collision(self._h, _dptr(f), _dptr(g))
         return f, g
+
+    def scalar_step(self, open_mask, ux, uy, n=1):
+        """Scalar-only steps with a given (already scaled) velocity field."""
+        ux = np.ascontiguousarray(np.broadcast_to(ux, (self.ny, self.nx)), np.float64)
+        uy = np.ascontiguousarray(np.broadcast_to(uy, (self.ny, self.nx)), np.float64)
+        for _ in range(int(n)):
+            self._lib.orc_scalar_step(self._h, ctypes.c_uint(int(open_mask) & 0xFFFFFFFF), _dptr(ux), _dptr(uy))
+            self.t += 1
 
     def adjoint_step(self, open_mask, S_t, S_t1, af, ag):
         """One reverse step: (af, ag) = dJ/dS_{t+1} -> dJ/dS_t, given the

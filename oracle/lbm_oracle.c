@@ -631,3 +631,52 @@ double orc_adjoint(orc_lattice* L, int n, const unsigned* masks, int n_obj,
     free(fs); free(gs); free(af); free(ag); free(grad);
     return J;
 }
+
+void orc_scalar_step(orc_lattice* L, unsigned open_mask, const double* ux, const double* uy)
+{
+    const int nx = L->nx, ny = L->ny;
+    /* collision with the given velocity (scalar counterpart of Eq. lbequation
+     * with the equilibrium of Eq. cdeequilibrium) */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (!is_fluid(L, x, y)) continue;
+            int c = node(L, x, y);
+            const double* gn = L->g + (size_t)c * 5;
+            double C = scalar_moment(gn);
+            for (int i = 0; i < 5; ++i)
+                L->gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux[c], uy[c])) / L->tau_g;
+        }
+    /* free flight with halfway bounce-back */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (!is_fluid(L, x, y)) continue;
+            int c = node(L, x, y);
+            for (int i = 0; i < 5; ++i) {
+                int xn = x + EX[i], yn = y + EY[i];
+                if (L->periodic) {
+                    xn = (xn + nx) % nx;
+                    yn = (yn + ny) % ny;
+                }
+                if (is_fluid(L, xn, yn)) L->g[node(L, xn, yn) * 5 + i] = L->gp[c * 5 + i];
+                else L->g[c * 5 + OPP[i]] = L->gp[c * 5 + i];
+            }
+        }
+    /* open valves: held concentration at inlets, do-nothing at outlets */
+    for (int p = 0; p < L->n_ports; ++p) {
+        const orc_port* P = &L->ports[p];
+        if (!((open_mask >> P->channel) & 1u)) continue;
+        int g_in = P->side == ORC_WEST ? 1 : 3;
+        for (int y = P->y0; y < P->y1; ++y) {
+            int c = node(L, P->x, y);
+            double* gn = L->g + (size_t)c * 5;
+            if (P->kind == ORC_VELOCITY) {
+                double others = 0.0;
+                for (int i = 0; i < 5; ++i)
+                    if (i != g_in) others += gn[i];
+                gn[g_in] = L->edge_C[P->side * ny + y] - others;
+            } else {
+                gn[g_in] = L->gp[c * 5 + g_in];
+            }
+        }
+    }
+}

@@ -97,6 +97,13 @@ void orc_diagnostics(const orc_lattice* L, unsigned open_mask, double out[4]);
 /* Lattice tables as the oracle uses them (for checks against Eq. lattice). */
 void orc_lattice_vectors(int ex[9], int ey[9], double w[9]);
 
+/* Scalar-only step with a given velocity field (section "Results": the
+ * stationary velocity fields are computed once and the advection-diffusion
+ * solver reads them; the fluid populations do not change).  ux, uy: ny*nx
+ * values already scaled to the scalar's time step.  Same scalar boundary
+ * nodes as orc_step. */
+void orc_scalar_step(orc_lattice* L, unsigned open_mask, const double* ux, const double* uy);
+
 /* ---- Adjoint (reverse-mode derivative of the time step) ----
  *
  * The step maps the pre-collision state S_t = (f, g) to S_{t+1}; its

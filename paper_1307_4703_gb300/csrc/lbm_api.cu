@@ -73,6 +73,11 @@ struct lbm_ctx {
 
     std::string last_error = "no error";
     std::vector<uint8_t> solid;  // host copy of the mask (non-zero = solid)
+    struct Field {
+        uint32_t word;
+        float* u;                    // 2 planes (u_x, u_y) of ny x pitch floats
+    };
+    std::vector<Field> fields;       // stored velocity fields, one per valve word
 
     uint32_t mask_at(int64_t t) const
     {
@@ -878,6 +883,97 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     *J = host[0];
     *dJ_dtau_c = -host[1] / (h->tau_c * h->tau_c);  // d(1/tau_c)/dtau_c = -1/tau_c^2
     return read_err_word(h);
+}
+
+namespace {
+float* field_slot(lbm_ctx* h, uint32_t word)
+{
+    for (auto& f : h->fields)
+        if (f.word == word) return f.u;
+    if (int(h->fields.size()) >= LBM_MAX_FIELDS) return nullptr;
+    float* u = static_cast<float*>(dev_alloc(h, size_t(2) * h->plane * sizeof(float)));
+    if (u) h->fields.push_back({word, u});
+    return u;
+}
+const float* find_field(const lbm_ctx* h, uint32_t word)
+{
+    for (auto& f : h->fields)
+        if (f.word == word) return f.u;
+    return nullptr;
+}
+}  // namespace
+
+lbm_status lbm_store_velocity(lbm_handle h, uint32_t open_mask)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    float* u = field_slot(h, open_mask);
+    if (!u) return fail(h, LBM_ERR_OOM, "no room for the velocity field of valve word %u (at most %d fields)",
+                        open_mask, LBM_MAX_FIELDS);
+    cudaError_t e = lbm::launch_velocity_of_state(h->pop[h->cur], h->links, h->plane, u, u + h->plane, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "velocity kernel launch");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_velocity_field(lbm_handle h, uint32_t open_mask, const float* ux, const float* uy)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (!ux || !uy) return fail(h, LBM_ERR_ARG, "ux or uy is NULL");
+    float* u = field_slot(h, open_mask);
+    if (!u) return fail(h, LBM_ERR_OOM, "no room for the velocity field of valve word %u (at most %d fields)",
+                        open_mask, LBM_MAX_FIELDS);
+    const size_t row = size_t(h->nx) * sizeof(float), pitch = size_t(h->pitch) * sizeof(float);
+    LBM_CUDA(h, cudaMemcpy2DAsync(u, pitch, ux, row, row, size_t(h->ny), cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, cudaMemcpy2DAsync(u + h->plane, pitch, uy, row, row, size_t(h->ny), cudaMemcpyHostToDevice, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
+    if (!std::isfinite(u_scale)) return fail(h, LBM_ERR_ARG, "u_scale = %g is not finite", u_scale);
+    // every valve word the steps use needs a field
+    const std::vector<uint32_t> words = h->schedule.empty() ? std::vector<uint32_t>{h->fixed_mask} : h->schedule;
+    const int64_t reach = h->schedule.empty() ? 1 : std::min<int64_t>(int64_t(words.size()), (n + h->period - 1) / h->period + 1);
+    for (int64_t k = 0; k < reach && n > 0; ++k) {
+        const uint32_t w = h->schedule.empty() ? words[0] : h->mask_at(h->step + k * h->period);
+        if (!find_field(h, w)) return fail(h, LBM_ERR_STATE, "no stored velocity field for valve word %u", w);
+    }
+    lbm::ScalarArgs a{};
+    a.links = h->links;
+    a.rowbc = h->rowbc;
+    a.tiles = h->tiles;
+    a.n_tiles = h->n_tiles;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.u_scale = float(u_scale);
+    a.omega_g = float(1.0 / h->tau_c);
+    a.wg0 = h->wg0;
+    a.wg1 = h->wg1;
+    a.inv_cs2g = h->inv_cs2g;
+    a.partials = h->partials;
+    a.err = h->err;
+    int g = h->cur;  // buffer holding the current scalar planes
+    for (int64_t k = 0; k < n; ++k) {
+        const uint32_t w = h->mask_at(h->step);
+        const float* u = find_field(h, w);
+        if (!u) return fail(h, LBM_ERR_STATE, "no stored velocity field for valve word %u", w);
+        a.src = h->pop[g] + 9 * h->plane;
+        a.dst = h->pop[1 - g] + 9 * h->plane;
+        a.ux = u;
+        a.uy = u + h->plane;
+        a.open_mask = w;
+        cudaError_t e = lbm::launch_scalar_step(a, h->launch.grid, 256, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "scalar step launch");
+        g = 1 - g;
+        ++h->step;
+    }
+    if (g != h->cur)  // bring the scalar planes back next to the fluid planes
+        LBM_CUDA(h, cudaMemcpyAsync(h->pop[h->cur] + 9 * h->plane, h->pop[g] + 9 * h->plane,
+                                    size_t(5) * h->plane * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return pending_numeric(h);
 }
 
 lbm_status lbm_get_step(lbm_handle h, int64_t* t)

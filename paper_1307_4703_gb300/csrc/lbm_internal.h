@@ -99,6 +99,30 @@ cudaError_t launch_adjoint_seed(const float* state, long long plane, int pitch, 
                                 cudaStream_t s);
 cudaError_t launch_sum_doubles(const double* v, int n, double* out, cudaStream_t s);
 
+// One scalar-only step on a stored velocity field (lbm_scalar.cu).
+struct ScalarArgs {
+    const float* src;       // scalar plane 0 (g_0) of the source buffer; planes 1..4 follow
+    float* dst;             // scalar plane 0 of the destination buffer
+    const uint8_t* links;
+    const RowBC* rowbc;
+    const uint2* tiles;
+    int n_tiles;
+    int ny;
+    int pitch;
+    long long plane;
+    const float* ux;        // stored field of this step's valve word, ny x pitch
+    const float* uy;
+    float u_scale;          // ratio of the scalar's time step to the fluid's
+    float omega_g, wg0, wg1, inv_cs2g;
+    uint32_t open_mask;
+    double* partials;       // writes slots 1 and 3 of each block's four
+    unsigned int* err;
+};
+
+cudaError_t launch_scalar_step(const ScalarArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, long long plane, float* ux, float* uy,
+                                     cudaStream_t s);
+
 // Dynamic shared memory of the bulk variant, and the attribute it needs.
 size_t bulk_smem_bytes(int stages);
 int bulk_stage_bytes();

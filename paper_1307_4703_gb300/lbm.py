@@ -113,6 +113,9 @@ SIGNATURES = {
     "lbm_step_noalloc": (ctypes.c_int, [_P(lbm_noalloc_step)]),
     "lbm_adjoint": (ctypes.c_int, [ctypes.c_void_p, _P(lbm_objective), ctypes.c_int64, ctypes.c_int32,
                                    _f64p, _f64p, _f64p, _f64p]),
+    "lbm_store_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    "lbm_set_velocity_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _f32p, _f32p]),
+    "lbm_scalar_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -326,6 +329,17 @@ class Chip:
                                           ctypes.byref(J), ctypes.byref(dtau), du.ctypes.data_as(_f64p),
                                           dc.ctypes.data_as(_f64p)))
         return J.value, dtau.value, du, dc
+
+    def store_velocity(self, open_mask):
+        self._check(self._lib.lbm_store_velocity(self._h, int(open_mask) & 0xFFFFFFFF))
+
+    def set_velocity_field(self, open_mask, ux, uy):
+        a = _f32(np.broadcast_to(ux, (self.ny, self.nx)))
+        b = _f32(np.broadcast_to(uy, (self.ny, self.nx)))
+        self._check(self._lib.lbm_set_velocity_field(self._h, int(open_mask) & 0xFFFFFFFF, _fp(a), _fp(b)))
+
+    def scalar_step(self, n=1, u_scale=1.0):
+        self._check(self._lib.lbm_scalar_step(self._h, int(n), float(u_scale)))
 
     def info(self):
         i = lbm_info()
