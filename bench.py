@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled D2Q9+D2Q5 GLUPS and % HBM roofline; adjoint/forward time ratio"
 UNIT = "GLUPS"
 BYTES_PER_NODE = 112  # 14 FP32 populations read + written per fluid node and step
-KERNEL_SRC = os.path.join(ROOT, "paper_1307_4703_gb300", "csrc", "lbm_kernels.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_1307_4703_gb300", "csrc", f)
+              for f in ("lbm_device.cuh", "lbm_internal.h", "lbm_kernels.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "coupled_step_chip-4096x2048.md")
 
 
@@ -47,6 +48,8 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                    help="step kernel: 0 library default, 1 registers, 2 bulk-copy pipeline")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+                   help="storage of the populations of the timed chip (profiling runs)")
     return p.parse_args()
 
 
@@ -76,8 +79,11 @@ def _peak():
 
 
 def _kernel_hash():
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _traffic(nodes_now):
@@ -255,6 +261,39 @@ def _frozen_scalar(chip, prob, steps, stream, peak):
                          "frac": achieved / peak, "bytes_per_launch": fluid * 48}}
 
 
+def _reduced_precision(prob, steps, stream, device, peak):
+    """The same coupled step with 16-bit population storage (FP16 and BF16
+    deviations, FP32 arithmetic): 56 bytes per fluid node and step.  Device
+    time over `steps` single-step calls after 50 warm-up steps."""
+    import torch
+    from paper_1307_4703_gb300 import lbm, workloads as W
+    fluid = W.fluid_count(prob)
+    out = {}
+    for prec in ("fp16", "bf16"):
+        chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=device, precision=prec)
+        chip.set_valve_schedule(prob["period"], prob["states"])
+        chip.step(50)
+        chip.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            chip.step(1)
+        e1.record(stream)
+        stream.synchronize()
+        s = e0.elapsed_time(e1) / 1e3
+        chip.diagnostics()  # raises on a numeric error flag
+        info = chip.info()
+        chip.close()
+        achieved = info["algorithmic_bytes_per_step"] * steps / s / 1e9
+        out[prec] = {"value": fluid * steps / s / 1e9, "unit": UNIT, "steps": steps,
+                     "us_per_step": s / steps * 1e6,
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak,
+                                  "bytes_per_launch": info["algorithmic_bytes_per_step"]}}
+    return out
+
+
 def _e2e(prob, steps, device):
     """The same metric through the public C ABI with host buffers: create the
     chip from host arrays, then every step upload the step's valve word, run
@@ -321,7 +360,8 @@ def main():
     prob = _problem(args.workload)
     fluid = W.fluid_count(prob)
     stream = torch.cuda.Stream()
-    chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=local, variant=args.variant)
+    chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=local, variant=args.variant,
+                                 precision=args.precision)
     chip.set_valve_schedule(prob["period"], prob["states"])
     info = chip.info()
 
@@ -353,10 +393,11 @@ def main():
     ms = reduce_max(ms, ws)
     ms_per_step = ms / max(args.steps, 1)
     peak, peak_src = _peak()
-    achieved = fluid * BYTES_PER_NODE / (ms_per_step / 1e3) / 1e9
+    achieved = info["algorithmic_bytes_per_step"] / (ms_per_step / 1e3) / 1e9
     extras = {}
     if not args.skip_extras:
         extras["frozen_scalar_step"] = _frozen_scalar(chip, prob, min(args.steps, 2000), stream, peak)
+        extras["reduced_precision_storage"] = _reduced_precision(prob, min(args.steps, 5000), stream, local, peak)
         e2e_steps = min(args.steps, 5000)
         e = _e2e(prob, e2e_steps, local)
         e["value"] = aggregate_glups(fluid * e2e_steps, e["seconds"], ws)
@@ -370,20 +411,22 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%s two-channel gradient chip, FP32 populations" % prob["name"],
+            "config": {"workload": "%s two-channel gradient chip, %s populations"
+                                   % (prob["name"], args.precision.upper()),
                        "nx": prob["nx"], "ny": prob["ny"], "fluid_nodes": fluid,
                        "tau": prob["tau"], "tau_c": prob["tau_c"], "valve_period": prob["period"],
                        "l2": "inputs larger than L2 (%.2f GB of populations per copy)"
-                             % (info["pitch"] * prob["ny"] * 14 * 4 / 1e9),
+                             % (info["pitch"] * prob["ny"] * 14 * (4 if args.precision == "fp32" else 2) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "launch": {"variant": {1: "registers", 2: "bulk-copy pipeline"}[info["variant"]],
                                   "grid": info["grid"], "block": info["block"],
                                   "stages": info["stages"], "tiles": info["n_tiles"]}},
             "all_node_glups": ws * prob["nx"] * prob["ny"] * args.steps / (ms / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": _traffic(fluid),
+                         "frac": achieved / peak,
+                         "traffic": _traffic(fluid) if args.precision == "fp32" else None,
                          "peak_source": "%s (hbm_gbs)" % peak_src,
-                         "bytes_per_launch": fluid * BYTES_PER_NODE},
+                         "bytes_per_launch": info["algorithmic_bytes_per_step"]},
             "gpu_launches": args.steps,
             "clocks": clk,
             "diagnostics": {"mass": d[0], "scalar": d[1]},

@@ -110,11 +110,30 @@ typedef struct {
     int32_t variant;        /* step kernel: 0 = default (2), 1 = registers and warp shuffles,
                                2 = bulk-copy pipeline through shared memory with a producer warp,
                                3 = bulk-copy pipeline in which every warp refills its own stages */
-    int32_t pipeline_stages;/* variants 2, 3: shared-memory stages per computing warp, 0 = default (1);
+    int32_t pipeline_stages;/* variants 2, 3: shared-memory stages per computing warp, 0 = default
+                               (1, or 2 with 16-bit storage);
                                computing warps x stages <= 24 */
     int32_t consumer_warps; /* variants 2, 3: computing warps per block, 0 = default (2: 3, 3: 4),
                                else 1..7 (variant 2) or 1..8 (variant 3) */
+    int32_t precision;      /* storage of the populations (LBM_FP32, LBM_FP16, LBM_BF16), see below */
 } lbm_options;
+
+/* Storage precision.  The paper computes in double precision ("Numerical
+ * Methods"); the library always does the arithmetic of a step in FP32.
+ * LBM_FP32 (default) stores every population in FP32.  LBM_FP16 and LBM_BF16
+ * store 16-bit deviations instead: f_i - w_i for the fluid and
+ * g_i - w_i C_ref with C_ref = 1/2 for the scalar, converted to FP32 on
+ * loading and rounded to nearest on storing; this halves the bytes a step
+ * moves (56 instead of 112 per fluid node) at the cost of a rounding of
+ * every population in every step.  16-bit handles run variants 1 and 2
+ * (variant 3 is rejected with LBM_ERR_ARG) and support
+ * lbm_step, the field, diagnostics and population calls and
+ * lbm_save_state / lbm_load_state (which keep the 16-bit values bit for
+ * bit); lbm_adjoint, lbm_store_velocity, lbm_set_velocity_field and
+ * lbm_scalar_step need FP32 storage and return LBM_ERR_STATE. */
+#define LBM_FP32 0
+#define LBM_FP16 1
+#define LBM_BF16 2
 
 /* Fill *opt with the defaults listed above. */
 void lbm_default_options(lbm_options* opt);
@@ -274,14 +293,17 @@ lbm_status lbm_clear_error(lbm_handle h);
 
 typedef struct {
     int32_t nx, ny;
-    int32_t pitch;          /* floats per stored row (multiple of 128) */
+    int32_t pitch;          /* elements per stored row (multiple of 128) */
     int32_t n_tiles;        /* 128-node row segments that hold fluid */
     int32_t grid, block;    /* step kernel launch shape */
     int32_t variant;        /* 1 registers, 2 bulk-copy pipeline with producer warp, 3 self-refilling warps */
     int32_t stages;         /* shared-memory stages per block (variants 2, 3), 0 otherwise */
     int64_t fluid_nodes;
-    int64_t algorithmic_bytes_per_step;  /* fluid_nodes * 112: 14 FP32 populations read and written */
+    int64_t algorithmic_bytes_per_step;  /* fluid_nodes * 28 * element size: 14 populations read and
+                                            written (112 B for FP32, 56 B for FP16 / BF16) */
     int64_t device_bytes;   /* device memory held by the handle */
+    int32_t precision;      /* LBM_FP32, LBM_FP16 or LBM_BF16 */
+    int32_t reserved;
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_handle h, lbm_info* info);

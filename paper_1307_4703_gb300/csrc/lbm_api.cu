@@ -28,6 +28,7 @@ constexpr int kMaxSchedule = 4096;
 // three computing warps with one stage each, four blocks per SM.
 constexpr int kDefaultConsumers = 3;
 constexpr int kDefaultStagesPerConsumer = 1;
+constexpr int kDefaultStagesPerConsumer16 = 2;  // 16-bit stages are half as large
 constexpr int kDefaultPipeWarps = 4;
 
 struct Alloc {
@@ -49,7 +50,11 @@ struct lbm_ctx {
     void* alloc_user = nullptr;
 
     std::vector<Alloc> allocs;
+    // The two state buffers.  They hold elements of `precision` (FP32, or
+    // 16-bit for FP16 / BF16 storage); the float type serves FP32 paths.
     float* pop[2] = {nullptr, nullptr};
+    int precision = lbm::kFP32;
+    size_t elem = sizeof(float);
     int cur = 0;  // buffer holding the current state
     uint8_t* links = nullptr;
     lbm::RowBC* rowbc = nullptr;
@@ -227,13 +232,20 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     if (opt.max_blocks < 0) return fail(nullptr, LBM_ERR_ARG, "max_blocks = %d < 0", opt.max_blocks);
     if (opt.variant < 0 || opt.variant > 3)
         return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1, 2 or 3", opt.variant);
+    if (opt.precision != LBM_FP32 && opt.precision != LBM_FP16 && opt.precision != LBM_BF16)
+        return fail(nullptr, LBM_ERR_ARG, "precision = %d: use LBM_FP32, LBM_FP16 or LBM_BF16", opt.precision);
+    if (opt.precision != LBM_FP32 && opt.variant == 3)
+        return fail(nullptr, LBM_ERR_ARG, "precision = %d: 16-bit storage runs variants 1 and 2, not 3",
+                    opt.precision);
     const int max_cw = opt.variant == 3 ? 8 : 7;
     if (opt.consumer_warps < 0 || opt.consumer_warps > max_cw)
         return fail(nullptr, LBM_ERR_ARG, "consumer_warps = %d: use 0 or 1..%d", opt.consumer_warps, max_cw);
     {
         const int nc = opt.consumer_warps ? opt.consumer_warps
                                           : opt.variant == 3 ? kDefaultPipeWarps : kDefaultConsumers;
-        const int per = opt.pipeline_stages ? opt.pipeline_stages : kDefaultStagesPerConsumer;
+        const int per = opt.pipeline_stages                ? opt.pipeline_stages
+                        : opt.precision == LBM_FP32 ? kDefaultStagesPerConsumer
+                                                    : kDefaultStagesPerConsumer16;
         if (opt.pipeline_stages < 0 || nc * per > lbm::kMaxStages)
             return fail(nullptr, LBM_ERR_ARG,
                         "pipeline_stages = %d per consumer warp with %d consumer warps: the ring holds at most %d stages",
@@ -348,6 +360,8 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     h->n_tiles = int(tiles.size());
     h->solid.assign(mask, mask + size_t(nx) * ny);
     h->fluid = fluid;
+    h->precision = opt.precision;
+    h->elem = opt.precision == LBM_FP32 ? sizeof(float) : sizeof(uint16_t);
 
     auto bail = [&](lbm_status s) {
         g_create_error = h->last_error;
@@ -367,9 +381,12 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
     lbm::StepLaunch& L = h->launch;
     L.variant = opt.variant == 1 ? lbm::kVariantRegs : opt.variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
+    L.precision = opt.precision;
     if (L.variant == lbm::kVariantBulk) {
         const int nc = opt.consumer_warps ? opt.consumer_warps : kDefaultConsumers;
-        L.stages = nc * (opt.pipeline_stages ? opt.pipeline_stages : kDefaultStagesPerConsumer);
+        L.stages = nc * (opt.pipeline_stages                ? opt.pipeline_stages
+                         : opt.precision == LBM_FP32 ? kDefaultStagesPerConsumer
+                                                     : kDefaultStagesPerConsumer16);
         L.block = 32 * (nc + 1);
         e = lbm::prepare_step_kernels();
         if (e != cudaSuccess) return bail(cuda_fail(h, e, "shared-memory attribute"));
@@ -392,7 +409,7 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     L.grid = std::max(1, std::min(need, per_sm * sms));
     if (opt.max_blocks > 0) L.grid = std::min(L.grid, opt.max_blocks);
 
-    const size_t pop_bytes = size_t(h->plane) * lbm::kPlanes * sizeof(float);
+    const size_t pop_bytes = size_t(h->plane) * lbm::kPlanes * h->elem;
     h->pop[0] = static_cast<float*>(dev_alloc(h, pop_bytes));
     h->pop[1] = static_cast<float*>(dev_alloc(h, pop_bytes));
     h->links = static_cast<uint8_t*>(dev_alloc(h, links.size()));
@@ -417,9 +434,11 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->partials, 0, size_t(h->launch.grid) * 4 * sizeof(double), st);
     if (e == cudaSuccess)
-        e = lbm::launch_init_rest(h->pop[0], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0), st);
+        e = lbm::launch_init_rest(h->pop[0], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0),
+                                  h->precision, st);
     if (e == cudaSuccess)
-        e = lbm::launch_init_rest(h->pop[1], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0), st);
+        e = lbm::launch_init_rest(h->pop[1], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0),
+                                  h->precision, st);
     // the host tables above are pageable: wait so they may go out of scope
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "device initialisation"));
@@ -480,6 +499,10 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     a.inv_cs2g = h->inv_cs2g;
     a.partials = h->partials;
     a.err = h->err;
+    if (h->precision != LBM_FP32) {
+        a.gref0 = h->wg0 * lbm::kCRef;
+        a.gref1 = h->wg1 * lbm::kCRef;
+    }
     for (int64_t k = 0; k < n; ++k) {
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
@@ -528,7 +551,8 @@ lbm_status lbm_clear_error(lbm_handle h)
 lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy, float* C)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
-    cudaError_t e = lbm::launch_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, rho, ux, uy, C, h->stream);
+    cudaError_t e = lbm::launch_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, rho, ux, uy, C, h->wg0,
+                                       h->wg1, h->precision, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel launch");
     return LBM_OK;
 }
@@ -566,29 +590,99 @@ namespace {
 constexpr float kW9[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
                           1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
 
-// Copies of the stored representation, [plane][y][x] on the host.
+// Device temporaries of one call, released in reverse order on every exit.
+struct Scratch {
+    lbm_ctx* h;
+    std::vector<Alloc> items;
+    explicit Scratch(lbm_ctx* ctx) : h(ctx) {}
+    void* get(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        void* p = nullptr;
+        if (h->alloc_fn) {
+            p = h->alloc_fn(bytes, h->alloc_user);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) items.push_back({p, bytes});
+        return p;
+    }
+    ~Scratch()
+    {
+        cudaStreamSynchronize(h->stream);
+        for (auto it = items.rbegin(); it != items.rend(); ++it) {
+            if (h->free_fn) h->free_fn(it->ptr, it->bytes, h->alloc_user);
+            else cudaFree(it->ptr);
+        }
+    }
+};
+
+// The state in its FP32 representation (fluid planes f_i - w_i, scalar planes
+// g_i), [plane][y][x] on the host; 16-bit storage is converted on the device.
 lbm_status raw_out(lbm_ctx* h, float* f, float* g)
 {
     const float* src = h->pop[h->cur];
+    Scratch sc(h);
+    if (h->precision != LBM_FP32) {
+        void* tmp = sc.get(size_t(h->plane) * lbm::kPlanes * sizeof(float));
+        if (!tmp) return fail(h, LBM_ERR_OOM, "no device memory for the FP32 copy of the state");
+        cudaError_t e = lbm::launch_convert(src, tmp, h->plane, h->wg0, h->wg1, h->precision, true, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "conversion kernel launch");
+        src = static_cast<const float*>(tmp);
+    }
     const size_t row = size_t(h->nx) * sizeof(float), pitch = size_t(h->pitch) * sizeof(float);
-    if (f)
-        LBM_CUDA(h, cudaMemcpy2DAsync(f, row, src, pitch, row, size_t(9) * h->ny, cudaMemcpyDeviceToHost, h->stream));
-    if (g)
-        LBM_CUDA(h, cudaMemcpy2DAsync(g, row, src + 9 * h->plane, pitch, row, size_t(5) * h->ny,
-                                      cudaMemcpyDeviceToHost, h->stream));
-    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    cudaError_t e = cudaSuccess;
+    if (f) e = cudaMemcpy2DAsync(f, row, src, pitch, row, size_t(9) * h->ny, cudaMemcpyDeviceToHost, h->stream);
+    if (g && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(g, row, src + 9 * h->plane, pitch, row, size_t(5) * h->ny, cudaMemcpyDeviceToHost,
+                              h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "population read-out");
     return LBM_OK;
 }
 
 lbm_status raw_in(lbm_ctx* h, const float* f, const float* g)
 {
     float* dst = h->pop[h->cur];
+    Scratch sc(h);
+    void* tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (h->precision != LBM_FP32) {
+        // planes that are not given keep their values: start from the state
+        tmp = sc.get(size_t(h->plane) * lbm::kPlanes * sizeof(float));
+        if (!tmp) return fail(h, LBM_ERR_OOM, "no device memory for the FP32 copy of the state");
+        e = lbm::launch_convert(dst, tmp, h->plane, h->wg0, h->wg1, h->precision, true, h->stream);
+        dst = static_cast<float*>(tmp);
+    }
     const size_t row = size_t(h->nx) * sizeof(float), pitch = size_t(h->pitch) * sizeof(float);
-    if (f)
-        LBM_CUDA(h, cudaMemcpy2DAsync(dst, pitch, f, row, row, size_t(9) * h->ny, cudaMemcpyHostToDevice, h->stream));
-    if (g)
-        LBM_CUDA(h, cudaMemcpy2DAsync(dst + 9 * h->plane, pitch, g, row, row, size_t(5) * h->ny,
-                                      cudaMemcpyHostToDevice, h->stream));
+    if (f && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dst, pitch, f, row, row, size_t(9) * h->ny, cudaMemcpyHostToDevice, h->stream);
+    if (g && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dst + 9 * h->plane, pitch, g, row, row, size_t(5) * h->ny, cudaMemcpyHostToDevice,
+                              h->stream);
+    if (tmp && e == cudaSuccess)
+        e = lbm::launch_convert(tmp, h->pop[h->cur], h->plane, h->wg0, h->wg1, h->precision, false, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "population write-in");
+    return LBM_OK;
+}
+
+// The stored elements as they are (elem bytes each), [plane][y][x].
+lbm_status stored_out(lbm_ctx* h, void* out)
+{
+    const size_t row = size_t(h->nx) * h->elem, pitch = size_t(h->pitch) * h->elem;
+    LBM_CUDA(h, cudaMemcpy2DAsync(out, row, h->pop[h->cur], pitch, row, size_t(lbm::kPlanes) * h->ny,
+                                  cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status stored_in(lbm_ctx* h, const void* in)
+{
+    const size_t row = size_t(h->nx) * h->elem, pitch = size_t(h->pitch) * h->elem;
+    LBM_CUDA(h, cudaMemcpy2DAsync(h->pop[h->cur], pitch, in, row, row, size_t(lbm::kPlanes) * h->ny,
+                                  cudaMemcpyHostToDevice, h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
@@ -632,7 +726,8 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux,
     for (int q = 0; q < 4; ++q)
         LBM_CUDA(h, cudaMemcpyAsync(t + q * n, ins[q], n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     cudaError_t e = lbm::launch_init_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, t, t + n,
-                                            t + 2 * n, t + 3 * n, h->wg0, h->wg1, h->inv_cs2g, h->stream);
+                                            t + 2 * n, t + 3 * n, h->wg0, h->wg1, h->inv_cs2g, h->precision,
+                                            h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium kernel launch");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
@@ -646,32 +741,32 @@ struct StateHeader {
     int64_t step;
     int64_t period;
     uint32_t fixed_mask;
-    uint32_t reserved;
+    uint32_t precision;
 };
 }  // namespace
 
 lbm_status lbm_save_state(lbm_handle h, void* buf, size_t* bytes)
 {
     if (check_ctx(h) || !bytes) return fail(h, LBM_ERR_ARG, "bytes is NULL");
-    const size_t pop = size_t(h->nx) * h->ny * lbm::kPlanes * sizeof(float);
+    const size_t pop = size_t(h->nx) * h->ny * lbm::kPlanes * h->elem;
     const size_t need = sizeof(StateHeader) + h->schedule.size() * 4 + pop;
     if (!buf) {
         *bytes = need;
         return LBM_OK;
     }
     if (*bytes < need) return fail(h, LBM_ERR_ARG, "state buffer of %zu bytes, need %zu", *bytes, need);
-    StateHeader hd{kStateMagic, h->nx, h->ny, int32_t(h->schedule.size()), h->step, h->period, h->fixed_mask, 0};
+    StateHeader hd{kStateMagic, h->nx,        h->ny, int32_t(h->schedule.size()), h->step, h->period,
+                   h->fixed_mask, uint32_t(h->precision)};
     char* p = static_cast<char*>(buf);
     std::memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
     if (!h->schedule.empty()) std::memcpy(p, h->schedule.data(), h->schedule.size() * 4);
     p += h->schedule.size() * 4;
     // the stored representation, bit for bit (the buffer may be unaligned)
-    const size_t n = size_t(h->nx) * h->ny;
-    std::vector<float> stored(n * lbm::kPlanes);
-    lbm_status s = raw_out(h, stored.data(), stored.data() + 9 * n);
+    std::vector<uint8_t> stored(pop);
+    lbm_status s = stored_out(h, stored.data());
     if (s != LBM_OK) return s;
-    std::memcpy(p, stored.data(), stored.size() * sizeof(float));
+    std::memcpy(p, stored.data(), stored.size());
     *bytes = need;
     return LBM_OK;
 }
@@ -683,19 +778,19 @@ lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes)
     if (bytes < sizeof(hd)) return fail(h, LBM_ERR_ARG, "state buffer too short");
     std::memcpy(&hd, buf, sizeof(hd));
     if (hd.magic != kStateMagic || hd.nx != h->nx || hd.ny != h->ny || hd.n_sched < 0 ||
-        hd.n_sched > kMaxSchedule || (hd.n_sched > 0 && hd.period < 1))
+        hd.n_sched > kMaxSchedule || (hd.n_sched > 0 && hd.period < 1) || hd.precision != uint32_t(h->precision))
         return fail(h, LBM_ERR_ARG, "state buffer does not match this chip");
     const size_t n = size_t(h->nx) * h->ny;
-    const size_t need = sizeof(hd) + size_t(hd.n_sched) * 4 + n * lbm::kPlanes * sizeof(float);
+    const size_t need = sizeof(hd) + size_t(hd.n_sched) * 4 + n * lbm::kPlanes * h->elem;
     if (bytes < need) return fail(h, LBM_ERR_ARG, "state buffer of %zu bytes, need %zu", bytes, need);
     const char* p = static_cast<const char*>(buf) + sizeof(hd);
     std::vector<uint32_t> sched(size_t(hd.n_sched));
     if (hd.n_sched) std::memcpy(sched.data(), p, sched.size() * 4);
     p += sched.size() * 4;
-    // the populations may not be 4-byte aligned inside a caller's buffer
-    std::vector<float> pop(n * lbm::kPlanes);
-    std::memcpy(pop.data(), p, pop.size() * sizeof(float));
-    lbm_status s = raw_in(h, pop.data(), pop.data() + 9 * n);
+    // the populations may not be aligned inside a caller's buffer
+    std::vector<uint8_t> pop(n * lbm::kPlanes * h->elem);
+    std::memcpy(pop.data(), p, pop.size());
+    lbm_status s = stored_in(h, pop.data());
     if (s != LBM_OK) return s;
     h->step = hd.step;
     h->period = hd.period;
@@ -705,39 +800,13 @@ lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes)
 }
 
 namespace {
-// Device temporaries of one call, released in reverse order on every exit.
-struct Scratch {
-    lbm_ctx* h;
-    std::vector<Alloc> items;
-    explicit Scratch(lbm_ctx* ctx) : h(ctx) {}
-    void* get(size_t bytes)
-    {
-        bytes = (bytes + 255) & ~size_t(255);
-        void* p = nullptr;
-        if (h->alloc_fn) {
-            p = h->alloc_fn(bytes, h->alloc_user);
-        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-        }
-        if (p) items.push_back({p, bytes});
-        return p;
-    }
-    ~Scratch()
-    {
-        cudaStreamSynchronize(h->stream);
-        for (auto it = items.rbegin(); it != items.rend(); ++it) {
-            if (h->free_fn) h->free_fn(it->ptr, it->bytes, h->alloc_user);
-            else cudaFree(it->ptr);
-        }
-    }
-};
 }  // namespace
 
 lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_t K, double* J,
                        double* dJ_dtau_c, double* dJ_du_in, double* dJ_dC_in)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
+    if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_adjoint");
     if (!obj || !J || !dJ_dtau_c) return fail(h, LBM_ERR_ARG, "objective, J or dJ_dtau_c is NULL");
     if (n < 1 || K < 1) return fail(h, LBM_ERR_ARG, "n_steps = %lld and ckpt_every = %d must be >= 1", (long long)n, K);
     if (obj->n < 1 || !obj->x || !obj->y || !obj->target || !obj->weight)
@@ -906,6 +975,7 @@ const float* find_field(const lbm_ctx* h, uint32_t word)
 lbm_status lbm_store_velocity(lbm_handle h, uint32_t open_mask)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
+    if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_store_velocity");
     float* u = field_slot(h, open_mask);
     if (!u) return fail(h, LBM_ERR_OOM, "no room for the velocity field of valve word %u (at most %d fields)",
                         open_mask, LBM_MAX_FIELDS);
@@ -917,6 +987,7 @@ lbm_status lbm_store_velocity(lbm_handle h, uint32_t open_mask)
 lbm_status lbm_set_velocity_field(lbm_handle h, uint32_t open_mask, const float* ux, const float* uy)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
+    if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_set_velocity_field");
     if (!ux || !uy) return fail(h, LBM_ERR_ARG, "ux or uy is NULL");
     float* u = field_slot(h, open_mask);
     if (!u) return fail(h, LBM_ERR_OOM, "no room for the velocity field of valve word %u (at most %d fields)",
@@ -931,6 +1002,7 @@ lbm_status lbm_set_velocity_field(lbm_handle h, uint32_t open_mask, const float*
 lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
+    if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_scalar_step");
     if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
     if (!std::isfinite(u_scale)) return fail(h, LBM_ERR_ARG, "u_scale = %g is not finite", u_scale);
     // every valve word the steps use needs a field
@@ -995,8 +1067,10 @@ lbm_status lbm_get_info(lbm_handle h, lbm_info* info)
     info->variant = h->launch.variant;
     info->stages = h->launch.stages;
     info->fluid_nodes = h->fluid;
-    info->algorithmic_bytes_per_step = h->fluid * 112;
+    info->algorithmic_bytes_per_step = h->fluid * 28 * (long long)h->elem;
     info->device_bytes = h->device_bytes;
+    info->precision = h->precision;
+    info->reserved = 0;
     return LBM_OK;
 }
 

@@ -8,6 +8,9 @@
 #include <cmath>
 #include <cstddef>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -60,6 +63,99 @@ __device__ __forceinline__ float& at(float4& v, int k)
 __device__ __forceinline__ float at(const float4& v, int k)
 {
     return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// Storage of the populations.  FP32 keeps them as they are (fluid planes as
+// f_i - w_i, scalar planes as g_i).  FP16 and BF16 hold deviations from a
+// reference: the fluid planes the same f_i - w_i, the scalar planes
+// g_i - w_i C_ref; the codec adds the plane's offset on loading and
+// subtracts it on storing, so all arithmetic stays FP32.
+template <typename T>
+struct Codec;
+
+template <>
+struct Codec<float> {
+    static __device__ __forceinline__ float4 ld4(const float* p, float) { return ldg4(p); }
+    static __device__ __forceinline__ float ld1(const float* p, float) { return __ldg(p); }
+    static __device__ __forceinline__ void st4(float* p, const float4& v, float) { stg4(p, v); }
+    static __device__ __forceinline__ void st1(float* p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float4 lds4(const float* p, float) { return *reinterpret_cast<const float4*>(p); }
+    static __device__ __forceinline__ float lds1(const float* p, float) { return *p; }
+};
+
+template <>
+struct Codec<__half> {
+    static __device__ __forceinline__ float4 ld4(const __half* p, float off)
+    {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+    }
+    static __device__ __forceinline__ float ld1(const __half* p, float off) { return __half2float(__ldg(p)) + off; }
+    static __device__ __forceinline__ void st4(__half* p, const float4& v, float off)
+    {
+        const __half2 a = __floats2half2_rn(v.x - off, v.y - off);
+        const __half2 b = __floats2half2_rn(v.z - off, v.w - off);
+        uint2 r;
+        r.x = *reinterpret_cast<const unsigned*>(&a);
+        r.y = *reinterpret_cast<const unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = r;
+    }
+    static __device__ __forceinline__ void st1(__half* p, float v, float off) { *p = __float2half_rn(v - off); }
+    static __device__ __forceinline__ float4 lds4(const __half* p, float off)
+    {
+        const uint2 r = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+    }
+    static __device__ __forceinline__ float lds1(const __half* p, float off) { return __half2float(*p) + off; }
+};
+
+template <>
+struct Codec<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 ld4(const __nv_bfloat16* p, float off)
+    {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+    }
+    static __device__ __forceinline__ float ld1(const __nv_bfloat16* p, float off)
+    {
+        return __bfloat162float(__ldg(p)) + off;
+    }
+    static __device__ __forceinline__ void st4(__nv_bfloat16* p, const float4& v, float off)
+    {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x - off, v.y - off);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v.z - off, v.w - off);
+        uint2 r;
+        r.x = *reinterpret_cast<const unsigned*>(&a);
+        r.y = *reinterpret_cast<const unsigned*>(&b);
+        *reinterpret_cast<uint2*>(p) = r;
+    }
+    static __device__ __forceinline__ void st1(__nv_bfloat16* p, float v, float off)
+    {
+        *p = __float2bfloat16_rn(v - off);
+    }
+    static __device__ __forceinline__ float4 lds4(const __nv_bfloat16* p, float off)
+    {
+        const uint2 r = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+    }
+    static __device__ __forceinline__ float lds1(const __nv_bfloat16* p, float off)
+    {
+        return __bfloat162float(*p) + off;
+    }
+};
+
+// Offset of plane p in 16-bit storage (0 for the fluid planes).
+__device__ __forceinline__ float plane_offset(int p, float gref0, float gref1)
+{
+    return p < 9 ? 0.f : p == 9 ? gref0 : gref1;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -172,8 +268,9 @@ struct LaneDiag {
 // Halfway bounce-back: a link from a wall returns the node's own
 // post-collision population of the opposite direction (row y of the source
 // buffer).  Only lanes next to a wall load anything here.
-__device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, const float* S, long long P,
-                                            long long oC)
+template <typename T>
+__device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, const T* S, long long P,
+                                            long long oC, float gref1 = 0.f)
 {
     unsigned wall = 0;  // union of the wall links of the fluid nodes
 #pragma unroll
@@ -185,8 +282,8 @@ __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, c
 #pragma unroll
     for (int i = 1; i <= 8; ++i) {
         if (wall & (1u << (i - 1))) {
-            const float4 own = ldg4(S + opp(i) * P + oC);
-            const float4 ownc = i <= 4 ? ldg4(S + (9 + opp(i)) * P + oC) : own;
+            const float4 own = Codec<T>::ld4(S + opp(i) * P + oC, 0.f);
+            const float4 ownc = i <= 4 ? Codec<T>::ld4(S + (9 + opp(i)) * P + oC, gref1) : own;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if ((lk >> (8 * k + i - 1)) & 1u) {
@@ -206,8 +303,9 @@ __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, c
 // zero tangential velocity; the scalar's unknown population keeps its own
 // post-collision value of the previous step (read from the source buffer at
 // index own).  Returns true for a pressure node.
+template <typename T>
 __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool west, const RowBC& b,
-                                              const float* S, long long P, long long own)
+                                              const T* S, long long P, long long own, float gref1 = 0.f)
 {
     const float s = west ? 1.f : -1.f;
     const bool velocity = ((b.chan_kind >> 8) & 0xFF) == 0;
@@ -240,8 +338,8 @@ __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool
         return false;
     }
     // do-nothing: the node keeps its own post-collision value
-    if (west) g[1] = __ldg(S + 10 * P + own);
-    else g[3] = __ldg(S + 12 * P + own);
+    if (west) g[1] = Codec<T>::ld1(S + 10 * P + own, gref1);
+    else g[3] = Codec<T>::ld1(S + 12 * P + own, gref1);
     return true;
 }
 
@@ -251,10 +349,11 @@ __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool
 // from the neighbouring segment.  act: this lane holds fluid; ld_w / ld_e:
 // this lane's edge value feeds a fluid neighbour lane.  reverse: pull from
 // (x0 + k) + e_i instead (the transposed free flight of the adjoint).
-template <bool kReverse>
-__device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const float* __restrict__ S, long long P,
+template <bool kReverse, typename T>
+__device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const T* __restrict__ S, long long P,
                                           long long oC, long long oS, long long oN, int halo_w, int halo_e,
-                                          bool act, bool ld_w, bool ld_e, int lane)
+                                          bool act, bool ld_w, bool ld_e, int lane, float gref0 = 0.f,
+                                          float gref1 = 0.f)
 {
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
@@ -262,16 +361,17 @@ __device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const float* __r
         const int sc = kReverse ? (src_col(p) == 0 ? 0 : 3 - src_col(p)) : src_col(p);
         const long long o = p * P + (sr == 0 ? oC : sr == 1 ? oS : oN);
         const bool ld = sc == 0 ? act : sc == 1 ? ld_w : ld_e;
-        float4 r = ld ? ldg4(S + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float off = plane_offset(p, gref0, gref1);
+        float4 r = ld ? Codec<T>::ld4(S + o, off) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (sc == 1) {  // from column x - 1
             float h = 0.f;
-            if (act && lane == 0) h = __ldg(S + o + halo_w);
+            if (act && lane == 0) h = Codec<T>::ld1(S + o + halo_w, off);
             float w = __shfl_up_sync(kFull, r.w, 1);
             if (lane == 0) w = h;
             r = make_float4(w, r.x, r.y, r.z);
         } else if (sc == 2) {  // from column x + 1
             float h = 0.f;
-            if (act && lane == 31) h = __ldg(S + o + halo_e);
+            if (act && lane == 31) h = Codec<T>::ld1(S + o + halo_e, off);
             float e = __shfl_down_sync(kFull, r.x, 1);
             if (lane == 31) e = h;
             r = make_float4(r.y, r.z, r.w, e);
@@ -284,8 +384,9 @@ __device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const float* __r
 // row whose port entries are bw (west) and be (east); v holds the streamed
 // populations on entry and the post-collision populations on exit (fluid
 // planes as deviations f_i - w_i).
+template <typename T>
 __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, int x0, const RowBC& bw,
-                                             const RowBC& be, const StepArgs& a, const float* S, long long oC,
+                                             const RowBC& be, const StepArgs& a, const T* S, long long oC,
                                              QuadAcc& acc)
 {
     const long long P = a.plane;
@@ -313,7 +414,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         const bool pw = open_w && bw.x == xk;
         const bool pe = !pw && open_e && be.x == xk;
         bool pressure_node = false;
-        if (pw || pe) pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k);
+        if (pw || pe) pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k, a.gref1);
 
         // ---- moments (Eq. moments) and BGK collision of f, in deviations
         //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----

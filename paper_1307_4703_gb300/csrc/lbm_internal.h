@@ -36,12 +36,15 @@ constexpr int kBulkMaxThreads = 256;        // bulk variant: at most 7 consumer 
 constexpr int kMaxStages = 24;              // bulk variant: largest shared-memory ring
 
 enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3 };
+enum Precision { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+constexpr float kCRef = 0.5f;  // reference concentration of 16-bit scalar storage
 
 struct StepLaunch {
     int variant;  // kVariantRegs, kVariantBulk or kVariantPipe
     int grid;
     int block;
     int stages;   // shared-memory stages per block (computing warps x stages per warp)
+    int precision = kFP32;  // storage of the populations; 16-bit runs the register variant
 };
 
 struct RowBC {
@@ -69,6 +72,7 @@ struct StepArgs {
     uint32_t open_mask;     // valve word of this step
     double* partials;       // 4 diagnostics partial sums per block (scratch)
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
+    float gref0, gref1;     // 16-bit storage: offsets w_0 C_ref and w_1 C_ref of the scalar planes
 };
 
 // One adjoint step (lbm_adjoint.cu): A(t) from A(t+1) and the state P(t).
@@ -124,8 +128,8 @@ cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, lon
                                      cudaStream_t s);
 
 // Dynamic shared memory of the bulk variant, and the attribute it needs.
-size_t bulk_smem_bytes(int stages);
-int bulk_stage_bytes();
+size_t bulk_smem_bytes(int stages, int precision = 0);
+int bulk_stage_bytes(int precision = 0);
 cudaError_t prepare_step_kernels();
 cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s);
 // out[0..3] = sum of the n_blocks x 4 block partials, in a fixed order.
@@ -133,18 +137,24 @@ cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out
 cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm);
 
 // Every node (fluid and solid, padding included) to the rest equilibrium
-// of rho0 and C0.
-cudaError_t launch_init_rest(float* pop, int ny, int pitch, float rho0, float wg0, float wg1,
-                             float C0, cudaStream_t s);
+// of rho0 and C0.  `pop` holds elements of the given precision.
+cudaError_t launch_init_rest(void* pop, int ny, int pitch, float rho0, float wg0, float wg1,
+                             float C0, int precision, cudaStream_t s);
 
 // Fluid nodes to the equilibrium of fields given row-major [y][x] (nx per row).
-cudaError_t launch_init_fields(float* pop, const uint8_t* links, int nx, int ny, int pitch,
+cudaError_t launch_init_fields(void* pop, const uint8_t* links, int nx, int ny, int pitch,
                                const float* rho, const float* ux, const float* uy, const float* C,
-                               float wg0, float wg1, float inv_cs2g, cudaStream_t s);
+                               float wg0, float wg1, float inv_cs2g, int precision, cudaStream_t s);
 
 // Moments of the stored populations into row-major [y][x] arrays (any may be
 // null); solid nodes give 0.
-cudaError_t launch_fields(const float* pop, const uint8_t* links, int nx, int ny, int pitch,
-                          float* rho, float* ux, float* uy, float* C, cudaStream_t s);
+cudaError_t launch_fields(const void* pop, const uint8_t* links, int nx, int ny, int pitch,
+                          float* rho, float* ux, float* uy, float* C, float wg0, float wg1, int precision,
+                          cudaStream_t s);
+
+// 16-bit storage <-> the FP32 representation (fluid planes f_i - w_i, scalar
+// planes g_i), element by element over n_elems = 14 * ny * pitch.
+cudaError_t launch_convert(const void* src, void* dst, long long plane, float wg0, float wg1, int precision,
+                           bool to_fp32, cudaStream_t s);
 
 }  // namespace lbm

@@ -27,9 +27,11 @@
 //                      bandwidth-bound stream needs.
 //   coupled_step_regs  each lane loads its quads with 128-bit loads into
 //                      registers; the +-1 column shifts travel between lanes
-//                      by warp shuffle.
-// All share the per-node arithmetic of lbm_device.cuh and give identical
-// results.
+//                      by warp shuffle.  Instantiated for FP32 storage and for
+//                      FP16 / BF16 storage (64-bit loads of four 16-bit
+//                      deviations, FP32 arithmetic); so is the bulk variant.
+// All share the per-node arithmetic of lbm_device.cuh; the FP32 variants give
+// identical results.
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -60,13 +62,15 @@ __global__ void diag_finish(const double* partials, int n_blocks, double* out)
 // ---------------------------------------------------------------------------
 // Variant 1: registers and warp shuffles
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     const long long P = a.plane;
-    const float* __restrict__ S = a.src;
+    const T* __restrict__ S = reinterpret_cast<const T*>(a.src);
+    T* __restrict__ D = reinterpret_cast<T*>(a.dst);
 
     LaneDiag diag;
     bool bad = false;
@@ -99,15 +103,16 @@ __global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
 
         // ---- free flight (pull): v[p] component k = plane p at (x0+k) - e ----
         float4 v[kPlanes];
-        pull_quad<false>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
+        pull_quad<false>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane, a.gref0, a.gref1);
         if (act) {
-            bounce_back(v, lk, S, P, oC);
+            bounce_back(v, lk, S, P, oC, a.gref1);
             const RowBC bw = a.rowbc[y];
             const RowBC be = a.rowbc[a.ny + y];
             QuadAcc q;
             collide_quad(v, lk, x0, bw, be, a, S, oC, q);
 #pragma unroll
-            for (int p = 0; p < kPlanes; ++p) stg4(a.dst + p * P + oC, v[p]);
+            for (int p = 0; p < kPlanes; ++p)
+                Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
             bad |= q.bad;
             diag.add(q);
         }
@@ -121,36 +126,51 @@ __global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
 // Variant 2: bulk-copy pipeline through shared memory
 // ---------------------------------------------------------------------------
 // One staged tile: the 14 plane rows the tile pulls from, each with a
-// 4-float halo on both sides (so that every copy starts on a 16-byte
-// boundary), the tile's 128 wall-link bytes, the port entries of its row and
-// the tile's table entry.
-struct __align__(16) Stage {
-    float pl[kPlanes][kRowFloats];
+// 16-byte halo on both sides (4 FP32 or 8 16-bit elements, so that every copy
+// starts on a 16-byte boundary), the tile's 128 wall-link bytes, the port
+// entries of its row and the tile's table entry.
+template <typename T>
+struct __align__(16) StageT {
+    static constexpr int kHalo = 16 / int(sizeof(T));  // elements per 16 bytes
+    T pl[kPlanes][kTileNodes + 2 * kHalo];
     unsigned links[kTileNodes / 4];
     RowBC bc[2];
     uint2 tile;
     uint2 pad;
 };
-static_assert(sizeof(Stage) % 16 == 0, "stage size must keep 16-byte alignment");
+using Stage = StageT<float>;
+static_assert(sizeof(Stage) % 16 == 0 && sizeof(StageT<__half>) % 16 == 0,
+              "stage size must keep 16-byte alignment");
 static_assert(offsetof(Stage, links) % 16 == 0 && offsetof(Stage, bc) % 16 == 0, "bulk-copy targets");
+static_assert(offsetof(StageT<__half>, links) % 16 == 0 && offsetof(StageT<__half>, bc) % 16 == 0,
+              "bulk-copy targets");
+static_assert(sizeof(StageT<__half>) == sizeof(StageT<__nv_bfloat16>), "16-bit stages");
 
 // Stage ring: consumer warp c owns stages [c * per, (c + 1) * per) and takes
 // the block's tiles c, c + nc, c + 2 nc, ...; its k-th tile goes to stage
 // c * per + k % per as that stage's use k / per.  Every stage is therefore
 // filled and drained in order by one producer and one consumer, so the
 // parity waits on its two mbarriers never skip a phase.
+//
+// Copies must start and end on 16-byte boundaries: a row's copied span is
+// widened to whole multiples of Q = 16 / sizeof(T) elements (4 FP32 or 8
+// 16-bit), and the shifted planes take Q more on each side.
+template <typename T>
 __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const StepArgs a, int per)
 {
+    using StageX = StageT<T>;
+    constexpr int Q = StageX::kHalo;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nc = (blockDim.x >> 5) - 1;  // consumer warps; the last warp produces
     const int n_stages = nc * per;
-    Stage* st = reinterpret_cast<Stage*>(smem);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(n_stages) * sizeof(Stage));
+    StageX* st = reinterpret_cast<StageX*>(smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(n_stages) * sizeof(StageX));
     uint64_t* empty = full + n_stages;
     const long long P = a.plane;
-    const float* __restrict__ S = a.src;
+    const T* __restrict__ S = reinterpret_cast<const T*>(a.src);
+    T* __restrict__ D = reinterpret_cast<T*>(a.dst);
     const int G = int(gridDim.x);
     // this block's tiles: blockIdx.x, blockIdx.x + G, ...
     const int n_items = int(blockIdx.x) < a.n_tiles ? (a.n_tiles - 1 - int(blockIdx.x)) / G + 1 : 0;
@@ -186,16 +206,18 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
                     const int y = int(tile.x >> kSegBits);
                     const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
                     const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
-                    // columns of the lanes that hold fluid, and one quad more on
-                    // each side for the planes that pull from x -+ 1
-                    const int us = x0 + 4 * q0, ue = x0 + 4 * q1 + 4;
-                    const int ss = us - 4 > 0 ? us - 4 : 0;
-                    const int se = ue + 4 < a.pitch ? ue + 4 : a.pitch;
+                    // columns of the lanes that hold fluid (widened to whole
+                    // 16-byte units), and one unit more on each side for the
+                    // planes that pull from x -+ 1
+                    const int us = x0 + ((4 * q0) & ~(Q - 1));
+                    const int ue = x0 + ((4 * q1 + 4 + Q - 1) & ~(Q - 1));
+                    const int ss = us - Q > 0 ? us - Q : 0;
+                    const int se = ue + Q < a.pitch ? ue + Q : a.pitch;
                     const long long rC = (long long)y * a.pitch;
                     const long long rS = (long long)(y > 0 ? y - 1 : y) * a.pitch;
                     const long long rN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch;
-                    const uint32_t bytes =
-                        uint32_t(6 * (ue - us) + 8 * (se - ss)) * 4u + kTileNodes + 2 * sizeof(RowBC);
+                    const uint32_t bytes = uint32_t(6 * (ue - us) + 8 * (se - ss)) * uint32_t(sizeof(T)) +
+                                           kTileNodes + 2 * sizeof(RowBC);
                     st[s].tile = tile;  // ordered before the consumer by the arrive below
                     mbar_arrive_expect_tx(&full[s], bytes);
 #pragma unroll
@@ -203,7 +225,8 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
                         const long long r = src_row(p) == 0 ? rC : src_row(p) == 1 ? rS : rN;
                         const int b = src_col(p) == 0 ? us : ss;
                         const int e = src_col(p) == 0 ? ue : se;
-                        bulk_g2s(&st[s].pl[p][b - x0 + 4], S + p * P + r + b, uint32_t(e - b) * 4u, &full[s]);
+                        bulk_g2s(&st[s].pl[p][b - x0 + Q], S + p * P + r + b, uint32_t(e - b) * uint32_t(sizeof(T)),
+                                 &full[s]);
                     }
                     bulk_g2s(st[s].links, a.links + rC + x0, kTileNodes, &full[s]);
                     bulk_g2s(&st[s].bc[0], a.rowbc + y, sizeof(RowBC), &full[s]);
@@ -228,7 +251,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
                 if (lane == 0) atomicOr(a.err, 2u);
                 break;
             }
-            const Stage& sg = st[s];
+            const StageX& sg = st[s];
             const uint2 tile = sg.tile;
             const int y = int(tile.x >> kSegBits);
             const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
@@ -241,21 +264,23 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
             if (act) {
 #pragma unroll
                 for (int p = 0; p < kPlanes; ++p) {
-                    const float* row = sg.pl[p] + 4 * lane;
-                    const float4 c = *reinterpret_cast<const float4*>(row + 4);
+                    const T* row = sg.pl[p] + 4 * lane;
+                    const float off = plane_offset(p, a.gref0, a.gref1);
+                    const float4 c = Codec<T>::lds4(row + Q, off);
                     if (src_col(p) == 0) v[p] = c;
-                    else if (src_col(p) == 1) v[p] = make_float4(row[3], c.x, c.y, c.z);
-                    else v[p] = make_float4(c.y, c.z, c.w, row[8]);
+                    else if (src_col(p) == 1) v[p] = make_float4(Codec<T>::lds1(row + Q - 1, off), c.x, c.y, c.z);
+                    else v[p] = make_float4(c.y, c.z, c.w, Codec<T>::lds1(row + Q + 4, off));
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be refilled
             if (act) {
-                bounce_back(v, lk, S, P, oC);
+                bounce_back(v, lk, S, P, oC, a.gref1);
                 QuadAcc q;
                 collide_quad(v, lk, x0, bw, be, a, S, oC, q);
 #pragma unroll
-                for (int p = 0; p < kPlanes; ++p) stg4(a.dst + p * P + oC, v[p]);
+                for (int p = 0; p < kPlanes; ++p)
+                    Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
                 bad |= q.bad;
                 diag.add(q);
             }
@@ -400,7 +425,9 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
 // ---------------------------------------------------------------------------
 // Set-up and read-out kernels
 // ---------------------------------------------------------------------------
-__global__ void init_rest(float* pop, long long plane, float rho0, float wg0, float wg1, float C0)
+template <typename T>
+__global__ void init_rest(T* pop, long long plane, float rho0, float wg0, float wg1, float C0, float gref0,
+                          float gref1)
 {
     const long long n = plane * kPlanes;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -409,13 +436,14 @@ __global__ void init_rest(float* pop, long long plane, float rho0, float wg0, fl
         float w;  // f is stored as f_i - w_i
         if (p < 9) w = (p == 0 ? kWr : p <= 4 ? kWa : kWd) * (rho0 - 1.f);
         else w = (p == 9 ? wg0 : wg1) * C0;
-        pop[e] = w;
+        Codec<T>::st1(pop + e, w, plane_offset(p, gref0, gref1));
     }
 }
 
-__global__ void init_fields(float* pop, const uint8_t* links, int nx, int ny, int pitch,
+template <typename T>
+__global__ void init_fields(T* pop, const uint8_t* links, int nx, int ny, int pitch,
                             const float* rho_in, const float* ux_in, const float* uy_in,
-                            const float* C_in, float wg0, float wg1, float inv_cs2g)
+                            const float* C_in, float wg0, float wg1, float inv_cs2g, float gref0, float gref1)
 {
     const long long P = (long long)ny * pitch;
     for (int y = blockIdx.y; y < ny; y += gridDim.y) {
@@ -430,16 +458,17 @@ __global__ void init_fields(float* pop, const uint8_t* links, int nx, int ny, in
 #pragma unroll
         for (int i = 0; i < 9; ++i) {  // f_eq_i - w_i
             const float w = i == 0 ? kWr : i <= 4 ? kWa : kWd;
-            pop[i * P + o] = w * ((rho - 1.f) + rho * (3.f * e[i] + 4.5f * e[i] * e[i] - usq));
+            Codec<T>::st1(pop + i * P + o, w * ((rho - 1.f) + rho * (3.f * e[i] + 4.5f * e[i] * e[i] - usq)), 0.f);
         }
-        pop[9 * P + o] = wg0 * C;
+        Codec<T>::st1(pop + 9 * P + o, wg0 * C, gref0);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) pop[(9 + i) * P + o] = wg1 * C * (1.f + e[i] * inv_cs2g);
+        for (int i = 1; i <= 4; ++i) Codec<T>::st1(pop + (9 + i) * P + o, wg1 * C * (1.f + e[i] * inv_cs2g), gref1);
     }
 }
 
-__global__ void fields_kernel(const float* pop, const uint8_t* links, int nx, int ny, int pitch,
-                              float* rho_out, float* ux_out, float* uy_out, float* C_out)
+template <typename T>
+__global__ void fields_kernel(const T* pop, const uint8_t* links, int nx, int ny, int pitch,
+                              float* rho_out, float* ux_out, float* uy_out, float* C_out, float gref0, float gref1)
 {
     const long long P = (long long)ny * pitch;
     for (int y = blockIdx.y; y < ny; y += gridDim.y) {
@@ -450,14 +479,16 @@ __global__ void fields_kernel(const float* pop, const uint8_t* links, int nx, in
         if (links[o] != kSolid) {
             float f[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = pop[i * P + o];
+            for (int i = 0; i < 9; ++i) f[i] = Codec<T>::ld1(pop + i * P + o, 0.f);
             r = 1.f + (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]);
             const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
             const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
             vx = jx / r;
             vy = jy / r;
-            c = ((pop[9 * P + o] + pop[10 * P + o]) + (pop[11 * P + o] + pop[12 * P + o])) +
-                pop[13 * P + o];
+            float g[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) g[i] = Codec<T>::ld1(pop + (9 + i) * P + o, i == 0 ? gref0 : gref1);
+            c = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
         }
         const long long idx = (long long)y * nx + x;
         if (rho_out) rho_out[idx] = r;
@@ -467,24 +498,51 @@ __global__ void fields_kernel(const float* pop, const uint8_t* links, int nx, in
     }
 }
 
-}  // namespace
-
-size_t bulk_smem_bytes(int stages)
+// 16-bit storage <-> FP32 representation, element by element.
+template <typename T>
+__global__ void convert_kernel(const void* src, void* dst, long long plane, float gref0, float gref1,
+                               bool to_fp32)
 {
-    return size_t(stages) * (sizeof(Stage) + 2 * sizeof(uint64_t));
+    const long long n = plane * kPlanes;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const float off = plane_offset(int(e / plane), gref0, gref1);
+        if (to_fp32) static_cast<float*>(dst)[e] = Codec<T>::ld1(static_cast<const T*>(src) + e, off);
+        else Codec<T>::st1(static_cast<T*>(dst) + e, static_cast<const float*>(src)[e], off);
+    }
 }
 
-int bulk_stage_bytes()
+int elementwise_grid(long long n)
 {
-    return int(sizeof(Stage));
+    const long long want = (n + 255) / 256;
+    return int(want < 65536 ? want : 65536);
+}
+
+}  // namespace
+
+size_t bulk_smem_bytes(int stages, int precision)
+{
+    const size_t stage = precision == kFP32 ? sizeof(Stage) : sizeof(StageT<__half>);
+    return size_t(stages) * (stage + 2 * sizeof(uint64_t));
+}
+
+int bulk_stage_bytes(int precision)
+{
+    return int(precision == kFP32 ? sizeof(Stage) : sizeof(StageT<__half>));
 }
 
 cudaError_t prepare_step_kernels()
 {
     // The attribute belongs to the kernel, not to a handle: allow the largest
     // ring any handle may ask for, so handles of different shapes coexist.
-    cudaError_t e = cudaFuncSetAttribute(coupled_step_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(coupled_step_bulk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(bulk_smem_bytes(kMaxStages)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(coupled_step_bulk<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(bulk_smem_bytes(kMaxStages, kFP16)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(coupled_step_bulk<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(bulk_smem_bytes(kMaxStages, kBF16)));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(coupled_step_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(bulk_smem_bytes(kMaxStages)));
@@ -495,12 +553,19 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
 {
     if (l.variant == kVariantBulk) {
         const int per = l.stages / (l.block / 32 - 1);
-        coupled_step_bulk<<<l.grid, l.block, bulk_smem_bytes(l.stages), s>>>(a, per);
+        const size_t smem = bulk_smem_bytes(l.stages, l.precision);
+        if (l.precision == kFP16) coupled_step_bulk<__half><<<l.grid, l.block, smem, s>>>(a, per);
+        else if (l.precision == kBF16) coupled_step_bulk<__nv_bfloat16><<<l.grid, l.block, smem, s>>>(a, per);
+        else coupled_step_bulk<float><<<l.grid, l.block, smem, s>>>(a, per);
     } else if (l.variant == kVariantPipe) {
         const int per = l.stages / (l.block / 32);
         coupled_step_pipe<<<l.grid, l.block, bulk_smem_bytes(l.stages), s>>>(a, per);
+    } else if (l.precision == kFP16) {
+        coupled_step_regs<__half><<<l.grid, l.block, 0, s>>>(a);
+    } else if (l.precision == kBF16) {
+        coupled_step_regs<__nv_bfloat16><<<l.grid, l.block, 0, s>>>(a);
     } else {
-        coupled_step_regs<<<l.grid, l.block, 0, s>>>(a);
+        coupled_step_regs<float><<<l.grid, l.block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -513,41 +578,89 @@ cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out
 
 cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm)
 {
-    if (l.variant == kVariantBulk)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk, l.block,
-                                                             bulk_smem_bytes(l.stages));
+    if (l.variant == kVariantBulk) {
+        const size_t smem = bulk_smem_bytes(l.stages, l.precision);
+        if (l.precision == kFP16)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<__half>, l.block,
+                                                                 smem);
+        if (l.precision == kBF16)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<__nv_bfloat16>,
+                                                                 l.block, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<float>, l.block, smem);
+    }
     if (l.variant == kVariantPipe)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_pipe, l.block,
                                                              bulk_smem_bytes(l.stages));
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs, l.block, 0);
+    if (l.precision == kFP16)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__half>, l.block, 0);
+    if (l.precision == kBF16)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__nv_bfloat16>,
+                                                             l.block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<float>, l.block, 0);
 }
 
-cudaError_t launch_init_rest(float* pop, int ny, int pitch, float rho0, float wg0, float wg1,
-                             float C0, cudaStream_t s)
+cudaError_t launch_init_rest(void* pop, int ny, int pitch, float rho0, float wg0, float wg1,
+                             float C0, int precision, cudaStream_t s)
 {
     const long long plane = (long long)ny * pitch;
-    const long long n = plane * kPlanes;
-    const int block = 256;
-    const long long want = (n + block - 1) / block;
-    const int grid = int(want < 65536 ? want : 65536);
-    init_rest<<<grid, block, 0, s>>>(pop, plane, rho0, wg0, wg1, C0);
+    const int grid = elementwise_grid(plane * kPlanes);
+    const float r0 = wg0 * kCRef, r1 = wg1 * kCRef;
+    if (precision == kFP16)
+        init_rest<<<grid, 256, 0, s>>>(static_cast<__half*>(pop), plane, rho0, wg0, wg1, C0, r0, r1);
+    else if (precision == kBF16)
+        init_rest<<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16*>(pop), plane, rho0, wg0, wg1, C0, r0, r1);
+    else
+        init_rest<<<grid, 256, 0, s>>>(static_cast<float*>(pop), plane, rho0, wg0, wg1, C0, 0.f, 0.f);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_fields(float* pop, const uint8_t* links, int nx, int ny, int pitch,
+cudaError_t launch_init_fields(void* pop, const uint8_t* links, int nx, int ny, int pitch,
                                const float* rho, const float* ux, const float* uy, const float* C,
-                               float wg0, float wg1, float inv_cs2g, cudaStream_t s)
+                               float wg0, float wg1, float inv_cs2g, int precision, cudaStream_t s)
 {
     dim3 grid((nx + 255) / 256, ny < 65535 ? ny : 65535);
-    init_fields<<<grid, 256, 0, s>>>(pop, links, nx, ny, pitch, rho, ux, uy, C, wg0, wg1, inv_cs2g);
+    const float r0 = wg0 * kCRef, r1 = wg1 * kCRef;
+    if (precision == kFP16)
+        init_fields<<<grid, 256, 0, s>>>(static_cast<__half*>(pop), links, nx, ny, pitch, rho, ux, uy, C, wg0, wg1,
+                                         inv_cs2g, r0, r1);
+    else if (precision == kBF16)
+        init_fields<<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16*>(pop), links, nx, ny, pitch, rho, ux, uy, C,
+                                         wg0, wg1, inv_cs2g, r0, r1);
+    else
+        init_fields<<<grid, 256, 0, s>>>(static_cast<float*>(pop), links, nx, ny, pitch, rho, ux, uy, C, wg0, wg1,
+                                         inv_cs2g, 0.f, 0.f);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields(const float* pop, const uint8_t* links, int nx, int ny, int pitch,
-                          float* rho, float* ux, float* uy, float* C, cudaStream_t s)
+cudaError_t launch_fields(const void* pop, const uint8_t* links, int nx, int ny, int pitch,
+                          float* rho, float* ux, float* uy, float* C, float wg0, float wg1, int precision,
+                          cudaStream_t s)
 {
     dim3 grid((nx + 255) / 256, ny < 65535 ? ny : 65535);
-    fields_kernel<<<grid, 256, 0, s>>>(pop, links, nx, ny, pitch, rho, ux, uy, C);
+    const float r0 = wg0 * kCRef, r1 = wg1 * kCRef;
+    if (precision == kFP16)
+        fields_kernel<<<grid, 256, 0, s>>>(static_cast<const __half*>(pop), links, nx, ny, pitch, rho, ux, uy, C,
+                                           r0, r1);
+    else if (precision == kBF16)
+        fields_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(pop), links, nx, ny, pitch, rho, ux,
+                                           uy, C, r0, r1);
+    else
+        fields_kernel<<<grid, 256, 0, s>>>(static_cast<const float*>(pop), links, nx, ny, pitch, rho, ux, uy, C,
+                                           0.f, 0.f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* src, void* dst, long long plane, float wg0, float wg1, int precision,
+                           bool to_fp32, cudaStream_t s)
+{
+    const int grid = elementwise_grid(plane * kPlanes);
+    const float r0 = wg0 * kCRef, r1 = wg1 * kCRef;
+    if (precision == kFP16)
+        convert_kernel<__half><<<grid, 256, 0, s>>>(src, dst, plane, r0, r1, to_fp32);
+    else if (precision == kBF16)
+        convert_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(src, dst, plane, r0, r1, to_fp32);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@ WEST, EAST = 0, 1
 VELOCITY, PRESSURE = 0, 1
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NUMERIC, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(7)
+LBM_FP32, LBM_FP16, LBM_BF16 = range(3)
+PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblbm_gb300.so")
@@ -46,14 +48,16 @@ class lbm_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("block_threads", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("pipeline_stages", ctypes.c_int32), ("consumer_warps", ctypes.c_int32)]
+                ("pipeline_stages", ctypes.c_int32), ("consumer_warps", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
 
 
 class lbm_info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("pitch", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("stages", ctypes.c_int32), ("fluid_nodes", ctypes.c_int64), ("algorithmic_bytes_per_step", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("variant", ctypes.c_int32), ("stages", ctypes.c_int32), ("fluid_nodes", ctypes.c_int64),
+                ("algorithmic_bytes_per_step", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class lbm_objective(ctypes.Structure):
@@ -173,11 +177,13 @@ class Chip:
     side, x, y0, y1, kind, rho.  ``edge_u`` / ``edge_C``: (2, ny) per side
     and row.  ``stream``: a ``torch.cuda.Stream`` (or raw cudaStream_t int);
     ``torch_alloc``: take device memory from PyTorch's caching allocator.
+    ``precision``: storage of the populations, "fp32" (default), "fp16" or
+    "bf16" (16-bit deviations, FP32 arithmetic).
     """
 
     def __init__(self, solid, tau, tau_c, ports=(), edge_u=None, edge_C=None, w0=1.0 / 3.0,
                  rho0=1.0, C0=0.0, stream=None, torch_alloc=False, device=-1, block_threads=0,
-                 max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0):
+                 max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0, precision="fp32"):
         self._lib = load()
         solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
         self.ny, self.nx = solid.shape
@@ -197,6 +203,7 @@ class Chip:
         opt.variant = int(variant)
         opt.pipeline_stages = int(pipeline_stages)
         opt.consumer_warps = int(consumer_warps)
+        opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.stream = stream
         if stream is not None:
             opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))

@@ -81,6 +81,8 @@ def _create(lib, nx, ny, mask, tau=0.8, tau_c=0.6, ports=(), edge_u=None, edge_C
     (dict(ports=[(0, 0, 0, 0, 99, 1, 1.0)]), "outside the grid"),
     (dict(opt="badsize"), "struct_size"),
     (dict(opt="badblock"), "block_threads"),
+    (dict(opt="badprecision"), "precision = 3"),
+    (dict(opt="fp16pipe"), "variants 1 and 2"),
 ])
 def test_create_rejects_invalid_arguments(lib, case, needle):
     nx, ny = case.get("nx", 8), 6
@@ -99,6 +101,10 @@ def test_create_rejects_invalid_arguments(lib, case, needle):
         lib.lbm_default_options(ctypes.byref(opt))
         if case["opt"] == "badsize":
             opt.struct_size = 3
+        elif case["opt"] == "badprecision":
+            opt.precision = 3
+        elif case["opt"] == "fp16pipe":
+            opt.precision, opt.variant = lbm.LBM_FP16, 3
         else:
             opt.block_threads = 100
     st, msg = _create(lib, nx, ny, mask, tau=case.get("tau", 0.8), tau_c=case.get("tau_c", 0.6),
