@@ -294,6 +294,54 @@ def _reduced_precision(prob, steps, stream, device, peak):
     return out
 
 
+def _batch(steps, stream, device, peak, n_chips=64):
+    """64 independent chips of 256 x 128 ... 1024 x 512 (seeded sizes,
+    relaxation times and valve periods): all in one handle, one launch per
+    step, against the same chips stepped one handle after another."""
+    import torch
+    from paper_1307_4703_gb300 import lbm, workloads as W
+    chips = W.config_batch(n_chips)
+    fluid = sum(W.fluid_count(p) for p in chips)
+
+    def timed(fn, n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    batch = lbm.Chip.batch(chips, stream=stream, torch_alloc=True, device=device)
+    for k, p in enumerate(chips):
+        batch.set_instance_schedule(k, p["period"], p["states"])
+    batch.step(20)
+    batch.synchronize()
+    s_batch = timed(lambda: batch.step(1), steps)
+    info = batch.info()
+    batch.diagnostics()
+    batch.close()
+    singles = [lbm.Chip.from_problem(p, stream=stream, torch_alloc=True, device=device) for p in chips]
+    for c, p in zip(singles, chips):
+        c.set_valve_schedule(p["period"], p["states"])
+        c.step(5)
+    n_single = max(1, steps // 10)
+
+    def one_by_one():
+        for c in singles:
+            c.step(1)
+
+    s_single = timed(one_by_one, n_single)
+    for c in singles:
+        c.close()
+    achieved = info["algorithmic_bytes_per_step"] * steps / s_batch / 1e9
+    return {"value": fluid * steps / s_batch / 1e9, "unit": UNIT, "chips": n_chips, "fluid_nodes": fluid,
+            "steps": steps, "one_by_one": fluid * n_single / s_single / 1e9, "one_by_one_steps": n_single,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "bytes_per_launch": info["algorithmic_bytes_per_step"]}}
+
+
 def _e2e(prob, steps, device):
     """The same metric through the public C ABI with host buffers: create the
     chip from host arrays, then every step upload the step's valve word, run
@@ -398,6 +446,7 @@ def main():
     if not args.skip_extras:
         extras["frozen_scalar_step"] = _frozen_scalar(chip, prob, min(args.steps, 2000), stream, peak)
         extras["reduced_precision_storage"] = _reduced_precision(prob, min(args.steps, 5000), stream, local, peak)
+        extras["batch_64_chips"] = _batch(min(args.steps, 2000), stream, local, peak)
         e2e_steps = min(args.steps, 5000)
         e = _e2e(prob, e2e_steps, local)
         e["value"] = aggregate_glups(fluid * e2e_steps, e["seconds"], ws)

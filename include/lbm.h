@@ -303,10 +303,57 @@ typedef struct {
                                             written (112 B for FP32, 56 B for FP16 / BF16) */
     int64_t device_bytes;   /* device memory held by the handle */
     int32_t precision;      /* LBM_FP32, LBM_FP16 or LBM_BF16 */
-    int32_t reserved;
+    int32_t instances;      /* chips in the handle: 1, or n of lbm_create_batch */
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_handle h, lbm_info* info);
+
+/* ---- Batches of independent chips in one launch ----
+ *
+ * The paper studies one chip at a time; screening many designs (channel
+ * widths, relaxation times, valve periods) runs many small, independent
+ * chips.  Each alone fills a fraction of the GPU, and a step of a small chip
+ * costs little more than its kernel launch.  lbm_create_batch stacks n chips
+ * along y into one lattice, with one solid row between neighbours: every
+ * link that leaves a chip ends on a solid node, exactly as at the edge of a
+ * single chip (halfway bounce-back at y = -1/2 and y = ny - 1/2), so each
+ * chip evolves as it would alone, and one launch of the step kernel advances
+ * all of them.  Each chip keeps its own tau and tau_c (per-row relaxation
+ * rates) and its own valve program.
+ *
+ * The handle is an ordinary lbm_handle over the stacked lattice (width the
+ * largest nx, height the sum of the ny plus n - 1): lbm_step, the field,
+ * population, diagnostics and save/load calls see the stacked lattice, and
+ * lbm_get_instance gives where chip k sits in it.  Chip k's channel c is
+ * lattice channel channel_base + c (at most 256 lattice channels in all).
+ * lbm_set_valves and lbm_set_valve_schedule set the same valve program on
+ * every chip; lbm_set_instance_valves and lbm_set_instance_schedule set
+ * chip k's own (channel bits of that chip, 0..31).  Diagnostics are totals
+ * over all chips.  lbm_save_state keeps the populations, the step count and
+ * the handle-wide valve program, not per-chip programs.  lbm_adjoint,
+ * lbm_store_velocity, lbm_set_velocity_field and lbm_scalar_step need a single
+ * chip and return LBM_ERR_STATE on a batch. */
+typedef struct {
+    int32_t nx, ny;
+    const uint8_t* mask;    /* nx*ny bytes as in lbm_create */
+    double tau, tau_c;
+    int32_t n_ports;        /* 0..64; channels 0..31 of this chip */
+    const lbm_port* ports;  /* rows and columns of this chip */
+    const float* edge_u;    /* 2*ny floats as in lbm_create (NULL only without velocity ports) */
+    const float* edge_C;
+} lbm_chip_desc;
+
+typedef struct {
+    int32_t row0;           /* first lattice row of the chip */
+    int32_t nx, ny;
+    int32_t channel_base;   /* lattice channel of the chip's channel 0 */
+} lbm_instance;
+
+/* n in [1, 4096] chips; the arrays are copied.  Options as in lbm_create. */
+lbm_status lbm_create_batch(lbm_handle* out, int32_t n, const lbm_chip_desc* chips, const lbm_options* opt);
+lbm_status lbm_get_instance(lbm_handle h, int32_t k, lbm_instance* out);
+lbm_status lbm_set_instance_valves(lbm_handle h, int32_t k, uint32_t open_mask);
+lbm_status lbm_set_instance_schedule(lbm_handle h, int32_t k, int64_t period, int32_t n, const uint32_t* states);
 
 /* ---- One step on caller-owned buffers, allocating nothing ----
  *

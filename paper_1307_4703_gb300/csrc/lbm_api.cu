@@ -24,6 +24,7 @@ thread_local std::string g_create_error = "no error";
 constexpr uint32_t kStateMagic = 0x4C424D31u;  // "LBM1"
 constexpr int kMaxPorts = 64;
 constexpr int kMaxSchedule = 4096;
+constexpr int kMaxInstances = 4096;
 // Bulk-copy pipeline shape measured fastest on GB300 for the 4096 x 2048 chip:
 // three computing warps with one stage each, four blocks per SM.
 constexpr int kDefaultConsumers = 3;
@@ -55,7 +56,9 @@ struct lbm_ctx {
     float* pop[2] = {nullptr, nullptr};
     int precision = lbm::kFP32;
     size_t elem = sizeof(float);
-    int cur = 0;  // buffer holding the current state
+    int cur = 0;   // buffer holding the current state
+    int gbuf = 0;  // buffer holding the current scalar planes: cur, except after
+                   // an odd number of scalar-only steps (joined lazily)
     uint8_t* links = nullptr;
     lbm::RowBC* rowbc = nullptr;
     uint2* tiles = nullptr;
@@ -65,6 +68,8 @@ struct lbm_ctx {
     float* fields_tmp = nullptr;  // 4 * nx * ny floats
 
     int n_tiles = 0;
+    int sms = 0;
+    int scalar_grid = 0;  // one wave of the scalar-only step kernel (set on first use)
     lbm::StepLaunch launch{lbm::kVariantBulk, 0, 0, 0};
     long long fluid = 0;
     long long device_bytes = 0;
@@ -73,6 +78,24 @@ struct lbm_ctx {
     uint32_t fixed_mask = 0;
     int64_t period = 0;
     std::vector<uint32_t> schedule;
+
+    // Batches of chips (lbm_create_batch): instance k occupies rows
+    // [row0, row0 + ny) and columns [0, nx) of the stacked lattice, with its
+    // channels c at lattice channels chan_base + c and its own valve program.
+    struct Inst {
+        int row0, nx, ny, chan_base, n_chan;
+        double tau, tau_c;
+        uint32_t fixed_mask;
+        int64_t period;
+        std::vector<uint32_t> schedule;
+        uint32_t word_at(int64_t t) const
+        {
+            if (!schedule.empty()) return schedule[size_t((t / period) % int64_t(schedule.size()))];
+            return fixed_mask;
+        }
+    };
+    std::vector<Inst> inst;  // empty for a single chip
+    float4* rates = nullptr; // per-row relaxation rates of a batch
     bool numeric = false;  // the device error word was found set (bit 0)
     bool timeout = false;  // a bounded device wait gave up (bit 1)
 
@@ -89,6 +112,22 @@ struct lbm_ctx {
         if (!schedule.empty())
             return schedule[size_t((t / period) % int64_t(schedule.size()))];
         return fixed_mask;
+    }
+
+    // Valve bits of every lattice channel at step t.
+    void mask_words(int64_t t, uint32_t (&w)[lbm::kMaskWords]) const
+    {
+        for (int j = 0; j < lbm::kMaskWords; ++j) w[j] = 0;
+        if (inst.empty()) {
+            w[0] = mask_at(t);
+            return;
+        }
+        for (const Inst& k : inst) {
+            const uint64_t bits = uint64_t(k.word_at(t)) & ((k.n_chan >= 32 ? 0xFFFFFFFFull : (1ull << k.n_chan) - 1));
+            const uint64_t sh = bits << (k.chan_base & 31);
+            w[k.chan_base >> 5] |= uint32_t(sh);
+            if ((k.chan_base >> 5) + 1 < lbm::kMaskWords) w[(k.chan_base >> 5) + 1] |= uint32_t(sh >> 32);
+        }
     }
 };
 
@@ -153,9 +192,28 @@ bool is_fluid(const uint8_t* mask, int nx, int ny, int x, int y)
 constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
+// What lbm_create_batch adds to a stacked lattice.
+struct BatchSpec {
+    std::vector<lbm_ctx::Inst> inst;
+    std::vector<float4> rates;  // one per lattice row
+};
+
 lbm_status check_ctx(lbm_ctx* h)
 {
     if (!h) return LBM_ERR_ARG;
+    return LBM_OK;
+}
+
+// Bring the scalar planes back next to the fluid planes after scalar-only
+// steps left them in the other buffer (one device copy of 5 planes).
+lbm_status join_scalar(lbm_ctx* h)
+{
+    if (h->gbuf == h->cur) return LBM_OK;
+    const size_t off = size_t(9) * h->plane * h->elem;
+    char* to = reinterpret_cast<char*>(h->pop[h->cur]) + off;
+    const char* from = reinterpret_cast<const char*>(h->pop[h->gbuf]) + off;
+    LBM_CUDA(h, cudaMemcpyAsync(to, from, size_t(5) * h->plane * h->elem, cudaMemcpyDeviceToDevice, h->stream));
+    h->gbuf = h->cur;
     return LBM_OK;
 }
 
@@ -198,9 +256,12 @@ const char* lbm_last_error(lbm_handle h)
     return h ? h->last_error.c_str() : g_create_error.c_str();
 }
 
-lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* mask, double tau,
-                      double tau_c, int32_t n_ports, const lbm_port* ports, const float* edge_u,
-                      const float* edge_C, const lbm_options* opt_in)
+}  // extern "C"
+
+namespace {
+lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* mask, double tau, double tau_c,
+                       int32_t n_ports, const lbm_port* ports, const float* edge_u, const float* edge_C,
+                       const lbm_options* opt_in, const BatchSpec* batch)
 {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -253,8 +314,10 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     }
     if ((opt.alloc == nullptr) != (opt.free == nullptr))
         return fail(nullptr, LBM_ERR_ARG, "alloc and free hooks must be given together");
-    if (n_ports < 0 || n_ports > kMaxPorts)
-        return fail(nullptr, LBM_ERR_ARG, "n_ports = %d outside [0, %d]", n_ports, kMaxPorts);
+    const int max_ports = batch ? kMaxPorts * int(batch->inst.size()) : kMaxPorts;
+    const int max_channel = batch ? 32 * lbm::kMaskWords - 1 : 31;
+    if (n_ports < 0 || n_ports > max_ports)
+        return fail(nullptr, LBM_ERR_ARG, "n_ports = %d outside [0, %d]", n_ports, max_ports);
     if (n_ports > 0 && !ports) return fail(nullptr, LBM_ERR_ARG, "ports is NULL");
 
     long long fluid = 0;
@@ -265,8 +328,8 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     bool any_velocity = false;
     for (int p = 0; p < n_ports; ++p) {
         const lbm_port& P = ports[p];
-        if (P.channel < 0 || P.channel > 31)
-            return fail(nullptr, LBM_ERR_ARG, "port %d: channel %d outside [0, 31]", p, P.channel);
+        if (P.channel < 0 || P.channel > max_channel)
+            return fail(nullptr, LBM_ERR_ARG, "port %d: channel %d outside [0, %d]", p, P.channel, max_channel);
         if (P.side != LBM_WEST && P.side != LBM_EAST)
             return fail(nullptr, LBM_ERR_ARG, "port %d: side %d invalid", p, P.side);
         if (P.kind != LBM_PORT_VELOCITY && P.kind != LBM_PORT_PRESSURE)
@@ -379,6 +442,7 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
+    h->sms = sms;
     lbm::StepLaunch& L = h->launch;
     L.variant = opt.variant == 1 ? lbm::kVariantRegs : opt.variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
     L.precision = opt.precision;
@@ -419,9 +483,11 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     h->err = static_cast<unsigned*>(dev_alloc(h, sizeof(unsigned)));
     h->diag = static_cast<double*>(dev_alloc(h, 4 * sizeof(double)));
     h->fields_tmp = static_cast<float*>(dev_alloc(h, size_t(4) * nx * ny * sizeof(float)));
+    if (batch) h->rates = static_cast<float4*>(dev_alloc(h, size_t(ny) * sizeof(float4)));
     if (!h->pop[0] || !h->pop[1] || !h->links || !h->rowbc || !h->tiles || !h->partials ||
-        !h->err || !h->diag || !h->fields_tmp)
+        !h->err || !h->diag || !h->fields_tmp || (batch && !h->rates))
         return bail(fail(h, LBM_ERR_OOM, "device allocation of %zu bytes failed", 2 * pop_bytes));
+    if (batch) h->inst = batch->inst;
 
     cudaStream_t st = h->stream;
     e = cudaMemcpyAsync(h->links, links.data(), links.size(), cudaMemcpyHostToDevice, st);
@@ -430,6 +496,8 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !tiles.empty())
         e = cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && batch)
+        e = cudaMemcpyAsync(h->rates, batch->rates.data(), size_t(ny) * sizeof(float4), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->partials, 0, size_t(h->launch.grid) * 4 * sizeof(double), st);
@@ -444,6 +512,140 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "device initialisation"));
     *out = h;
     g_create_error = "no error";
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* mask, double tau,
+                      double tau_c, int32_t n_ports, const lbm_port* ports, const float* edge_u,
+                      const float* edge_C, const lbm_options* opt_in)
+{
+    return create_impl(out, nx, ny, mask, tau, tau_c, n_ports, ports, edge_u, edge_C, opt_in, nullptr);
+}
+
+lbm_status lbm_create_batch(lbm_handle* out, int32_t n, const lbm_chip_desc* chips, const lbm_options* opt)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > kMaxInstances) return fail(nullptr, LBM_ERR_ARG, "n = %d outside [1, %d]", n, kMaxInstances);
+    if (!chips) return fail(nullptr, LBM_ERR_ARG, "chips is NULL");
+    // stack the chips along y, one solid row between neighbours, so that no
+    // link of one chip reaches another (every link that leaves a chip ends
+    // on a solid node, as at the edge of a single chip)
+    BatchSpec b;
+    int nx = 0, ny = 0, chan = 0;
+    for (int k = 0; k < n; ++k) {
+        const lbm_chip_desc& c = chips[k];
+        if (c.nx < 1 || c.ny < 1) return fail(nullptr, LBM_ERR_ARG, "chip %d: grid %d x %d is empty", k, c.nx, c.ny);
+        if (!c.mask) return fail(nullptr, LBM_ERR_ARG, "chip %d: mask is NULL", k);
+        if (!(c.tau > 0.5) || !std::isfinite(c.tau) || !(c.tau_c > 0.5) || !std::isfinite(c.tau_c))
+            return fail(nullptr, LBM_ERR_ARG, "chip %d: tau = %g, tau_c = %g: relaxation times must exceed 1/2", k,
+                        c.tau, c.tau_c);
+        if (c.n_ports < 0 || c.n_ports > kMaxPorts || (c.n_ports > 0 && !c.ports))
+            return fail(nullptr, LBM_ERR_ARG, "chip %d: n_ports = %d or ports invalid", k, c.n_ports);
+        int top = -1;
+        for (int p = 0; p < c.n_ports; ++p) {
+            if (c.ports[p].channel < 0 || c.ports[p].channel > 31)
+                return fail(nullptr, LBM_ERR_ARG, "chip %d port %d: channel %d outside [0, 31]", k, p,
+                            c.ports[p].channel);
+            top = std::max(top, c.ports[p].channel);
+        }
+        if (k > 0) ++ny;  // separator row
+        lbm_ctx::Inst I{ny, c.nx, c.ny, chan, top + 1, c.tau, c.tau_c, 0u, 0, {}};
+        b.inst.push_back(I);
+        chan += top + 1;
+        nx = std::max(nx, int(c.nx));
+        if (int64_t(ny) + c.ny >= (1 << 19)) return fail(nullptr, LBM_ERR_ARG, "the stacked chips are too tall");
+        ny += c.ny;
+    }
+    if (chan > 32 * lbm::kMaskWords)
+        return fail(nullptr, LBM_ERR_ARG, "the chips have %d valve channels in all, more than %d", chan,
+                    32 * lbm::kMaskWords);
+    std::vector<uint8_t> mask(size_t(nx) * ny, 1);
+    std::vector<float> eu(size_t(2) * ny, 0.f), ec(size_t(2) * ny, 0.f);
+    std::vector<lbm_port> ports;
+    b.rates.assign(size_t(ny), make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int k = 0; k < n; ++k) {
+        const lbm_chip_desc& c = chips[k];
+        const lbm_ctx::Inst& I = b.inst[k];
+        for (int y = 0; y < c.ny; ++y) {
+            std::memcpy(&mask[size_t(I.row0 + y) * nx], c.mask + size_t(y) * c.nx, size_t(c.nx));
+            b.rates[I.row0 + y] = make_float4(float(1.0 / c.tau), float(1.0 / c.tau_c), 0.f, 0.f);
+            for (int side = 0; side < 2; ++side) {
+                if (c.edge_u) eu[size_t(side) * ny + I.row0 + y] = c.edge_u[size_t(side) * c.ny + y];
+                if (c.edge_C) ec[size_t(side) * ny + I.row0 + y] = c.edge_C[size_t(side) * c.ny + y];
+            }
+        }
+        for (int p = 0; p < c.n_ports; ++p) {
+            lbm_port q = c.ports[p];
+            if (q.y0 < 0 || q.y1 > c.ny || q.y0 >= q.y1 || q.x < 0 || q.x >= c.nx)
+                return fail(nullptr, LBM_ERR_ARG, "chip %d port %d: column %d rows [%d, %d) outside the chip", k, p,
+                            q.x, q.y0, q.y1);
+            if (q.kind == LBM_PORT_VELOCITY && (!c.edge_u || !c.edge_C))
+                return fail(nullptr, LBM_ERR_ARG, "chip %d: velocity ports need edge_u and edge_C", k);
+            q.channel += I.chan_base;
+            q.y0 += I.row0;
+            q.y1 += I.row0;
+            ports.push_back(q);
+        }
+    }
+    lbm_options o;
+    lbm_default_options(&o);
+    if (opt) {
+        if (opt->struct_size != sizeof(lbm_options))
+            return fail(nullptr, LBM_ERR_ARG, "lbm_options.struct_size is %u, expected %zu", opt->struct_size,
+                        sizeof(lbm_options));
+        o = *opt;
+    }
+    return create_impl(out, nx, ny, mask.data(), chips[0].tau, chips[0].tau_c, int32_t(ports.size()), ports.data(),
+                       eu.data(), ec.data(), &o, &b);
+}
+
+lbm_status lbm_get_instance(lbm_handle h, int32_t k, lbm_instance* out)
+{
+    if (check_ctx(h) || !out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    const int n = h->inst.empty() ? 1 : int(h->inst.size());
+    if (k < 0 || k >= n) return fail(h, LBM_ERR_ARG, "instance %d outside [0, %d)", k, n);
+    if (h->inst.empty()) {
+        *out = lbm_instance{0, h->nx, h->ny, 0};
+    } else {
+        const lbm_ctx::Inst& I = h->inst[size_t(k)];
+        *out = lbm_instance{I.row0, I.nx, I.ny, I.chan_base};
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_instance_valves(lbm_handle h, int32_t k, uint32_t open_mask)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (h->inst.empty()) {
+        if (k != 0) return fail(h, LBM_ERR_ARG, "instance %d of a single chip", k);
+        return lbm_set_valves(h, open_mask);
+    }
+    if (k < 0 || k >= int(h->inst.size())) return fail(h, LBM_ERR_ARG, "instance %d outside [0, %zu)", k, h->inst.size());
+    lbm_ctx::Inst& I = h->inst[size_t(k)];
+    I.fixed_mask = open_mask;
+    I.schedule.clear();
+    I.period = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_instance_schedule(lbm_handle h, int32_t k, int64_t period, int32_t n, const uint32_t* states)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (h->inst.empty()) {
+        if (k != 0) return fail(h, LBM_ERR_ARG, "instance %d of a single chip", k);
+        return lbm_set_valve_schedule(h, period, n, states);
+    }
+    if (k < 0 || k >= int(h->inst.size())) return fail(h, LBM_ERR_ARG, "instance %d outside [0, %zu)", k, h->inst.size());
+    if (n < 0 || n > kMaxSchedule) return fail(h, LBM_ERR_ARG, "schedule length %d outside [0, %d]", n, kMaxSchedule);
+    if (n > 0 && period < 1) return fail(h, LBM_ERR_ARG, "schedule period %lld < 1", (long long)period);
+    if (n > 0 && !states) return fail(h, LBM_ERR_ARG, "states is NULL");
+    lbm_ctx::Inst& I = h->inst[size_t(k)];
+    I.schedule.assign(states, states + n);
+    I.period = n > 0 ? period : 0;
     return LBM_OK;
 }
 
@@ -461,6 +663,11 @@ lbm_status lbm_set_valves(lbm_handle h, uint32_t open_mask)
     h->fixed_mask = open_mask;
     h->schedule.clear();
     h->period = 0;
+    for (lbm_ctx::Inst& I : h->inst) {  // every chip of a batch runs this valve word
+        I.fixed_mask = open_mask;
+        I.schedule.clear();
+        I.period = 0;
+    }
     return LBM_OK;
 }
 
@@ -470,6 +677,10 @@ lbm_status lbm_set_valve_schedule(lbm_handle h, int64_t period, int32_t n, const
     if (n == 0) {
         h->schedule.clear();
         h->period = 0;
+        for (lbm_ctx::Inst& I : h->inst) {
+            I.schedule.clear();
+            I.period = 0;
+        }
         return LBM_OK;
     }
     if (n < 0 || n > kMaxSchedule) return fail(h, LBM_ERR_ARG, "schedule length %d outside [0, %d]", n, kMaxSchedule);
@@ -477,6 +688,10 @@ lbm_status lbm_set_valve_schedule(lbm_handle h, int64_t period, int32_t n, const
     if (!states) return fail(h, LBM_ERR_ARG, "states is NULL");
     h->schedule.assign(states, states + n);
     h->period = period;
+    for (lbm_ctx::Inst& I : h->inst) {  // every chip of a batch runs this schedule
+        I.schedule.assign(states, states + n);
+        I.period = period;
+    }
     return LBM_OK;
 }
 
@@ -484,6 +699,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
+    if (lbm_status js = join_scalar(h)) return js;
     lbm::StepArgs a{};
     a.links = h->links;
     a.rowbc = h->rowbc;
@@ -499,6 +715,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     a.inv_cs2g = h->inv_cs2g;
     a.partials = h->partials;
     a.err = h->err;
+    a.rates = h->rates;
     if (h->precision != LBM_FP32) {
         a.gref0 = h->wg0 * lbm::kCRef;
         a.gref1 = h->wg1 * lbm::kCRef;
@@ -506,10 +723,11 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     for (int64_t k = 0; k < n; ++k) {
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
-        a.open_mask = h->mask_at(h->step);
+        h->mask_words(h->step, a.open_mask);
         cudaError_t e = lbm::launch_step(a, h->launch, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
+        h->gbuf = h->cur;
         ++h->step;
     }
     return pending_numeric(h);
@@ -551,6 +769,7 @@ lbm_status lbm_clear_error(lbm_handle h)
 lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy, float* C)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
+    if (lbm_status js = join_scalar(h)) return js;
     cudaError_t e = lbm::launch_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, rho, ux, uy, C, h->wg0,
                                        h->wg1, h->precision, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel launch");
@@ -622,6 +841,7 @@ struct Scratch {
 // g_i), [plane][y][x] on the host; 16-bit storage is converted on the device.
 lbm_status raw_out(lbm_ctx* h, float* f, float* g)
 {
+    if (lbm_status js = join_scalar(h)) return js;
     const float* src = h->pop[h->cur];
     Scratch sc(h);
     if (h->precision != LBM_FP32) {
@@ -644,6 +864,7 @@ lbm_status raw_out(lbm_ctx* h, float* f, float* g)
 
 lbm_status raw_in(lbm_ctx* h, const float* f, const float* g)
 {
+    if (lbm_status js = join_scalar(h)) return js;
     float* dst = h->pop[h->cur];
     Scratch sc(h);
     void* tmp = nullptr;
@@ -671,6 +892,7 @@ lbm_status raw_in(lbm_ctx* h, const float* f, const float* g)
 // The stored elements as they are (elem bytes each), [plane][y][x].
 lbm_status stored_out(lbm_ctx* h, void* out)
 {
+    if (lbm_status js = join_scalar(h)) return js;
     const size_t row = size_t(h->nx) * h->elem, pitch = size_t(h->pitch) * h->elem;
     LBM_CUDA(h, cudaMemcpy2DAsync(out, row, h->pop[h->cur], pitch, row, size_t(lbm::kPlanes) * h->ny,
                                   cudaMemcpyDeviceToHost, h->stream));
@@ -680,6 +902,7 @@ lbm_status stored_out(lbm_ctx* h, void* out)
 
 lbm_status stored_in(lbm_ctx* h, const void* in)
 {
+    if (lbm_status js = join_scalar(h)) return js;
     const size_t row = size_t(h->nx) * h->elem, pitch = size_t(h->pitch) * h->elem;
     LBM_CUDA(h, cudaMemcpy2DAsync(h->pop[h->cur], pitch, in, row, row, size_t(lbm::kPlanes) * h->ny,
                                   cudaMemcpyHostToDevice, h->stream));
@@ -720,6 +943,7 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux,
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (!rho || !ux || !uy || !C) return fail(h, LBM_ERR_ARG, "a field pointer is NULL");
+    if (lbm_status js = join_scalar(h)) return js;
     const size_t n = size_t(h->nx) * h->ny;
     float* t = h->fields_tmp;
     const float* ins[4] = {rho, ux, uy, C};
@@ -807,6 +1031,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_adjoint");
+    if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_adjoint");
     if (!obj || !J || !dJ_dtau_c) return fail(h, LBM_ERR_ARG, "objective, J or dJ_dtau_c is NULL");
     if (n < 1 || K < 1) return fail(h, LBM_ERR_ARG, "n_steps = %lld and ckpt_every = %d must be >= 1", (long long)n, K);
     if (obj->n < 1 || !obj->x || !obj->y || !obj->target || !obj->weight)
@@ -865,15 +1090,17 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     a.partials = h->partials;
     a.err = h->err;
     const int64_t t0 = h->step;
+    if (lbm_status js = join_scalar(h)) return js;
     for (int64_t t = 0; t < n; ++t) {
         if (t % K == 0)
             LBM_CUDA(h, cudaMemcpyAsync(ckpt + size_t(t / K) * S, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
-        a.open_mask = h->mask_at(t0 + t);
+        a.open_mask[0] = h->mask_at(t0 + t);
         cudaError_t e = lbm::launch_step(a, h->launch, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
+        h->gbuf = h->cur;
         ++h->step;
     }
 
@@ -926,7 +1153,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         for (int j = 1; j < len; ++j) {
             r.src = state(j - 1);
             r.dst = state(j);
-            r.open_mask = h->mask_at(t0 + s0 + j - 1);
+            r.open_mask[0] = h->mask_at(t0 + s0 + j - 1);
             cudaError_t e = lbm::launch_step(r, h->launch, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "recompute step launch");
         }
@@ -976,6 +1203,7 @@ lbm_status lbm_store_velocity(lbm_handle h, uint32_t open_mask)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_store_velocity");
+    if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_store_velocity");
     float* u = field_slot(h, open_mask);
     if (!u) return fail(h, LBM_ERR_OOM, "no room for the velocity field of valve word %u (at most %d fields)",
                         open_mask, LBM_MAX_FIELDS);
@@ -988,6 +1216,7 @@ lbm_status lbm_set_velocity_field(lbm_handle h, uint32_t open_mask, const float*
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_set_velocity_field");
+    if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_set_velocity_field");
     if (!ux || !uy) return fail(h, LBM_ERR_ARG, "ux or uy is NULL");
     float* u = field_slot(h, open_mask);
     if (!u) return fail(h, LBM_ERR_OOM, "no room for the velocity field of valve word %u (at most %d fields)",
@@ -1003,6 +1232,7 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_scalar_step");
+    if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_scalar_step");
     if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
     if (!std::isfinite(u_scale)) return fail(h, LBM_ERR_ARG, "u_scale = %g is not finite", u_scale);
     // every valve word the steps use needs a field
@@ -1026,25 +1256,38 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
     a.partials = h->partials;
+    a.n_partials = h->launch.grid;
     a.err = h->err;
-    int g = h->cur;  // buffer holding the current scalar planes
+    if (h->scalar_grid == 0) {
+        // one wave of resident blocks (at most the coupled step's grid, whose
+        // partials buffer the kernel writes)
+        int per_sm = 0;
+        LBM_CUDA(h, lbm::scalar_step_occupancy(256, &per_sm));
+        const int need = (h->n_tiles + 7) / 8;
+        h->scalar_grid = std::max(1, std::min({need, std::max(1, per_sm) * h->sms, h->launch.grid}));
+    }
+    int g = h->gbuf;  // buffer holding the current scalar planes
     for (int64_t k = 0; k < n; ++k) {
         const uint32_t w = h->mask_at(h->step);
         const float* u = find_field(h, w);
-        if (!u) return fail(h, LBM_ERR_STATE, "no stored velocity field for valve word %u", w);
+        if (!u) {
+            h->gbuf = g;
+            return fail(h, LBM_ERR_STATE, "no stored velocity field for valve word %u", w);
+        }
         a.src = h->pop[g] + 9 * h->plane;
         a.dst = h->pop[1 - g] + 9 * h->plane;
         a.ux = u;
         a.uy = u + h->plane;
         a.open_mask = w;
-        cudaError_t e = lbm::launch_scalar_step(a, h->launch.grid, 256, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "scalar step launch");
+        cudaError_t e = lbm::launch_scalar_step(a, h->scalar_grid, 256, h->stream);
+        if (e != cudaSuccess) {
+            h->gbuf = g;
+            return cuda_fail(h, e, "scalar step launch");
+        }
         g = 1 - g;
         ++h->step;
     }
-    if (g != h->cur)  // bring the scalar planes back next to the fluid planes
-        LBM_CUDA(h, cudaMemcpyAsync(h->pop[h->cur] + 9 * h->plane, h->pop[g] + 9 * h->plane,
-                                    size_t(5) * h->plane * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    h->gbuf = g;  // joined with the fluid planes when a call needs both
     return pending_numeric(h);
 }
 
@@ -1070,7 +1313,7 @@ lbm_status lbm_get_info(lbm_handle h, lbm_info* info)
     info->algorithmic_bytes_per_step = h->fluid * 28 * (long long)h->elem;
     info->device_bytes = h->device_bytes;
     info->precision = h->precision;
-    info->reserved = 0;
+    info->instances = h->inst.empty() ? 1 : int32_t(h->inst.size());
     return LBM_OK;
 }
 

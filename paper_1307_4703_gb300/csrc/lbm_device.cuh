@@ -384,14 +384,34 @@ __device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const T* __restr
 // row whose port entries are bw (west) and be (east); v holds the streamed
 // populations on entry and the post-collision populations on exit (fluid
 // planes as deviations f_i - w_i).
+// Valve bit of the channel in a port entry's chan_kind (channel in the low
+// byte), selected without indexing the parameter array.
+__device__ __forceinline__ bool valve_open(const StepArgs& a, int chan_kind)
+{
+    const int ch = chan_kind & 0xFF;
+    uint32_t w = a.open_mask[0];
+#pragma unroll
+    for (int j = 1; j < kMaskWords; ++j)
+        if ((ch >> 5) == j) w = a.open_mask[j];
+    return (w >> (ch & 31)) & 1u;
+}
+
+// Relaxation rates {1 / tau_f, 1 / tau_g} of a row.
+__device__ __forceinline__ float2 row_rates(const StepArgs& a, int y)
+{
+    if (a.rates == nullptr) return make_float2(a.omega_f, a.omega_g);
+    const float4 r = __ldg(a.rates + y);
+    return make_float2(r.x, r.y);
+}
+
 template <typename T>
 __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, int x0, const RowBC& bw,
                                              const RowBC& be, const StepArgs& a, const T* S, long long oC,
-                                             QuadAcc& acc)
+                                             float2 omega, QuadAcc& acc)
 {
     const long long P = a.plane;
-    const bool open_w = bw.x >= 0 && ((a.open_mask >> (bw.chan_kind & 31)) & 1u);
-    const bool open_e = be.x >= 0 && ((a.open_mask >> (be.chan_kind & 31)) & 1u);
+    const bool open_w = bw.x >= 0 && valve_open(a, bw.chan_kind);
+    const bool open_e = be.x >= 0 && valve_open(a, be.chan_kind);
 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -425,7 +445,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         const float inv = 1.f / rho;
         const float ux = jx * inv, uy = jy * inv;
         const float usq = 1.5f * (ux * ux + uy * uy);
-        const float wo = a.omega_f;
+        const float wo = omega.x;
         {
             // f_eq_i - w_i = w_i [rho - 1 + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]
             const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
@@ -445,7 +465,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
         const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
         {
-            const float wg = a.omega_g;
+            const float wg = omega.y;
             const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
             // rest equilibrium w0 C formed as the remainder, so that the five
             // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)

@@ -33,7 +33,8 @@ constexpr int kSegBits = 12;     // tile encoding: segment in the low 12 bits
 constexpr uint8_t kSolid = 0xFF;
 constexpr int kRowFloats = kTileNodes + 8;  // staged plane row: 4-float halo on each side
 constexpr int kBulkMaxThreads = 256;        // bulk variant: at most 7 consumer warps + 1 producer
-constexpr int kMaxStages = 24;              // bulk variant: largest shared-memory ring
+constexpr int kMaxStages = 24;             // bulk variant: largest shared-memory ring
+constexpr int kMaskWords = 8;              // valve channels per lattice: 32 * kMaskWords
 
 enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3 };
 enum Precision { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
@@ -66,10 +67,12 @@ struct StepArgs {
     long long plane;        // ny * pitch
     float omega_f;          // 1 / tau_f
     float omega_g;          // 1 / tau_g
+    const float4* rates;    // per row {1 / tau_f, 1 / tau_g, 0, 0} (batches of chips), or null:
+                            // omega_f and omega_g hold everywhere
     float wg0;              // scalar rest weight
     float wg1;              // scalar axis weight (1 - wg0) / 4
     float inv_cs2g;         // 1 / c_s^2 of the scalar lattice
-    uint32_t open_mask;     // valve word of this step
+    uint32_t open_mask[kMaskWords];  // valve bits of this step: channel c is bit c % 32 of word c / 32
     double* partials;       // 4 diagnostics partial sums per block (scratch)
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
     float gref0, gref1;     // 16-bit storage: offsets w_0 C_ref and w_1 C_ref of the scalar planes
@@ -120,10 +123,12 @@ struct ScalarArgs {
     float omega_g, wg0, wg1, inv_cs2g;
     uint32_t open_mask;
     double* partials;       // writes slots 1 and 3 of each block's four
+    int n_partials;         // entries of `partials` (>= grid); those beyond the grid get 0
     unsigned int* err;
 };
 
 cudaError_t launch_scalar_step(const ScalarArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t scalar_step_occupancy(int block, int* blocks_per_sm);
 cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, long long plane, float* ux, float* uy,
                                      cudaStream_t s);
 

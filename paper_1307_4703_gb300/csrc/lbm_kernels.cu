@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
             const RowBC bw = a.rowbc[y];
             const RowBC be = a.rowbc[a.ny + y];
             QuadAcc q;
-            collide_quad(v, lk, x0, bw, be, a, S, oC, q);
+            collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p)
                 Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
@@ -135,14 +135,18 @@ struct __align__(16) StageT {
     T pl[kPlanes][kTileNodes + 2 * kHalo];
     unsigned links[kTileNodes / 4];
     RowBC bc[2];
+    float4 rates;  // the row's relaxation rates (copied only for batches of chips)
     uint2 tile;
     uint2 pad;
 };
 using Stage = StageT<float>;
 static_assert(sizeof(Stage) % 16 == 0 && sizeof(StageT<__half>) % 16 == 0,
               "stage size must keep 16-byte alignment");
-static_assert(offsetof(Stage, links) % 16 == 0 && offsetof(Stage, bc) % 16 == 0, "bulk-copy targets");
-static_assert(offsetof(StageT<__half>, links) % 16 == 0 && offsetof(StageT<__half>, bc) % 16 == 0,
+static_assert(offsetof(Stage, links) % 16 == 0 && offsetof(Stage, bc) % 16 == 0 &&
+                  offsetof(Stage, rates) % 16 == 0,
+              "bulk-copy targets");
+static_assert(offsetof(StageT<__half>, links) % 16 == 0 && offsetof(StageT<__half>, bc) % 16 == 0 &&
+                  offsetof(StageT<__half>, rates) % 16 == 0,
               "bulk-copy targets");
 static_assert(sizeof(StageT<__half>) == sizeof(StageT<__nv_bfloat16>), "16-bit stages");
 
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
                     const long long rS = (long long)(y > 0 ? y - 1 : y) * a.pitch;
                     const long long rN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch;
                     const uint32_t bytes = uint32_t(6 * (ue - us) + 8 * (se - ss)) * uint32_t(sizeof(T)) +
-                                           kTileNodes + 2 * sizeof(RowBC);
+                                           kTileNodes + 2 * sizeof(RowBC) + (a.rates ? sizeof(float4) : 0);
                     st[s].tile = tile;  // ordered before the consumer by the arrive below
                     mbar_arrive_expect_tx(&full[s], bytes);
 #pragma unroll
@@ -231,6 +235,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
                     bulk_g2s(st[s].links, a.links + rC + x0, kTileNodes, &full[s]);
                     bulk_g2s(&st[s].bc[0], a.rowbc + y, sizeof(RowBC), &full[s]);
                     bulk_g2s(&st[s].bc[1], a.rowbc + a.ny + y, sizeof(RowBC), &full[s]);
+                    if (a.rates) bulk_g2s(&st[s].rates, a.rates + y, sizeof(float4), &full[s]);
                     last_use = batch;
                 }
             }
@@ -259,6 +264,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
             const unsigned lk = sg.links[lane];
             const bool act = lk != 0xFFFFFFFFu;
             const RowBC bw = sg.bc[0], be = sg.bc[1];
+            const float2 omega = a.rates ? make_float2(sg.rates.x, sg.rates.y) : make_float2(a.omega_f, a.omega_g);
             // ---- free flight (pull) from the staged rows ----
             float4 v[kPlanes];
             if (act) {
@@ -277,7 +283,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
             if (act) {
                 bounce_back(v, lk, S, P, oC, a.gref1);
                 QuadAcc q;
-                collide_quad(v, lk, x0, bw, be, a, S, oC, q);
+                collide_quad(v, lk, x0, bw, be, a, S, oC, omega, q);
 #pragma unroll
                 for (int p = 0; p < kPlanes; ++p)
                     Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
@@ -315,7 +321,8 @@ __device__ __forceinline__ void issue_tile(const StepArgs& a, uint2 tile, Stage&
     const int se = ue + 4 < a.pitch ? ue + 4 : a.pitch;
     if (lane == 0) {
         sg.tile = tile;
-        const uint32_t bytes = uint32_t(6 * (ue - us) + 8 * (se - ss)) * 4u + kTileNodes + 2 * sizeof(RowBC);
+        const uint32_t bytes = uint32_t(6 * (ue - us) + 8 * (se - ss)) * 4u + kTileNodes + 2 * sizeof(RowBC) +
+                               (a.rates ? sizeof(float4) : 0);
         mbar_arrive_expect_tx(bar, bytes);
     }
     __syncwarp();
@@ -334,6 +341,8 @@ __device__ __forceinline__ void issue_tile(const StepArgs& a, uint2 tile, Stage&
         bulk_g2s(&sg.bc[0], a.rowbc + y, sizeof(RowBC), bar);
     } else if (lane == kPlanes + 2) {
         bulk_g2s(&sg.bc[1], a.rowbc + a.ny + y, sizeof(RowBC), bar);
+    } else if (lane == kPlanes + 3 && a.rates) {
+        bulk_g2s(&sg.rates, a.rates + y, sizeof(float4), bar);
     }
 }
 
@@ -384,6 +393,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
         const unsigned lk = sg.links[lane];
         const bool act = lk != 0xFFFFFFFFu;
         const RowBC bw = sg.bc[0], be = sg.bc[1];
+        const float2 omega = a.rates ? make_float2(sg.rates.x, sg.rates.y) : make_float2(a.omega_f, a.omega_g);
         // ---- free flight (pull) from the staged rows ----
         float4 v[kPlanes];
         if (act) {
@@ -407,7 +417,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
         if (act) {
             bounce_back(v, lk, S, P, oC);
             QuadAcc q;
-            collide_quad(v, lk, x0, bw, be, a, S, oC, q);
+            collide_quad(v, lk, x0, bw, be, a, S, oC, omega, q);
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p) stg4(a.dst + p * P + oC, v[p]);
             bad |= q.bad;

@@ -143,7 +143,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_noalloc_step* s)
     a.wg0 = float(s->w0);
     a.wg1 = float(0.25 * (1.0 - s->w0));
     a.inv_cs2g = float(2.0 / (1.0 - s->w0));
-    a.open_mask = s->open_mask;
+    a.open_mask[0] = s->open_mask;  // channels 0..31; the other words stay 0
     a.partials = d.scratch;
     a.err = s->err;
     cudaStream_t stream = static_cast<cudaStream_t>(s->stream);

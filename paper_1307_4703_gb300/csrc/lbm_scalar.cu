@@ -144,6 +144,9 @@ __global__ void __launch_bounds__(256) scalar_frozen_step(const ScalarArgs a)
         double s = 0.0;
         for (int w = 0; w < wpb; ++w) s += red[w][threadIdx.x];
         a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = s;
+        // entries of the coupled step's larger grid hold no scalar partial now
+        for (int b = blockIdx.x + gridDim.x; b < a.n_partials; b += gridDim.x)
+            a.partials[b * 4 + 1 + 2 * threadIdx.x] = 0.0;
     }
 }
 
@@ -174,6 +177,11 @@ cudaError_t launch_scalar_step(const ScalarArgs& a, int grid, int block, cudaStr
 {
     scalar_frozen_step<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t scalar_step_occupancy(int block, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, scalar_frozen_step, block, 0);
 }
 
 cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, long long plane, float* ux, float* uy,

@@ -57,7 +57,18 @@ class lbm_info(ctypes.Structure):
                 ("n_tiles", ctypes.c_int32), ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("stages", ctypes.c_int32), ("fluid_nodes", ctypes.c_int64),
                 ("algorithmic_bytes_per_step", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("instances", ctypes.c_int32)]
+
+
+class lbm_chip_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("mask", ctypes.c_void_p),
+                ("tau", ctypes.c_double), ("tau_c", ctypes.c_double), ("n_ports", ctypes.c_int32),
+                ("ports", ctypes.c_void_p), ("edge_u", ctypes.c_void_p), ("edge_C", ctypes.c_void_p)]
+
+
+class lbm_instance(ctypes.Structure):
+    _fields_ = [("row0", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("channel_base", ctypes.c_int32)]
 
 
 class lbm_objective(ctypes.Structure):
@@ -120,6 +131,12 @@ SIGNATURES = {
     "lbm_store_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     "lbm_set_velocity_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _f32p, _f32p]),
     "lbm_scalar_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
+    "lbm_create_batch": (ctypes.c_int, [_P(ctypes.c_void_p), ctypes.c_int32, _P(lbm_chip_desc),
+                                        _P(lbm_options)]),
+    "lbm_get_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _P(lbm_instance)]),
+    "lbm_set_instance_valves": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32]),
+    "lbm_set_instance_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                                 _u32p]),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -141,6 +158,16 @@ def load(path=None):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def _ports(ports):
+    ports = list(ports)
+    parr = (lbm_port * max(1, len(ports)))()
+    for k, p in enumerate(ports):
+        parr[k] = lbm_port(int(p["channel"]), int(p["side"]), int(p["x"]), int(p["y0"]),
+                           int(p["y1"]), int(p["kind"]), float(p.get("rho", 1.0)))
+    parr._keep = ports
+    return parr
 
 
 def _f32(a, shape=None):
@@ -183,17 +210,15 @@ class Chip:
 
     def __init__(self, solid, tau, tau_c, ports=(), edge_u=None, edge_C=None, w0=1.0 / 3.0,
                  rho0=1.0, C0=0.0, stream=None, torch_alloc=False, device=-1, block_threads=0,
-                 max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0, precision="fp32"):
+                 max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0, precision="fp32",
+                 _batch=None):
         self._lib = load()
-        solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
-        self.ny, self.nx = solid.shape
-        ports = list(ports)
-        parr = (lbm_port * max(1, len(ports)))()
-        for k, p in enumerate(ports):
-            parr[k] = lbm_port(int(p["channel"]), int(p["side"]), int(p["x"]), int(p["y0"]),
-                               int(p["y1"]), int(p["kind"]), float(p.get("rho", 1.0)))
-        eu = _f32(np.zeros((2, self.ny)) if edge_u is None else edge_u, (2, self.ny))
-        ec = _f32(np.zeros((2, self.ny)) if edge_C is None else edge_C, (2, self.ny))
+        if _batch is None:
+            solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
+            self.ny, self.nx = solid.shape
+            parr = _ports(ports)
+            eu = _f32(np.zeros((2, self.ny)) if edge_u is None else edge_u, (2, self.ny))
+            ec = _f32(np.zeros((2, self.ny)) if edge_C is None else edge_C, (2, self.ny))
         opt = lbm_options()
         self._lib.lbm_default_options(ctypes.byref(opt))
         opt.device = int(device)
@@ -214,18 +239,71 @@ class Chip:
             self._hooks = _torch_hooks(dev)
             opt.alloc, opt.free = self._hooks
         h = ctypes.c_void_p()
-        st = self._lib.lbm_create(ctypes.byref(h), self.nx, self.ny, solid.ctypes.data_as(_u8p),
-                                  float(tau), float(tau_c), len(ports), parr, _fp(eu), _fp(ec),
-                                  ctypes.byref(opt))
+        if _batch is None:
+            st = self._lib.lbm_create(ctypes.byref(h), self.nx, self.ny, solid.ctypes.data_as(_u8p),
+                                      float(tau), float(tau_c), len(parr._keep), parr, _fp(eu), _fp(ec),
+                                      ctypes.byref(opt))
+        else:
+            descs, keep = _batch
+            st = self._lib.lbm_create_batch(ctypes.byref(h), len(descs), descs, ctypes.byref(opt))
         if st != LBM_OK:
             raise LbmError(st, self._lib.lbm_last_error(None).decode())
         self._h = h
-        self.solid = solid.astype(bool)
+        if _batch is None:
+            self.solid = solid.astype(bool)
+        else:
+            inf = self.info()
+            self.nx, self.ny = inf["nx"], inf["ny"]
+            self.solid = np.ones((self.ny, self.nx), bool)
+            for k in range(inf["instances"]):
+                i = self.instance(k)
+                self.solid[i["row0"]:i["row0"] + i["ny"], :i["nx"]] = keep[4 * k] != 0
 
     @classmethod
     def from_problem(cls, prob, **kw):
         return cls(prob["solid"], prob["tau"], prob["tau_c"], ports=prob["ports"],
                    edge_u=prob["edge_u"], edge_C=prob["edge_C"], w0=prob.get("w0", 1.0 / 3.0), **kw)
+
+    @classmethod
+    def batch(cls, problems, **kw):
+        """One handle over many independent chips (lbm_create_batch), each a
+        problem dict as ``from_problem`` takes; chip k is ``instance(k)``."""
+        problems = list(problems)
+        descs = (lbm_chip_desc * len(problems))()
+        keep = []
+        for k, prob in enumerate(problems):
+            solid = np.ascontiguousarray(np.asarray(prob["solid"]) != 0, dtype=np.uint8)
+            ny, nx = solid.shape
+            parr = _ports(prob["ports"])
+            eu = _f32(prob["edge_u"], (2, ny))
+            ec = _f32(prob["edge_C"], (2, ny))
+            keep += [solid, eu, ec, parr]
+            descs[k] = lbm_chip_desc(nx, ny, solid.ctypes.data, float(prob["tau"]), float(prob["tau_c"]),
+                                     len(parr._keep), ctypes.cast(parr, ctypes.c_void_p), eu.ctypes.data,
+                                     ec.ctypes.data)
+        kw.setdefault("w0", problems[0].get("w0", 1.0 / 3.0))
+        chip = cls(None, None, None, _batch=(descs, keep), **kw)
+        chip.problems = problems
+        return chip
+
+    def instance(self, k):
+        i = lbm_instance()
+        self._check(self._lib.lbm_get_instance(self._h, int(k), ctypes.byref(i)))
+        return {n: getattr(i, n) for n, _ in lbm_instance._fields_}
+
+    def instance_fields(self, k, fields=None):
+        """rho, ux, uy, C of chip k of a batch (slices of ``fields()``)."""
+        i = self.instance(k)
+        fields = self.fields() if fields is None else fields
+        return tuple(a[i["row0"]:i["row0"] + i["ny"], :i["nx"]] for a in fields)
+
+    def set_instance_valves(self, k, open_mask):
+        self._check(self._lib.lbm_set_instance_valves(self._h, int(k), int(open_mask) & 0xFFFFFFFF))
+
+    def set_instance_schedule(self, k, period, states):
+        arr = np.ascontiguousarray(states, dtype=np.uint32)
+        self._check(self._lib.lbm_set_instance_schedule(self._h, int(k), int(period), len(arr),
+                                                        arr.ctypes.data_as(_u32p)))
 
     # -- plumbing ------------------------------------------------------------
     def _check(self, st):

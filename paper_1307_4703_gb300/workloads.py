@@ -108,6 +108,25 @@ def config_adjoint_chip():
                             name="chip-1024x512")
 
 
+def config_batch(n=64, steps=10000, seed=SEED):
+    """``n`` independent two-channel chips for the batched step, drawn with
+    PCG64: nx uniform over the multiples of 64 in [256, 1024], ny = nx / 2,
+    channels ny / 8 rows wide over the full length, chamber centred with a
+    width uniform in [40, 200] (at most nx / 2), tau = 0.8, u_max = 0.05,
+    tau_c uniform in [0.505, 0.6), valve period uniform in [250, 4000]."""
+    r = rng(seed)
+    chips = []
+    for k in range(n):
+        nx = 64 * int(r.integers(4, 17))
+        ny = nx // 2
+        cw = min(int(r.integers(40, 201)), nx // 2)
+        tau_c = float(r.uniform(0.505, 0.6))
+        period = int(r.integers(250, 4001))
+        chips.append(two_channel_chip(nx, ny, ny // 8, nx, cw, 0.8, tau_c, 0.05, period, steps,
+                                      name="batch-%d-%dx%d" % (k, nx, ny)))
+    return chips
+
+
 def has_isolated_fluid(solid):
     """True when some fluid cell has no fluid cell among its 8 neighbours
     inside the grid (such masks are rejected by the library)."""

@@ -133,3 +133,22 @@ def test_valid_arguments_reach_the_device_step(lib):
         assert st == lbm.LBM_OK, msg
     else:
         assert st == lbm.LBM_ERR_CUDA, msg
+
+
+def test_batch_creation_checks_run_on_the_host(lib):
+    """lbm_create_batch rejects an empty batch and more than 256 valve
+    channels before any device call."""
+    h = ctypes.c_void_p()
+    assert lib.lbm_create_batch(ctypes.byref(h), 0, None, None) == lbm.LBM_ERR_ARG
+    mask = np.zeros((8, 8), np.uint8)
+    eu = np.zeros((2, 8), np.float32)
+    port = (lbm.lbm_port * 1)(lbm.lbm_port(1, 0, 0, 0, 4, 1, 1.0))  # channel 1: two channels per chip
+    descs = (lbm.lbm_chip_desc * 129)()
+    for k in range(129):
+        descs[k] = lbm.lbm_chip_desc(8, 8, mask.ctypes.data, 0.8, 0.6, 1, ctypes.cast(port, ctypes.c_void_p),
+                                     eu.ctypes.data, eu.ctypes.data)
+    assert lib.lbm_create_batch(ctypes.byref(h), 129, descs, None) == lbm.LBM_ERR_ARG
+    assert b"valve channels" in lib.lbm_last_error(None)
+    descs[0].tau_c = 0.5
+    assert lib.lbm_create_batch(ctypes.byref(h), 1, descs, None) == lbm.LBM_ERR_ARG
+    assert b"chip 0" in lib.lbm_last_error(None)
