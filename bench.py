@@ -342,6 +342,37 @@ def _batch(steps, stream, device, peak, n_chips=64):
                          "frac": achieved / peak, "bytes_per_launch": info["algorithmic_bytes_per_step"]}}
 
 
+def _graphs(steps, stream, device, peak):
+    """The 1024 x 768 chip (the paper's 1 um lattice, 313,600 fluid nodes:
+    a few microseconds per step, so launch costs show): single-step launches
+    against replayed CUDA graphs of 100 steps, after lbm_autotune."""
+    import torch
+    from paper_1307_4703_gb300 import lbm, workloads as W
+    prob = W.config_full_chip()
+    fluid = W.fluid_count(prob)
+    out = {"workload": "chip-1024x768, %d fluid nodes" % fluid}
+    for key, gs in (("launches", 0), ("graphs_100", 100)):
+        chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=device, graph_steps=gs)
+        chip.set_valve_schedule(prob["period"], prob["states"])
+        info = chip.autotune()
+        chip.step(200)
+        chip.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        chip.step(steps)
+        e1.record(stream)
+        stream.synchronize()
+        s = e0.elapsed_time(e1) / 1e3
+        chip.diagnostics()
+        chip.close()
+        achieved = info["algorithmic_bytes_per_step"] * steps / s / 1e9
+        out[key] = {"value": fluid * steps / s / 1e9, "unit": UNIT, "steps": steps,
+                    "launch": {k: info[k] for k in ("variant", "grid", "block", "stages")},
+                    "roofline_frac": achieved / peak}
+    return out
+
+
 def _e2e(prob, steps, device):
     """The same metric through the public C ABI with host buffers: create the
     chip from host arrays, then every step upload the step's valve word, run
@@ -447,6 +478,7 @@ def main():
         extras["frozen_scalar_step"] = _frozen_scalar(chip, prob, min(args.steps, 2000), stream, peak)
         extras["reduced_precision_storage"] = _reduced_precision(prob, min(args.steps, 5000), stream, local, peak)
         extras["batch_64_chips"] = _batch(min(args.steps, 2000), stream, local, peak)
+        extras["small_chip_graphs"] = _graphs(min(args.steps, 20000), stream, local, peak)
         e2e_steps = min(args.steps, 5000)
         e = _e2e(prob, e2e_steps, local)
         e["value"] = aggregate_glups(fluid * e2e_steps, e["seconds"], ws)

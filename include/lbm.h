@@ -116,6 +116,10 @@ typedef struct {
     int32_t consumer_warps; /* variants 2, 3: computing warps per block, 0 = default (2: 3, 3: 4),
                                else 1..7 (variant 2) or 1..8 (variant 3) */
     int32_t precision;      /* storage of the populations (LBM_FP32, LBM_FP16, LBM_BF16), see below */
+    int32_t graph_steps;    /* 0 = off; else an even number <= 4096: lbm_step replays runs of this many
+                               steps with unchanged valve words as one cached CUDA graph (captured
+                               on first use, at most 16 per handle), which removes the per-launch
+                               host cost on small chips.  Results are identical either way. */
 } lbm_options;
 
 /* Storage precision.  The paper computes in double precision ("Numerical
@@ -307,6 +311,16 @@ typedef struct {
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_handle h, lbm_info* info);
+
+/* Time the step kernel's launch shapes on this chip and keep the fastest
+ * (the paper has no counterpart; launch shapes are a property of the GPU).
+ * Candidates: the register variant with 128 and 256 threads, the bulk-copy
+ * variant with 2..4 computing warps and 1..2 (16-bit: up to 3) stages each,
+ * and variant 3 (FP32).  Each runs 3 + trial_steps (0 = 20) launches from the
+ * current state into scratch buffers, so the state, the step count and the
+ * diagnostics do not change; every shape gives identical populations.
+ * lbm_get_info reports the shape kept.  Synchronises the stream. */
+lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps);
 
 /* ---- Batches of independent chips in one launch ----
  *

@@ -25,6 +25,9 @@ constexpr uint32_t kStateMagic = 0x4C424D31u;  // "LBM1"
 constexpr int kMaxPorts = 64;
 constexpr int kMaxSchedule = 4096;
 constexpr int kMaxInstances = 4096;
+constexpr int kMaxBlocksPerSM = 32;  // resident blocks per SM, an upper bound for every launch shape
+constexpr int kMaxGraphs = 16;       // cached CUDA graphs per handle
+constexpr int kMaxGraphSteps = 4096;
 // Bulk-copy pipeline shape measured fastest on GB300 for the 4096 x 2048 chip:
 // three computing warps with one stage each, four blocks per SM.
 constexpr int kDefaultConsumers = 3;
@@ -69,6 +72,8 @@ struct lbm_ctx {
 
     int n_tiles = 0;
     int sms = 0;
+    int partials_cap = 0;  // blocks the partials buffer holds (any launch shape fits)
+    int diag_grid = 0;     // blocks whose partials the last step wrote
     int scalar_grid = 0;  // one wave of the scalar-only step kernel (set on first use)
     lbm::StepLaunch launch{lbm::kVariantBulk, 0, 0, 0};
     long long fluid = 0;
@@ -96,6 +101,29 @@ struct lbm_ctx {
     };
     std::vector<Inst> inst;  // empty for a single chip
     float4* rates = nullptr; // per-row relaxation rates of a batch
+
+    // CUDA graphs of graph_steps consecutive step launches, one per valve
+    // words and starting buffer, captured on a private stream.
+    struct Graph {
+        uint32_t words[lbm::kMaskWords];
+        int parity;
+        cudaGraphExec_t exec;
+    };
+    int graph_steps = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<Graph> graphs;
+
+    // Whether the valve words stay the same over steps [t0, t0 + len).
+    bool mask_constant(int64_t t0, int64_t len) const
+    {
+        auto same = [&](int64_t period, size_t n) {
+            return n <= 1 || t0 / period == (t0 + len - 1) / period;
+        };
+        if (inst.empty()) return schedule.empty() || same(period, schedule.size());
+        for (const Inst& k : inst)
+            if (!k.schedule.empty() && !same(k.period, k.schedule.size())) return false;
+        return true;
+    }
     bool numeric = false;  // the device error word was found set (bit 0)
     bool timeout = false;  // a bounded device wait gave up (bit 1)
 
@@ -176,6 +204,10 @@ void* dev_alloc(lbm_ctx* h, size_t bytes)
 
 void free_all(lbm_ctx* h)
 {
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
     for (auto& a : h->allocs) {
         if (h->free_fn) h->free_fn(a.ptr, a.bytes, h->alloc_user);
         else cudaFree(a.ptr);
@@ -191,6 +223,51 @@ bool is_fluid(const uint8_t* mask, int nx, int ny, int x, int y)
 // Eq. lattice directions 1..8 (index 0 is the rest direction).
 constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// The cached graph of graph_steps launches for the valve words in
+// a.open_mask starting from buffer cur, captured on first use.
+lbm_status step_graph(lbm_ctx* h, lbm::StepArgs a, cudaGraphExec_t* out)
+{
+    for (auto& g : h->graphs)
+        if (g.parity == h->cur && std::memcmp(g.words, a.open_mask, sizeof(g.words)) == 0) {
+            *out = g.exec;
+            return LBM_OK;
+        }
+    if (int(h->graphs.size()) >= kMaxGraphs) {  // keep the cache small: start over
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+        h->graphs.clear();
+    }
+    LBM_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < h->graph_steps && e == cudaSuccess; ++j) {
+        a.src = h->pop[(h->cur + j) & 1];
+        a.dst = h->pop[(h->cur + j + 1) & 1];
+        e = lbm::launch_step(a, h->launch, h->cap_stream);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (e == cudaSuccess) e = e_end;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step graph capture");
+    lbm_ctx::Graph g;
+    std::memcpy(g.words, a.open_mask, sizeof(g.words));
+    g.parity = h->cur;
+    g.exec = exec;
+    h->graphs.push_back(g);
+    *out = exec;
+    return LBM_OK;
+}
+
+// One wave of resident blocks, which then stride over the tile table.
+int wave_grid(const lbm_ctx* h, const lbm::StepLaunch& L, int per_sm)
+{
+    const int tiles_per_block = L.variant == lbm::kVariantBulk ? 1 : L.block / 32;  // tiles in flight at once
+    const int need = (h->n_tiles + tiles_per_block - 1) / tiles_per_block;
+    return std::max(1, std::min(need, per_sm * h->sms));
+}
 
 // What lbm_create_batch adds to a stacked lattice.
 struct BatchSpec {
@@ -314,6 +391,9 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     }
     if ((opt.alloc == nullptr) != (opt.free == nullptr))
         return fail(nullptr, LBM_ERR_ARG, "alloc and free hooks must be given together");
+    if (opt.graph_steps < 0 || opt.graph_steps % 2 != 0 || opt.graph_steps > kMaxGraphSteps)
+        return fail(nullptr, LBM_ERR_ARG, "graph_steps = %d: use 0 or an even number up to %d", opt.graph_steps,
+                    kMaxGraphSteps);
     const int max_ports = batch ? kMaxPorts * int(batch->inst.size()) : kMaxPorts;
     const int max_channel = batch ? 32 * lbm::kMaskWords - 1 : 31;
     if (n_ports < 0 || n_ports > max_ports)
@@ -425,6 +505,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->fluid = fluid;
     h->precision = opt.precision;
     h->elem = opt.precision == LBM_FP32 ? sizeof(float) : sizeof(uint16_t);
+    h->graph_steps = opt.graph_steps;
 
     auto bail = [&](lbm_status s) {
         g_create_error = h->last_error;
@@ -467,10 +548,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     e = lbm::step_kernel_occupancy(L, &per_sm);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
     if (per_sm < 1) return bail(fail(h, LBM_ERR_ARG, "the step kernel cannot run with this launch shape"));
-    // one wave of resident blocks, which then stride over the tile table
-    const int tiles_per_block = L.variant == lbm::kVariantBulk ? 1 : L.block / 32;  // tiles in flight at once
-    const int need = (h->n_tiles + tiles_per_block - 1) / tiles_per_block;
-    L.grid = std::max(1, std::min(need, per_sm * sms));
+    L.grid = wave_grid(h, L, per_sm);
     if (opt.max_blocks > 0) L.grid = std::min(L.grid, opt.max_blocks);
 
     const size_t pop_bytes = size_t(h->plane) * lbm::kPlanes * h->elem;
@@ -479,7 +557,9 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->links = static_cast<uint8_t*>(dev_alloc(h, links.size()));
     h->rowbc = static_cast<lbm::RowBC*>(dev_alloc(h, rowbc.size() * sizeof(lbm::RowBC)));
     h->tiles = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, tiles.size()) * sizeof(uint2)));
-    h->partials = static_cast<double*>(dev_alloc(h, size_t(h->launch.grid) * 4 * sizeof(double)));
+    h->partials_cap = std::max(h->launch.grid, sms * kMaxBlocksPerSM);
+    h->diag_grid = h->launch.grid;
+    h->partials = static_cast<double*>(dev_alloc(h, size_t(h->partials_cap) * 4 * sizeof(double)));
     h->err = static_cast<unsigned*>(dev_alloc(h, sizeof(unsigned)));
     h->diag = static_cast<double*>(dev_alloc(h, 4 * sizeof(double)));
     h->fields_tmp = static_cast<float*>(dev_alloc(h, size_t(4) * nx * ny * sizeof(float)));
@@ -500,7 +580,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         e = cudaMemcpyAsync(h->rates, batch->rates.data(), size_t(ny) * sizeof(float4), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(h->partials, 0, size_t(h->launch.grid) * 4 * sizeof(double), st);
+        e = cudaMemsetAsync(h->partials, 0, size_t(h->partials_cap) * 4 * sizeof(double), st);
     if (e == cudaSuccess)
         e = lbm::launch_init_rest(h->pop[0], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0),
                                   h->precision, st);
@@ -508,6 +588,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         e = lbm::launch_init_rest(h->pop[1], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0),
                                   h->precision, st);
     // the host tables above are pageable: wait so they may go out of scope
+    if (e == cudaSuccess && h->graph_steps > 0) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "device initialisation"));
     *out = h;
@@ -720,15 +801,30 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
         a.gref0 = h->wg0 * lbm::kCRef;
         a.gref1 = h->wg1 * lbm::kCRef;
     }
-    for (int64_t k = 0; k < n; ++k) {
+    const int G = h->graph_steps;
+    for (int64_t k = 0; k < n;) {
+        h->mask_words(h->step, a.open_mask);
+        if (G > 0 && n - k >= G && h->mask_constant(h->step, G)) {
+            // G steps (an even number: the state ends in the buffer it
+            // started from) as one graph launch
+            cudaGraphExec_t exec = nullptr;
+            lbm_status s = step_graph(h, a, &exec);
+            if (s != LBM_OK) return s;
+            LBM_CUDA(h, cudaGraphLaunch(exec, h->stream));
+            h->step += G;
+            k += G;
+            h->diag_grid = h->launch.grid;
+            continue;
+        }
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
-        h->mask_words(h->step, a.open_mask);
         cudaError_t e = lbm::launch_step(a, h->launch, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
         h->gbuf = h->cur;
+        h->diag_grid = h->launch.grid;
         ++h->step;
+        ++k;
     }
     return pending_numeric(h);
 }
@@ -795,7 +891,7 @@ lbm_status lbm_get_fields(lbm_handle h, float* rho, float* ux, float* uy, float*
 lbm_status lbm_get_diagnostics(lbm_handle h, double out[4])
 {
     if (check_ctx(h) || !out) return fail(h, LBM_ERR_ARG, "out is NULL");
-    cudaError_t e = lbm::launch_diag_finish(h->partials, h->launch.grid, h->diag, h->stream);
+    cudaError_t e = lbm::launch_diag_finish(h->partials, h->diag_grid, h->diag, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics reduction launch");
     LBM_CUDA(h, cudaMemcpyAsync(out, h->diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return read_err_word(h);
@@ -1101,6 +1197,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
         h->gbuf = h->cur;
+        h->diag_grid = h->launch.grid;
         ++h->step;
     }
 
@@ -1256,7 +1353,7 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
     a.partials = h->partials;
-    a.n_partials = h->launch.grid;
+    a.n_partials = h->diag_grid;
     a.err = h->err;
     if (h->scalar_grid == 0) {
         // one wave of resident blocks (at most the coupled step's grid, whose
@@ -1264,8 +1361,9 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
         int per_sm = 0;
         LBM_CUDA(h, lbm::scalar_step_occupancy(256, &per_sm));
         const int need = (h->n_tiles + 7) / 8;
-        h->scalar_grid = std::max(1, std::min({need, std::max(1, per_sm) * h->sms, h->launch.grid}));
+        h->scalar_grid = std::max(1, std::min(need, std::max(1, per_sm) * h->sms));
     }
+    const int scalar_grid = std::min(h->scalar_grid, h->diag_grid);  // its partials go to the last step's slots
     int g = h->gbuf;  // buffer holding the current scalar planes
     for (int64_t k = 0; k < n; ++k) {
         const uint32_t w = h->mask_at(h->step);
@@ -1279,7 +1377,7 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
         a.ux = u;
         a.uy = u + h->plane;
         a.open_mask = w;
-        cudaError_t e = lbm::launch_scalar_step(a, h->scalar_grid, 256, h->stream);
+        cudaError_t e = lbm::launch_scalar_step(a, scalar_grid, 256, h->stream);
         if (e != cudaSuccess) {
             h->gbuf = g;
             return cuda_fail(h, e, "scalar step launch");
@@ -1295,6 +1393,104 @@ lbm_status lbm_get_step(lbm_handle h, int64_t* t)
 {
     if (check_ctx(h) || !t) return fail(h, LBM_ERR_ARG, "t is NULL");
     *t = h->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (trial_steps < 0 || trial_steps > 10000) return fail(h, LBM_ERR_ARG, "trial_steps = %d outside [0, 10000]", trial_steps);
+    if (trial_steps == 0) trial_steps = 20;
+    if (lbm_status js = join_scalar(h)) return js;
+    // candidate shapes: {variant, block (variant 1) or computing warps, stages per computing warp}
+    struct Cand { int variant, warps, per; };
+    std::vector<Cand> cands = {{1, 4, 0}, {1, 8, 0}, {2, 2, 1}, {2, 3, 1}, {2, 4, 1}, {2, 2, 2}, {2, 3, 2}, {2, 4, 2}};
+    if (h->precision == LBM_FP32) cands.push_back({3, 4, 1});
+    else cands.push_back({2, 3, 3});
+    // trials write to scratch buffers: the state, step count and diagnostics stay as they are
+    Scratch sc(h);
+    void* dst = sc.get(size_t(h->plane) * lbm::kPlanes * h->elem);
+    double* part = static_cast<double*>(sc.get(size_t(h->partials_cap) * 4 * sizeof(double)));
+    unsigned* err = static_cast<unsigned*>(sc.get(sizeof(unsigned)));
+    if (!dst || !part || !err) return fail(h, LBM_ERR_OOM, "no device memory for the trial steps");
+    LBM_CUDA(h, lbm::prepare_step_kernels());
+    lbm::StepArgs a{};
+    a.src = h->pop[h->cur];
+    a.dst = static_cast<float*>(dst);
+    a.links = h->links;
+    a.rowbc = h->rowbc;
+    a.tiles = h->tiles;
+    a.n_tiles = h->n_tiles;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.omega_f = float(1.0 / h->tau);
+    a.omega_g = float(1.0 / h->tau_c);
+    a.rates = h->rates;
+    a.wg0 = h->wg0;
+    a.wg1 = h->wg1;
+    a.inv_cs2g = h->inv_cs2g;
+    a.partials = part;
+    a.err = err;
+    if (h->precision != LBM_FP32) {
+        a.gref0 = h->wg0 * lbm::kCRef;
+        a.gref1 = h->wg1 * lbm::kCRef;
+    }
+    h->mask_words(h->step, a.open_mask);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LBM_CUDA(h, cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    lbm::StepLaunch best{};
+    float best_ms = 0.f;
+    for (const Cand& c : cands) {
+        if (e != cudaSuccess) break;
+        lbm::StepLaunch L{};
+        L.precision = h->precision;
+        if (c.variant == 1) {
+            L.variant = lbm::kVariantRegs;
+            L.block = 32 * c.warps;
+            L.stages = 0;
+        } else if (c.variant == 2) {
+            L.variant = lbm::kVariantBulk;
+            L.block = 32 * (c.warps + 1);
+            L.stages = c.warps * c.per;
+        } else {
+            L.variant = lbm::kVariantPipe;
+            L.block = 32 * c.warps;
+            L.stages = c.warps * c.per;
+        }
+        int per_sm = 0;
+        if (lbm::step_kernel_occupancy(L, &per_sm) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        L.grid = std::min(wave_grid(h, L, per_sm), h->partials_cap);
+        e = cudaMemsetAsync(err, 0, sizeof(unsigned), h->stream);
+        for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = lbm::launch_step(a, L, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int j = 0; j < trial_steps && e == cudaSuccess; ++j) e = lbm::launch_step(a, L, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        unsigned ew = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&ew, err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && (ew & 2u) == 0 && (best.grid == 0 || ms < best_ms)) {
+            best = L;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune trial");
+    if (best.grid == 0) return fail(h, LBM_ERR_STATE, "no launch shape completed its trial steps");
+    if (best.variant != h->launch.variant || best.block != h->launch.block || best.stages != h->launch.stages ||
+        best.grid != h->launch.grid) {
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old shape
+        h->graphs.clear();
+        h->launch = best;
+    }
     return LBM_OK;
 }
 

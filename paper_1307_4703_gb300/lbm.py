@@ -49,7 +49,7 @@ class lbm_options(ctypes.Structure):
                 ("alloc_user", ctypes.c_void_p), ("block_threads", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("consumer_warps", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
 
 
 class lbm_info(ctypes.Structure):
@@ -137,6 +137,7 @@ SIGNATURES = {
     "lbm_set_instance_valves": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32]),
     "lbm_set_instance_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                                  _u32p]),
+    "lbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lbm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -211,7 +212,7 @@ class Chip:
     def __init__(self, solid, tau, tau_c, ports=(), edge_u=None, edge_C=None, w0=1.0 / 3.0,
                  rho0=1.0, C0=0.0, stream=None, torch_alloc=False, device=-1, block_threads=0,
                  max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0, precision="fp32",
-                 _batch=None):
+                 graph_steps=0, _batch=None):
         self._lib = load()
         if _batch is None:
             solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
@@ -229,6 +230,7 @@ class Chip:
         opt.pipeline_stages = int(pipeline_stages)
         opt.consumer_warps = int(consumer_warps)
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opt.graph_steps = int(graph_steps)
         self.stream = stream
         if stream is not None:
             opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
@@ -425,6 +427,11 @@ class Chip:
 
     def scalar_step(self, n=1, u_scale=1.0):
         self._check(self._lib.lbm_scalar_step(self._h, int(n), float(u_scale)))
+
+    def autotune(self, trial_steps=0):
+        """Keep the fastest launch shape of the step kernel (lbm_autotune)."""
+        self._check(self._lib.lbm_autotune(self._h, int(trial_steps)))
+        return self.info()
 
     def info(self):
         i = lbm_info()

@@ -1,0 +1,88 @@
+"""CUDA-graph replay of step runs (graph_steps) and the launch-shape
+autotuner (lbm_autotune): both change how steps are launched, never what
+they compute, so the populations must stay bit-identical."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1307_4703_gb300 import lbm, workloads as W  # noqa: E402
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1307_4703_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def _same(a, b):
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    return np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+@pytest.mark.parametrize("graph_steps", [2, 10, 64])
+def test_graph_replay_is_bit_identical(graph_steps):
+    """Valve switches every 25 steps split the runs: graphs where the valve
+    word holds for graph_steps steps, single launches elsewhere."""
+    prob, init = W.random_case(12, 300, 20)
+    a = lbm.Chip.from_problem(prob)
+    b = lbm.Chip.from_problem(prob, graph_steps=graph_steps)
+    for c in (a, b):
+        c.init_equilibrium(**init)
+        c.set_valve_schedule(25, prob["states"])
+    for n in (137, 1, 64, 3):
+        a.step(n)
+        b.step(n)
+    assert a.step_count() == b.step_count() == 205
+    assert _same(a, b)
+    assert np.array_equal(a.diagnostics(), b.diagnostics())
+    a.close()
+    b.close()
+
+
+def test_graph_replay_on_a_batch_with_own_valve_programs():
+    chips = W.config_batch(3, seed=6)
+    a = lbm.Chip.batch(chips)
+    b = lbm.Chip.batch(chips, graph_steps=20)
+    for c in (a, b):
+        for k, p in enumerate(chips):
+            c.set_instance_schedule(k, 30 + 17 * k, p["states"])
+        c.step(250)
+    assert _same(a, b)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_autotune_keeps_the_state_and_the_results(prec):
+    prob = W.config_small()
+    a = lbm.Chip.from_problem(prob, precision=prec)
+    b = lbm.Chip.from_problem(prob, precision=prec, graph_steps=8)
+    for c in (a, b):
+        c.set_valve_schedule(prob["period"], prob["states"])
+        c.step(100)
+    d0 = b.diagnostics()
+    f0, g0 = b.populations()
+    info = b.autotune(trial_steps=5)
+    assert info["variant"] in (1, 2, 3) and info["grid"] >= 1
+    assert b.step_count() == 100
+    f1, g1 = b.populations()
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    assert np.array_equal(b.diagnostics(), d0)
+    for c in (a, b):
+        c.step(300)
+    assert _same(a, b)
+    a.close()
+    b.close()
+
+
+def test_graph_steps_must_be_even():
+    prob = W.config_small()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Chip.from_problem(prob, graph_steps=3)
+    assert e.value.status == lbm.LBM_ERR_ARG
