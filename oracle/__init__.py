@@ -16,7 +16,7 @@ import numpy as np
 from .build import build_oracle
 
 WEST, EAST = 0, 1
-VELOCITY, PRESSURE = 0, 1
+VELOCITY, PRESSURE, PRESSURE_RESCALE, INLET_RESCALE = 0, 1, 2, 3
 
 
 class _Port(ctypes.Structure):
@@ -49,6 +49,7 @@ def _load():
         lib.orc_lattice_vectors.argtypes = [P(ctypes.c_int), P(ctypes.c_int), d]
         lib.orc_adjoint_step.argtypes = [ctypes.c_void_p, ctypes.c_uint, d, d, d, d, d, d, d]
         lib.orc_scalar_step.argtypes = [ctypes.c_void_p, ctypes.c_uint, d, d]
+        lib.orc_set_decay.argtypes = [ctypes.c_void_p, ctypes.c_double]
         lib.orc_adjoint.restype = ctypes.c_double
         lib.orc_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_uint), ctypes.c_int,
                                     P(ctypes.c_int), P(ctypes.c_int), d, d, d, d, d]
@@ -81,7 +82,7 @@ class OracleLattice:
     """
 
     def __init__(self, solid, tau_f, tau_g, w0=1.0 / 3.0, periodic=False, ports=(),
-                 edge_u=None, edge_C=None):
+                 edge_u=None, edge_C=None, decay=0.0):
         lib = _load()
         solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
         self.ny, self.nx = solid.shape
@@ -104,6 +105,8 @@ class OracleLattice:
         self._h = ctypes.c_void_p(h)
         self._lib = lib
         self.t = 0
+        if decay:
+            lib.orc_set_decay(self._h, float(decay))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -190,7 +193,7 @@ class OracleLattice:
                                   ox.ctypes.data_as(ip), oy.ctypes.data_as(ip), _dptr(tg), _dptr(wt),
                                   _dptr(dtau), _dptr(du), _dptr(dc))
         if J < 0:
-            raise MemoryError("oracle adjoint: trajectory does not fit in host memory")
+            raise ValueError("oracle adjoint: needs Zou-He ports and no decay, and the trajectory in host memory")
         self.t += int(n)
         return J, float(dtau[0]), du, dc
 
@@ -211,6 +214,7 @@ def schedule_fn(period=None, states=None, fixed=None):
 def from_problem(prob, **over):
     """Build an OracleLattice from a problem dict of the seeded generators."""
     kw = dict(tau_f=prob["tau"], tau_g=prob["tau_c"], w0=prob.get("w0", 1.0 / 3.0),
-              ports=prob["ports"], edge_u=prob["edge_u"], edge_C=prob["edge_C"])
+              ports=prob["ports"], edge_u=prob["edge_u"], edge_C=prob["edge_C"],
+              decay=prob.get("decay", 0.0))
     kw.update(over)
     return OracleLattice(prob["solid"], **kw)

@@ -35,6 +35,7 @@ static const double W9[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
 struct orc_lattice {
     int nx, ny, periodic;
     double tau_f, tau_g, w0;
+    double decay;          /* k of the reaction term R = -k C */
     unsigned char* solid;  /* ny*nx */
     double* f;             /* pre-collision f_i(x,t), [node*9 + i] */
     double* g;             /* pre-collision g_i(x,t), [node*5 + i] */
@@ -147,7 +148,8 @@ orc_lattice* orc_new(int nx, int ny, const unsigned char* solid,
         int ok = P->channel >= 0 && P->channel < 32 && P->x >= 0 &&
                  P->x < nx && P->y0 >= 0 && P->y0 < P->y1 && P->y1 <= ny &&
                  (P->side == ORC_WEST || P->side == ORC_EAST) &&
-                 (P->kind == ORC_VELOCITY || P->kind == ORC_PRESSURE);
+                 P->kind >= ORC_VELOCITY && P->kind <= ORC_INLET_RESCALE &&
+                 (P->kind == ORC_VELOCITY || P->rho > 0.0);
         for (int y = P->y0; ok && y < P->y1; ++y)
             ok = L->solid[y * nx + P->x] == 0;
         if (!ok) {
@@ -182,6 +184,8 @@ void orc_free(orc_lattice* L)
     free(L);
 }
 
+void orc_set_decay(orc_lattice* L, double k) { L->decay = k; }
+
 void orc_init_equilibrium(orc_lattice* L, const double* rho, const double* ux,
                           const double* uy, const double* C)
 {
@@ -212,9 +216,40 @@ static void collide_all(const orc_lattice* L, double* fp, double* gp)
             for (int i = 0; i < 9; ++i)
                 fp[c * 9 + i] = fn[i] - (fn[i] - feq(i, rho, ux, uy)) / L->tau_f;
             double C = scalar_moment(gn);
+            double R = -L->decay * C;  /* reaction term of Eq. cde */
             for (int i = 0; i < 5; ++i)
-                gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux, uy)) / L->tau_g;
+                gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux, uy)) / L->tau_g + wg(L, i) * R;
         }
+}
+
+/* The paper's port boundary for f (section "Boundary Conditions"): the
+ * unknown populations (e_x = s) keep the node's own post-collision values
+ * fpn of the previous step, then every population is rescaled by
+ * gamma = rho_port / sum f_i. */
+static void rescale_port_f(double* fn, const double* fpn, int s, double rho_port)
+{
+    int unknown[3] = {s > 0 ? 1 : 3, s > 0 ? 5 : 6, s > 0 ? 8 : 7};
+    for (int k = 0; k < 3; ++k) fn[unknown[k]] = fpn[unknown[k]];
+    double sum = 0.0;
+    for (int i = 0; i < 9; ++i) sum += fn[i];
+    double gamma = rho_port / sum;
+    for (int i = 0; i < 9; ++i) fn[i] *= gamma;
+}
+
+/* The same for g at an inlet: do-nothing for the unknown population, then
+ * all five rescaled to C_in; with no compound at the node, the equilibrium
+ * of C_in at the node's velocity. */
+static void rescale_port_g(const orc_lattice* L, double* gn, const double* gpn, int g_in, double C_in,
+                           double ux, double uy)
+{
+    gn[g_in] = gpn[g_in];
+    double sum = scalar_moment(gn);
+    if (sum > 0.0) {
+        double gamma = C_in / sum;
+        for (int i = 0; i < 5; ++i) gn[i] *= gamma;
+    } else {
+        for (int i = 0; i < 5; ++i) gn[i] = geq(L, i, C_in, ux, uy);
+    }
 }
 
 /* Zou-He completion of the three unknown populations of a port node.  s is
@@ -311,10 +346,19 @@ void orc_step(orc_lattice* L, unsigned open_mask)
                 for (int i = 0; i < 5; ++i)
                     if (i != g_in) others += gn[i];
                 gn[g_in] = L->edge_C[P->side * ny + y] - others;
-            } else {
+            } else if (P->kind == ORC_PRESSURE) {
                 zou_he(fn, s, ORC_PRESSURE, 0.0, P->rho);
                 /* do-nothing: zeroth-order extrapolation in time */
                 gn[g_in] = L->gp[c * 5 + g_in];
+            } else {
+                rescale_port_f(fn, L->fp + (size_t)c * 9, s, P->rho);
+                if (P->kind == ORC_PRESSURE_RESCALE) {
+                    gn[g_in] = L->gp[c * 5 + g_in];
+                } else {
+                    double r, ux, uy;
+                    moments(fn, &r, &ux, &uy);
+                    rescale_port_g(L, gn, L->gp + (size_t)c * 5, g_in, L->edge_C[P->side * ny + y], ux, uy);
+                }
             }
         }
     }
@@ -380,7 +424,7 @@ void orc_diagnostics(const orc_lattice* L, unsigned open_mask, double out[4])
         }
     for (int p = 0; p < L->n_ports; ++p) {
         const orc_port* P = &L->ports[p];
-        if (P->kind != ORC_PRESSURE || !((open_mask >> P->channel) & 1u))
+        if ((P->kind != ORC_PRESSURE && P->kind != ORC_PRESSURE_RESCALE) || !((open_mask >> P->channel) & 1u))
             continue;
         for (int y = P->y0; y < P->y1; ++y) {
             int c = node(L, P->x, y);
@@ -593,6 +637,9 @@ double orc_adjoint(orc_lattice* L, int n, const unsigned* masks, int n_obj,
                    double* dJ_dC_in)
 {
     const int ny = L->ny;
+    if (L->decay != 0.0) return -1.0;
+    for (int p = 0; p < L->n_ports; ++p)
+        if (L->ports[p].kind != ORC_VELOCITY && L->ports[p].kind != ORC_PRESSURE) return -1.0;
     size_t nodes = (size_t)L->nx * (size_t)ny;
     double* fs = (double*)malloc((size_t)(n + 1) * nodes * 9 * sizeof(double));
     double* gs = (double*)malloc((size_t)(n + 1) * nodes * 5 * sizeof(double));
@@ -643,8 +690,9 @@ void orc_scalar_step(orc_lattice* L, unsigned open_mask, const double* ux, const
             int c = node(L, x, y);
             const double* gn = L->g + (size_t)c * 5;
             double C = scalar_moment(gn);
+            double R = -L->decay * C;  /* reaction term of Eq. cde */
             for (int i = 0; i < 5; ++i)
-                L->gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux[c], uy[c])) / L->tau_g;
+                L->gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux[c], uy[c])) / L->tau_g + wg(L, i) * R;
         }
     /* free flight with halfway bounce-back */
     for (int y = 0; y < ny; ++y)
@@ -674,6 +722,8 @@ void orc_scalar_step(orc_lattice* L, unsigned open_mask, const double* ux, const
                 for (int i = 0; i < 5; ++i)
                     if (i != g_in) others += gn[i];
                 gn[g_in] = L->edge_C[P->side * ny + y] - others;
+            } else if (P->kind == ORC_INLET_RESCALE) {
+                rescale_port_g(L, gn, L->gp + (size_t)c * 5, g_in, L->edge_C[P->side * ny + y], ux[c], uy[c]);
             } else {
                 gn[g_in] = L->gp[c * 5 + g_in];
             }

@@ -28,6 +28,20 @@
  *           extrapolation in time of section "Boundary Conditions").  A
  *           closed port is a wall (section "Results": closed valves are an
  *           ordinary no-flux wall).
+ *           The paper's own port boundary (section "Boundary Conditions") is
+ *           kept as two more kinds: the unknown populations of f keep the
+ *           node's own post-collision values of the previous step
+ *           (do-nothing), then all nine are rescaled by
+ *           gamma = rho_port / sum f_i to the prescribed density, which
+ *           leaves u unchanged.  ORC_PRESSURE_RESCALE is an outlet (g:
+ *           do-nothing); ORC_INLET_RESCALE is an inlet whose scalar is set
+ *           the same way: do-nothing for the unknown g, then all five are
+ *           rescaled to C_in.  When the node holds no compound (sum g = 0)
+ *           there is nothing to rescale, and the five take the equilibrium
+ *           g_eq(C_in, u) instead.
+ *   decay   the reaction term R = -k C of Eq. cde (the decaying compound of
+ *           section "Results"), added to the scalar collision as w_i R, so
+ *           that the step removes k C from the node's concentration.
  *
  * Populations are stored per node, f[(y*nx + x)*9 + i], g[(y*nx + x)*5 + i],
  * and are the PRE-collision values f_i(x, t) of Eq. lbequation.
@@ -40,7 +54,7 @@ extern "C" {
 #endif
 
 enum { ORC_WEST = 0, ORC_EAST = 1 };
-enum { ORC_VELOCITY = 0, ORC_PRESSURE = 1 };
+enum { ORC_VELOCITY = 0, ORC_PRESSURE = 1, ORC_PRESSURE_RESCALE = 2, ORC_INLET_RESCALE = 3 };
 
 /* One valve-controlled opening.  It covers the nodes (x, y) for
  * y0 <= y < y1.  WEST: fluid enters or leaves towards -x, so the populations
@@ -51,8 +65,8 @@ typedef struct {
     int side;      /* ORC_WEST or ORC_EAST */
     int x;         /* node column */
     int y0, y1;    /* rows [y0, y1) */
-    int kind;      /* ORC_VELOCITY or ORC_PRESSURE */
-    double rho;    /* prescribed density of a pressure port */
+    int kind;      /* ORC_VELOCITY, ORC_PRESSURE, ORC_PRESSURE_RESCALE, ORC_INLET_RESCALE */
+    double rho;    /* prescribed density of a pressure port (kinds 1-3) */
 } orc_port;
 
 typedef struct orc_lattice orc_lattice;
@@ -68,6 +82,9 @@ orc_lattice* orc_new(int nx, int ny, const unsigned char* solid,
                      int n_ports, const orc_port* ports,
                      const double* edge_u, const double* edge_C);
 void orc_free(orc_lattice* L);
+
+/* Decay rate k >= 0 of the compound (default 0). */
+void orc_set_decay(orc_lattice* L, double k);
 
 /* Set every fluid node to the equilibrium of the given fields (ny*nx). */
 void orc_init_equilibrium(orc_lattice* L, const double* rho, const double* ux,
@@ -91,7 +108,8 @@ void orc_post_collision(const orc_lattice* L, double* f, double* g);
 
 /* out[0] = sum rho over fluid nodes, out[1] = sum C over fluid nodes,
  * out[2] = sum rho*u_x and out[3] = sum C*u_x over the nodes of the
- * pressure ports that are open under open_mask. */
+ * outlet ports (kinds ORC_PRESSURE and ORC_PRESSURE_RESCALE) that are open
+ * under open_mask. */
 void orc_diagnostics(const orc_lattice* L, unsigned open_mask, double out[4]);
 
 /* Lattice tables as the oracle uses them (for checks against Eq. lattice). */
@@ -118,7 +136,9 @@ void orc_adjoint_step(const orc_lattice* L, unsigned open_mask, const double* f_
                       const double* g_t, const double* f_t1, const double* g_t1,
                       double* af, double* ag, double* grad);
 
-/* Run n steps forward from the current state with the given valve words
+/* Adjoint of lattices whose ports are of kinds ORC_VELOCITY and
+ * ORC_PRESSURE and without decay (orc_adjoint returns -1 otherwise).
+ * Run n steps forward from the current state with the given valve words
  * (the lattice ends at S_n, as after n calls of orc_step), then the reverse
  * pass for J = sum_k weight_k (C(x_k, y_k, n) - target_k)^2.  Returns J and
  * writes dJ/dtau_g, dJ/du_in (2*ny) and dJ/dC_in (2*ny).  Keeps every state

@@ -59,7 +59,8 @@ MUTANTS = [
     ("outlet mass flux without u", "q += r * ux;", "q += r;"),
     ("outlet scalar flux without u", "qc += scalar_moment(L->g + (size_t)c * 5) * ux;",
      "qc += scalar_moment(L->g + (size_t)c * 5);"),
-    ("flux over velocity ports too", "if (P->kind != ORC_PRESSURE || !((open_mask >> P->channel) & 1u))",
+    ("flux over velocity ports too",
+     "if ((P->kind != ORC_PRESSURE && P->kind != ORC_PRESSURE_RESCALE) || !((open_mask >> P->channel) & 1u))",
      "if (!((open_mask >> P->channel) & 1u))"),
     ("diagonal weight", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 18.0};"),
 ]
@@ -83,8 +84,28 @@ ADJOINT_MUTANTS = [
 ]
 
 
+# slips in the decay term and the paper's rescaling ports, caught by
+# tests/test_oracle_paper_bc.py
+PAPER_BC_MUTANTS = [
+    ("decay adds compound", "double R = -L->decay * C;  /* reaction term of Eq. cde */",
+     "double R = L->decay * C;  /* reaction term of Eq. cde */"),
+    ("decay on every population", "+ wg(L, i) * R;\n        }\n}", "+ R;\n        }\n}"),
+    ("decay skipped in the scalar-only step",
+     "L->gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux[c], uy[c])) / L->tau_g + wg(L, i) * R;",
+     "L->gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux[c], uy[c])) / L->tau_g;"),
+    ("rescale factor inverted", "double gamma = rho_port / sum;", "double gamma = sum / rho_port;"),
+    ("port unknowns not carried over", "for (int k = 0; k < 3; ++k) fn[unknown[k]] = fpn[unknown[k]];",
+     "(void)fpn;"),
+    ("port unknowns of the other side", "int unknown[3] = {s > 0 ? 1 : 3, s > 0 ? 5 : 6, s > 0 ? 8 : 7};",
+     "int unknown[3] = {s > 0 ? 3 : 1, s > 0 ? 7 : 8, s > 0 ? 6 : 5};"),
+    ("scalar rescaled to 1", "double gamma = C_in / sum;", "double gamma = 1.0 / sum;"),
+    ("scalar fallback at rest", "for (int i = 0; i < 5; ++i) gn[i] = geq(L, i, C_in, ux, uy);",
+     "for (int i = 0; i < 5; ++i) gn[i] = geq(L, i, C_in, 0.0, 0.0);"),
+]
+
 CASES = [m + ("tests/test_oracle_pins.py",) for m in MUTANTS] + \
-        [m + ("tests/test_oracle_adjoint.py",) for m in ADJOINT_MUTANTS]
+        [m + ("tests/test_oracle_adjoint.py",) for m in ADJOINT_MUTANTS] + \
+        [m + ("tests/test_oracle_paper_bc.py",) for m in PAPER_BC_MUTANTS]
 
 
 @pytest.mark.parametrize("name,old,new,pins", CASES, ids=[m[0] for m in CASES])
