@@ -60,7 +60,7 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_WEST = 0, LBM_EAST = 1 };
-enum { LBM_PORT_VELOCITY = 0, LBM_PORT_PRESSURE = 1 };
+enum { LBM_PORT_VELOCITY = 0, LBM_PORT_PRESSURE = 1, LBM_PORT_PRESSURE_RESCALE = 2, LBM_PORT_INLET_RESCALE = 3 };
 
 /* One valve-controlled opening of the chip ("Experimental Layout and
  * Conditions": each channel's inlet and outlet are controlled by valves).
@@ -78,15 +78,25 @@ enum { LBM_PORT_VELOCITY = 0, LBM_PORT_PRESSURE = 1 };
  * pressure node with density `rho` and zero tangential velocity for the
  * fluid, do-nothing for the scalar (its missing population keeps its own
  * post-collision value of the previous step: zeroth-order extrapolation in
- * time).  Closed port: wall, as everywhere else. */
+ * time).  Closed port: wall, as everywhere else.
+ *
+ * The paper's own port ("Boundary Conditions"), as two more kinds: the
+ * missing f keep the node's own post-collision values of the previous step
+ * (do-nothing), then all nine are scaled by gamma = rho / sum f_i to the
+ * prescribed density (u does not change).  PRESSURE_RESCALE (an outlet):
+ * do-nothing for the scalar.  INLET_RESCALE (a pressure-driven inlet): the
+ * scalar gets do-nothing for its missing population, then all five are
+ * scaled to the concentration C_in(y) of edge_C; a node without compound
+ * (sum g = 0) takes the equilibrium of C_in at its velocity instead.
+ * Lattices with these kinds support every call but lbm_adjoint. */
 typedef struct {
     int32_t channel;
     int32_t side;   /* LBM_WEST or LBM_EAST */
     int32_t x;
     int32_t y0;
     int32_t y1;
-    int32_t kind;   /* LBM_PORT_VELOCITY or LBM_PORT_PRESSURE */
-    double rho;     /* PRESSURE ports: prescribed density (> 0) */
+    int32_t kind;   /* LBM_PORT_VELOCITY, _PRESSURE, _PRESSURE_RESCALE or _INLET_RESCALE */
+    double rho;     /* all kinds but VELOCITY: prescribed density (> 0) */
 } lbm_port;
 
 /* Device allocator hooks.  alloc returns a device pointer (>= 256-byte
@@ -116,6 +126,9 @@ typedef struct {
     int32_t consumer_warps; /* variants 2, 3: computing warps per block, 0 = default (2: 3, 3: 4),
                                else 1..7 (variant 2) or 1..8 (variant 3) */
     int32_t precision;      /* storage of the populations (LBM_FP32, LBM_FP16, LBM_BF16), see below */
+    double decay;           /* decay rate k >= 0 of the compound: the reaction term R = -k C of the
+                               advection-diffusion equation ("Introduction", "Results"), added to
+                               the scalar collision as w_i R (default 0); not with lbm_adjoint */
     int32_t graph_steps;    /* 0 = off; else an even number <= 4096: lbm_step replays runs of this many
                                steps with unchanged valve words as one cached CUDA graph (captured
                                on first use, at most 16 per handle), which removes the per-launch

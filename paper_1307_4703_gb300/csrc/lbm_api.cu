@@ -111,6 +111,8 @@ struct lbm_ctx {
     };
     int graph_steps = 0;
     cudaStream_t cap_stream = nullptr;
+    float decay = 0.f;         // k of the reaction term R = -k C
+    bool paper_ports = false;  // some port has a rescaling kind (no adjoint)
     std::vector<Graph> graphs;
 
     // Whether the valve words stay the same over steps [t0, t0 + len).
@@ -391,6 +393,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     }
     if ((opt.alloc == nullptr) != (opt.free == nullptr))
         return fail(nullptr, LBM_ERR_ARG, "alloc and free hooks must be given together");
+    if (!(opt.decay >= 0.0 && opt.decay < 1.0))
+        return fail(nullptr, LBM_ERR_ARG, "decay = %g outside [0, 1)", opt.decay);
     if (opt.graph_steps < 0 || opt.graph_steps % 2 != 0 || opt.graph_steps > kMaxGraphSteps)
         return fail(nullptr, LBM_ERR_ARG, "graph_steps = %d: use 0 or an even number up to %d", opt.graph_steps,
                     kMaxGraphSteps);
@@ -405,19 +409,19 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (fluid == 0) return fail(nullptr, LBM_ERR_ARG, "the mask has no fluid node");
 
     std::vector<lbm::RowBC> rowbc(size_t(2) * ny, lbm::RowBC{-1, 0, 0.f, 0.f});
-    bool any_velocity = false;
+    bool any_velocity = false, any_inlet = false;
     for (int p = 0; p < n_ports; ++p) {
         const lbm_port& P = ports[p];
         if (P.channel < 0 || P.channel > max_channel)
             return fail(nullptr, LBM_ERR_ARG, "port %d: channel %d outside [0, %d]", p, P.channel, max_channel);
         if (P.side != LBM_WEST && P.side != LBM_EAST)
             return fail(nullptr, LBM_ERR_ARG, "port %d: side %d invalid", p, P.side);
-        if (P.kind != LBM_PORT_VELOCITY && P.kind != LBM_PORT_PRESSURE)
+        if (P.kind < LBM_PORT_VELOCITY || P.kind > LBM_PORT_INLET_RESCALE)
             return fail(nullptr, LBM_ERR_ARG, "port %d: kind %d invalid", p, P.kind);
         if (P.x < 0 || P.x >= nx || P.y0 < 0 || P.y1 > ny || P.y0 >= P.y1)
             return fail(nullptr, LBM_ERR_ARG, "port %d: column %d rows [%d, %d) outside the grid", p,
                         P.x, P.y0, P.y1);
-        if (P.kind == LBM_PORT_PRESSURE && !(P.rho > 0.0 && std::isfinite(P.rho)))
+        if (P.kind != LBM_PORT_VELOCITY && !(P.rho > 0.0 && std::isfinite(P.rho)))
             return fail(nullptr, LBM_ERR_ARG, "port %d: pressure density %g invalid", p, P.rho);
         const int s = P.side == LBM_WEST ? 1 : -1;
         for (int y = P.y0; y < P.y1; ++y) {
@@ -430,20 +434,29 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
                 return fail(nullptr, LBM_ERR_ARG, "port %d: node (%d, %d) is also a port of the other side", p, P.x, y);
             b.x = P.x;
             b.chan_kind = P.channel | (P.kind << 8);
-            b.a = P.kind == LBM_PORT_PRESSURE ? float(P.rho - 1.0) : 0.f;
+            b.a = P.kind != LBM_PORT_VELOCITY ? float(P.rho - 1.0) : 0.f;
         }
         for (int y = P.y0 - 1; y <= P.y1; ++y)
             if (is_fluid(mask, nx, ny, P.x - s, y))
                 return fail(nullptr, LBM_ERR_ARG, "port %d: cell (%d, %d) outside the port is fluid", p,
                             P.x - s, y);
         any_velocity |= P.kind == LBM_PORT_VELOCITY;
+        any_inlet |= P.kind == LBM_PORT_INLET_RESCALE;
     }
     if (any_velocity && (!edge_u || !edge_C))
         return fail(nullptr, LBM_ERR_ARG, "velocity ports need edge_u and edge_C");
+    if (any_inlet && !edge_C) return fail(nullptr, LBM_ERR_ARG, "INLET_RESCALE ports need edge_C");
     for (int side = 0; side < 2; ++side)
         for (int y = 0; y < ny; ++y) {
             lbm::RowBC& b = rowbc[size_t(side) * ny + y];
-            if (b.x < 0 || (b.chan_kind >> 8) != LBM_PORT_VELOCITY) continue;
+            if (b.x < 0) continue;
+            const int kind = b.chan_kind >> 8;
+            if (kind == LBM_PORT_INLET_RESCALE) {
+                const float c = edge_C[size_t(side) * ny + y];
+                if (!std::isfinite(c)) return fail(nullptr, LBM_ERR_ARG, "inlet port row %d: C = %g invalid", y, c);
+                b.c = c;
+            }
+            if (kind != LBM_PORT_VELOCITY) continue;
             const float u = edge_u[size_t(side) * ny + y], c = edge_C[size_t(side) * ny + y];
             if (!(std::fabs(u) < 1.f) || !std::isfinite(c))
                 return fail(nullptr, LBM_ERR_ARG, "velocity port row %d: u_x = %g, C = %g invalid", y, u, c);
@@ -506,6 +519,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->precision = opt.precision;
     h->elem = opt.precision == LBM_FP32 ? sizeof(float) : sizeof(uint16_t);
     h->graph_steps = opt.graph_steps;
+    h->decay = float(opt.decay);
+    for (int p = 0; p < n_ports; ++p) h->paper_ports |= ports[p].kind >= LBM_PORT_PRESSURE_RESCALE;
 
     auto bail = [&](lbm_status s) {
         g_create_error = h->last_error;
@@ -583,10 +598,10 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         e = cudaMemsetAsync(h->partials, 0, size_t(h->partials_cap) * 4 * sizeof(double), st);
     if (e == cudaSuccess)
         e = lbm::launch_init_rest(h->pop[0], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0),
-                                  h->precision, st);
+                                  h->precision, h->decay, st);
     if (e == cudaSuccess)
         e = lbm::launch_init_rest(h->pop[1], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0),
-                                  h->precision, st);
+                                  h->precision, h->decay, st);
     // the host tables above are pageable: wait so they may go out of scope
     if (e == cudaSuccess && h->graph_steps > 0) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -794,6 +809,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     a.wg0 = h->wg0;
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
+    a.decay = h->decay;
     a.partials = h->partials;
     a.err = h->err;
     a.rates = h->rates;
@@ -867,7 +883,7 @@ lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy,
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (lbm_status js = join_scalar(h)) return js;
     cudaError_t e = lbm::launch_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, rho, ux, uy, C, h->wg0,
-                                       h->wg1, h->precision, h->stream);
+                                       h->wg1, h->precision, h->decay, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "fields kernel launch");
     return LBM_OK;
 }
@@ -1047,7 +1063,7 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* ux,
         LBM_CUDA(h, cudaMemcpyAsync(t + q * n, ins[q], n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     cudaError_t e = lbm::launch_init_fields(h->pop[h->cur], h->links, h->nx, h->ny, h->pitch, t, t + n,
                                             t + 2 * n, t + 3 * n, h->wg0, h->wg1, h->inv_cs2g, h->precision,
-                                            h->stream);
+                                            h->decay, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "equilibrium kernel launch");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
@@ -1128,6 +1144,8 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_adjoint");
     if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_adjoint");
+    if (h->decay != 0.f || h->paper_ports)
+        return fail(h, LBM_ERR_STATE, "lbm_adjoint needs Zou-He ports and no decay");
     if (!obj || !J || !dJ_dtau_c) return fail(h, LBM_ERR_ARG, "objective, J or dJ_dtau_c is NULL");
     if (n < 1 || K < 1) return fail(h, LBM_ERR_ARG, "n_steps = %lld and ckpt_every = %d must be >= 1", (long long)n, K);
     if (obj->n < 1 || !obj->x || !obj->y || !obj->target || !obj->weight)
@@ -1352,6 +1370,7 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
     a.wg0 = h->wg0;
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
+    a.decay = h->decay;
     a.partials = h->partials;
     a.n_partials = h->diag_grid;
     a.err = h->err;
@@ -1430,6 +1449,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     a.wg0 = h->wg0;
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
+    a.decay = h->decay;
     a.partials = part;
     a.err = err;
     if (h->precision != LBM_FP32) {

@@ -297,42 +297,69 @@ __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, c
 
 // Completion of an open port node (fluid populations as deviations
 // f_i - w_i).  west: the port receives from -x, so the populations with
-// e_x = +1 are unknown (s = +1); otherwise e_x = -1 (s = -1).  Velocity port:
-// Zou-He with u = (u_x, 0) and the held concentration C_in for the scalar's
-// unknown population.  Pressure port: Zou-He with the prescribed density and
-// zero tangential velocity; the scalar's unknown population keeps its own
-// post-collision value of the previous step (read from the source buffer at
-// index own).  Returns true for a pressure node.
+// e_x = +1 are unknown (s = +1); otherwise e_x = -1 (s = -1).  The port kind
+// (bits 8..15 of chan_kind):
+//   0 velocity  Zou-He with u = (u_x, 0); the scalar's unknown population
+//               makes the node's concentration C_in.
+//   1 pressure  Zou-He with the prescribed density and zero tangential
+//               velocity; the scalar's unknown population keeps its own
+//               post-collision value of the previous step (do-nothing).
+//   2, 3        the paper's port (section "Boundary Conditions"): the
+//               unknown f keep their own post-collision values, then all
+//               nine are scaled by gamma = rho_port / rho, which leaves u as
+//               it is.  Kind 2 (outlet): do-nothing for the scalar.  Kind 3
+//               (inlet): do-nothing for the unknown g, then all five scaled to
+//               C_in; a node without compound takes g_eq(C_in, u) instead.
+// Post-collision values of the previous step are read from the source
+// buffer at index own.  Returns true for an outlet node (kinds 1, 2).
 template <typename T>
 __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool west, const RowBC& b,
-                                              const T* S, long long P, long long own, float gref1 = 0.f)
+                                              const T* S, long long P, long long own, float gref1 = 0.f,
+                                              float wg1 = 0.f, float inv_cs2g = 0.f)
 {
-    const float s = west ? 1.f : -1.f;
-    const bool velocity = ((b.chan_kind >> 8) & 0xFF) == 0;
-    // populations leaving through the port: e = (-s, 0), (-s, -1), (-s, +1)
-    const float fo_ax = west ? f[3] : f[1];
-    const float fo_dn = west ? f[7] : f[8];
-    const float fo_up = west ? f[6] : f[5];
-    // rho (1 - s u_x) = f0 + f2 + f4 + 2 (leaving) = 1 + Kd in deviations
-    // (the weights of those populations add up to one)
-    const float Kd = f[0] + f[2] + f[4] + 2.f * (fo_ax + fo_dn + fo_up);
-    float jx;  // rho u_x of the node
-    if (velocity) jx = (1.f + Kd) * b.a / (1.f - s * b.a);
-    else jx = s * (b.a - Kd);  // b.a = prescribed rho - 1
-    const float ht = 0.5f * (f[2] - f[4]);
-    const float fi_ax = fo_ax + s * (2.f / 3.f) * jx;
-    const float fi_up = fo_dn - ht + s * (1.f / 6.f) * jx;  // e = (s, +1)
-    const float fi_dn = fo_up + ht + s * (1.f / 6.f) * jx;  // e = (s, -1)
-    if (west) {
-        f[1] = fi_ax;
-        f[5] = fi_up;
-        f[8] = fi_dn;
+    const int kind = (b.chan_kind >> 8) & 0xFF;
+    if (kind <= 1) {
+        const float s = west ? 1.f : -1.f;
+        // populations leaving through the port: e = (-s, 0), (-s, -1), (-s, +1)
+        const float fo_ax = west ? f[3] : f[1];
+        const float fo_dn = west ? f[7] : f[8];
+        const float fo_up = west ? f[6] : f[5];
+        // rho (1 - s u_x) = f0 + f2 + f4 + 2 (leaving) = 1 + Kd in deviations
+        // (the weights of those populations add up to one)
+        const float Kd = f[0] + f[2] + f[4] + 2.f * (fo_ax + fo_dn + fo_up);
+        float jx;  // rho u_x of the node
+        if (kind == 0) jx = (1.f + Kd) * b.a / (1.f - s * b.a);
+        else jx = s * (b.a - Kd);  // b.a = prescribed rho - 1
+        const float ht = 0.5f * (f[2] - f[4]);
+        const float fi_ax = fo_ax + s * (2.f / 3.f) * jx;
+        const float fi_up = fo_dn - ht + s * (1.f / 6.f) * jx;  // e = (s, +1)
+        const float fi_dn = fo_up + ht + s * (1.f / 6.f) * jx;  // e = (s, -1)
+        if (west) {
+            f[1] = fi_ax;
+            f[5] = fi_up;
+            f[8] = fi_dn;
+        } else {
+            f[3] = fi_ax;
+            f[6] = fi_up;
+            f[7] = fi_dn;
+        }
     } else {
-        f[3] = fi_ax;
-        f[6] = fi_up;
-        f[7] = fi_dn;
+        if (west) {
+            f[1] = Codec<T>::ld1(S + 1 * P + own, 0.f);
+            f[5] = Codec<T>::ld1(S + 5 * P + own, 0.f);
+            f[8] = Codec<T>::ld1(S + 8 * P + own, 0.f);
+        } else {
+            f[3] = Codec<T>::ld1(S + 3 * P + own, 0.f);
+            f[6] = Codec<T>::ld1(S + 6 * P + own, 0.f);
+            f[7] = Codec<T>::ld1(S + 7 * P + own, 0.f);
+        }
+        const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        // gamma - 1 = (rho_port - rho) / rho; f_i' <- f_i' + (gamma - 1) (w_i + f_i')
+        const float gm1 = (b.a - rd) / (1.f + rd);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] += gm1 * ((i == 0 ? kWr : i <= 4 ? kWa : kWd) + f[i]);
     }
-    if (velocity) {
+    if (kind == 0) {
         if (west) g[1] = b.c - (g[0] + g[2] + g[3] + g[4]);
         else g[3] = b.c - (g[0] + g[1] + g[2] + g[4]);
         return false;
@@ -340,7 +367,24 @@ __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool
     // do-nothing: the node keeps its own post-collision value
     if (west) g[1] = Codec<T>::ld1(S + 10 * P + own, gref1);
     else g[3] = Codec<T>::ld1(S + 12 * P + own, gref1);
-    return true;
+    if (kind != 3) return true;
+    const float Cs = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+    if (Cs > 0.f) {
+        const float gc = b.c / Cs;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] *= gc;
+    } else {
+        const float rho = 1.f + (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]);
+        const float ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7])) / rho;
+        const float uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8])) / rho;
+        const float c1 = wg1 * b.c, cx = c1 * inv_cs2g * ux, cy = c1 * inv_cs2g * uy;
+        g[0] = b.c - 4.f * c1;
+        g[1] = c1 + cx;
+        g[3] = c1 - cx;
+        g[2] = c1 + cy;
+        g[4] = c1 - cy;
+    }
+    return false;
 }
 
 // Free flight (pull) of one lane's four nodes x0..x0+3 with 128-bit loads:
@@ -434,7 +478,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         const bool pw = open_w && bw.x == xk;
         const bool pe = !pw && open_e && be.x == xk;
         bool pressure_node = false;
-        if (pw || pe) pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k, a.gref1);
+        if (pw || pe) pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k, a.gref1, a.wg1, a.inv_cs2g);
 
         // ---- moments (Eq. moments) and BGK collision of f, in deviations
         //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
@@ -474,6 +518,12 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
             g[3] += wg * ((c1 - cx) - g[3]);
             g[2] += wg * ((c1 + cy) - g[2]);
             g[4] += wg * ((c1 - cy) - g[4]);
+            if (a.decay != 0.f) {  // reaction term R = -k C of Eq. cde, as w_i R
+                const float R = -a.decay * C;
+                g[0] += a.wg0 * R;
+#pragma unroll
+                for (int i = 1; i < 5; ++i) g[i] += a.wg1 * R;
+            }
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) at(v[i], k) = f[i];

@@ -50,9 +50,10 @@ struct StepLaunch {
 
 struct RowBC {
     int32_t x;          // port node column, -1 = no port on this side and row
-    int32_t chan_kind;  // valve channel | (kind << 8); kind 0 velocity, 1 pressure
-    float a;            // velocity port: u_x; pressure port: rho - 1
-    float c;            // velocity port: held concentration
+    int32_t chan_kind;  // valve channel | (kind << 8); kind 0 velocity, 1 pressure,
+                        // 2 rescaling outlet, 3 rescaling inlet (the paper's ports)
+    float a;            // velocity port: u_x; other kinds: rho - 1
+    float c;            // kinds 0 and 3: the prescribed concentration
 };
 
 struct StepArgs {
@@ -72,6 +73,7 @@ struct StepArgs {
     float wg0;              // scalar rest weight
     float wg1;              // scalar axis weight (1 - wg0) / 4
     float inv_cs2g;         // 1 / c_s^2 of the scalar lattice
+    float decay;            // k of the reaction term R = -k C (0: none)
     uint32_t open_mask[kMaskWords];  // valve bits of this step: channel c is bit c % 32 of word c / 32
     double* partials;       // 4 diagnostics partial sums per block (scratch)
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
@@ -121,6 +123,7 @@ struct ScalarArgs {
     const float* uy;
     float u_scale;          // ratio of the scalar's time step to the fluid's
     float omega_g, wg0, wg1, inv_cs2g;
+    float decay;            // k of the reaction term R = -k C (0: none)
     uint32_t open_mask;
     double* partials;       // writes slots 1 and 3 of each block's four
     int n_partials;         // entries of `partials` (>= grid); those beyond the grid get 0
@@ -142,20 +145,27 @@ cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out
 cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm);
 
 // Every node (fluid and solid, padding included) to the rest equilibrium
-// of rho0 and C0.  `pop` holds elements of the given precision.
+// of rho0 and C0.  `pop` holds elements of the given precision.  The stored
+// state is post-collision: with decay rate k the equilibrium loses
+// w_i k C (the collision of an equilibrium state).
 cudaError_t launch_init_rest(void* pop, int ny, int pitch, float rho0, float wg0, float wg1,
-                             float C0, int precision, cudaStream_t s);
+                             float C0, int precision, float decay, cudaStream_t s);
 
-// Fluid nodes to the equilibrium of fields given row-major [y][x] (nx per row).
+// Fluid nodes to the equilibrium of fields given row-major [y][x] (nx per
+// row), collided as above.
 cudaError_t launch_init_fields(void* pop, const uint8_t* links, int nx, int ny, int pitch,
                                const float* rho, const float* ux, const float* uy, const float* C,
-                               float wg0, float wg1, float inv_cs2g, int precision, cudaStream_t s);
+                               float wg0, float wg1, float inv_cs2g, int precision, float decay,
+                               cudaStream_t s);
 
 // Moments of the stored populations into row-major [y][x] arrays (any may be
-// null); solid nodes give 0.
+// null); solid nodes give 0.  The stored populations are post-collision:
+// with decay rate k the collision removed k C, so C is reported as
+// sum g / (1 - k), the concentration before the collision (the moments of f
+// are the same before and after it).
 cudaError_t launch_fields(const void* pop, const uint8_t* links, int nx, int ny, int pitch,
                           float* rho, float* ux, float* uy, float* C, float wg0, float wg1, int precision,
-                          cudaStream_t s);
+                          float decay, cudaStream_t s);
 
 // 16-bit storage <-> the FP32 representation (fluid planes f_i - w_i, scalar
 // planes g_i), element by element over n_elems = 14 * ny * pitch.

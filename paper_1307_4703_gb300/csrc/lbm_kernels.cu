@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void init_rest(T* pop, long long plane, float rho0, float wg0, float wg1, float C0, float gref0,
-                          float gref1)
+                          float gref1, float decay)
 {
     const long long n = plane * kPlanes;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -445,7 +445,7 @@ __global__ void init_rest(T* pop, long long plane, float rho0, float wg0, float 
         const int p = int(e / plane);
         float w;  // f is stored as f_i - w_i
         if (p < 9) w = (p == 0 ? kWr : p <= 4 ? kWa : kWd) * (rho0 - 1.f);
-        else w = (p == 9 ? wg0 : wg1) * C0;
+        else w = (p == 9 ? wg0 : wg1) * C0 - (p == 9 ? wg0 : wg1) * decay * C0;
         Codec<T>::st1(pop + e, w, plane_offset(p, gref0, gref1));
     }
 }
@@ -453,7 +453,8 @@ __global__ void init_rest(T* pop, long long plane, float rho0, float wg0, float 
 template <typename T>
 __global__ void init_fields(T* pop, const uint8_t* links, int nx, int ny, int pitch,
                             const float* rho_in, const float* ux_in, const float* uy_in,
-                            const float* C_in, float wg0, float wg1, float inv_cs2g, float gref0, float gref1)
+                            const float* C_in, float wg0, float wg1, float inv_cs2g, float gref0, float gref1,
+                            float decay)
 {
     const long long P = (long long)ny * pitch;
     for (int y = blockIdx.y; y < ny; y += gridDim.y) {
@@ -470,15 +471,18 @@ __global__ void init_fields(T* pop, const uint8_t* links, int nx, int ny, int pi
             const float w = i == 0 ? kWr : i <= 4 ? kWa : kWd;
             Codec<T>::st1(pop + i * P + o, w * ((rho - 1.f) + rho * (3.f * e[i] + 4.5f * e[i] * e[i] - usq)), 0.f);
         }
-        Codec<T>::st1(pop + 9 * P + o, wg0 * C, gref0);
+        const float R = -decay * C;  // the collision's reaction term, w_i R
+        Codec<T>::st1(pop + 9 * P + o, wg0 * C + wg0 * R, gref0);
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) Codec<T>::st1(pop + (9 + i) * P + o, wg1 * C * (1.f + e[i] * inv_cs2g), gref1);
+        for (int i = 1; i <= 4; ++i)
+            Codec<T>::st1(pop + (9 + i) * P + o, wg1 * C * (1.f + e[i] * inv_cs2g) + wg1 * R, gref1);
     }
 }
 
 template <typename T>
 __global__ void fields_kernel(const T* pop, const uint8_t* links, int nx, int ny, int pitch,
-                              float* rho_out, float* ux_out, float* uy_out, float* C_out, float gref0, float gref1)
+                              float* rho_out, float* ux_out, float* uy_out, float* C_out, float gref0, float gref1,
+                              float decay)
 {
     const long long P = (long long)ny * pitch;
     for (int y = blockIdx.y; y < ny; y += gridDim.y) {
@@ -499,6 +503,7 @@ __global__ void fields_kernel(const T* pop, const uint8_t* links, int nx, int ny
 #pragma unroll
             for (int i = 0; i < 5; ++i) g[i] = Codec<T>::ld1(pop + (9 + i) * P + o, i == 0 ? gref0 : gref1);
             c = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+            if (decay != 0.f) c /= 1.f - decay;
         }
         const long long idx = (long long)y * nx + x;
         if (rho_out) rho_out[idx] = r;
@@ -610,53 +615,55 @@ cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm)
 }
 
 cudaError_t launch_init_rest(void* pop, int ny, int pitch, float rho0, float wg0, float wg1,
-                             float C0, int precision, cudaStream_t s)
+                             float C0, int precision, float decay, cudaStream_t s)
 {
     const long long plane = (long long)ny * pitch;
     const int grid = elementwise_grid(plane * kPlanes);
     const float r0 = wg0 * kCRef, r1 = wg1 * kCRef;
     if (precision == kFP16)
-        init_rest<<<grid, 256, 0, s>>>(static_cast<__half*>(pop), plane, rho0, wg0, wg1, C0, r0, r1);
+        init_rest<<<grid, 256, 0, s>>>(static_cast<__half*>(pop), plane, rho0, wg0, wg1, C0, r0, r1, decay);
     else if (precision == kBF16)
-        init_rest<<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16*>(pop), plane, rho0, wg0, wg1, C0, r0, r1);
+        init_rest<<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16*>(pop), plane, rho0, wg0, wg1, C0, r0, r1,
+                                       decay);
     else
-        init_rest<<<grid, 256, 0, s>>>(static_cast<float*>(pop), plane, rho0, wg0, wg1, C0, 0.f, 0.f);
+        init_rest<<<grid, 256, 0, s>>>(static_cast<float*>(pop), plane, rho0, wg0, wg1, C0, 0.f, 0.f, decay);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_fields(void* pop, const uint8_t* links, int nx, int ny, int pitch,
                                const float* rho, const float* ux, const float* uy, const float* C,
-                               float wg0, float wg1, float inv_cs2g, int precision, cudaStream_t s)
+                               float wg0, float wg1, float inv_cs2g, int precision, float decay,
+                               cudaStream_t s)
 {
     dim3 grid((nx + 255) / 256, ny < 65535 ? ny : 65535);
     const float r0 = wg0 * kCRef, r1 = wg1 * kCRef;
     if (precision == kFP16)
         init_fields<<<grid, 256, 0, s>>>(static_cast<__half*>(pop), links, nx, ny, pitch, rho, ux, uy, C, wg0, wg1,
-                                         inv_cs2g, r0, r1);
+                                         inv_cs2g, r0, r1, decay);
     else if (precision == kBF16)
         init_fields<<<grid, 256, 0, s>>>(static_cast<__nv_bfloat16*>(pop), links, nx, ny, pitch, rho, ux, uy, C,
-                                         wg0, wg1, inv_cs2g, r0, r1);
+                                         wg0, wg1, inv_cs2g, r0, r1, decay);
     else
         init_fields<<<grid, 256, 0, s>>>(static_cast<float*>(pop), links, nx, ny, pitch, rho, ux, uy, C, wg0, wg1,
-                                         inv_cs2g, 0.f, 0.f);
+                                         inv_cs2g, 0.f, 0.f, decay);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fields(const void* pop, const uint8_t* links, int nx, int ny, int pitch,
                           float* rho, float* ux, float* uy, float* C, float wg0, float wg1, int precision,
-                          cudaStream_t s)
+                          float decay, cudaStream_t s)
 {
     dim3 grid((nx + 255) / 256, ny < 65535 ? ny : 65535);
     const float r0 = wg0 * kCRef, r1 = wg1 * kCRef;
     if (precision == kFP16)
         fields_kernel<<<grid, 256, 0, s>>>(static_cast<const __half*>(pop), links, nx, ny, pitch, rho, ux, uy, C,
-                                           r0, r1);
+                                           r0, r1, decay);
     else if (precision == kBF16)
         fields_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(pop), links, nx, ny, pitch, rho, ux,
-                                           uy, C, r0, r1);
+                                           uy, C, r0, r1, decay);
     else
         fields_kernel<<<grid, 256, 0, s>>>(static_cast<const float*>(pop), links, nx, ny, pitch, rho, ux, uy, C,
-                                           0.f, 0.f);
+                                           0.f, 0.f, decay);
     return cudaGetLastError();
 }
 

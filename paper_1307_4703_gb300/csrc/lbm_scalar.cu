@@ -94,21 +94,37 @@ __global__ void __launch_bounds__(256) scalar_frozen_step(const ScalarArgs a)
             const bool pw = open_w && bw.x == xk;
             const bool pe = !pw && open_e && be.x == xk;
             bool pressure_node = false;
+            const float ux = a.u_scale * at(ux4, k), uy = a.u_scale * at(uy4, k);
             if (pw || pe) {
                 const RowBC b = pw ? bw : be;
                 const int gi = pw ? 1 : 3;
-                if (((b.chan_kind >> 8) & 0xFF) == 0) {  // held concentration
+                const int kind = (b.chan_kind >> 8) & 0xFF;
+                if (kind == 0) {  // held concentration
                     float others = 0.f;
 #pragma unroll
                     for (int i = 0; i < 5; ++i)
                         if (i != gi) others += g[i];
                     g[gi] = b.c - others;
-                } else {                                 // do-nothing
+                } else {          // do-nothing
                     g[gi] = __ldg(S + gi * P + oC + k);
-                    pressure_node = true;
+                    pressure_node = kind != 3;
+                    if (kind == 3) {  // the paper's inlet: scaled to C_in
+                        const float Cs = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+                        if (Cs > 0.f) {
+                            const float gc = b.c / Cs;
+#pragma unroll
+                            for (int i = 0; i < 5; ++i) g[i] *= gc;
+                        } else {
+                            const float c1 = a.wg1 * b.c, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
+                            g[0] = b.c - 4.f * c1;
+                            g[1] = c1 + cx;
+                            g[3] = c1 - cx;
+                            g[2] = c1 + cy;
+                            g[4] = c1 - cy;
+                        }
+                    }
                 }
             }
-            const float ux = a.u_scale * at(ux4, k), uy = a.u_scale * at(uy4, k);
             const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
             const float wg = a.omega_g;
             const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
@@ -117,6 +133,12 @@ __global__ void __launch_bounds__(256) scalar_frozen_step(const ScalarArgs a)
             g[3] += wg * ((c1 - cx) - g[3]);
             g[2] += wg * ((c1 + cy) - g[2]);
             g[4] += wg * ((c1 - cy) - g[4]);
+            if (a.decay != 0.f) {  // reaction term R = -k C of Eq. cde, as w_i R
+                const float R = -a.decay * C;
+                g[0] += a.wg0 * R;
+#pragma unroll
+                for (int i = 1; i < 5; ++i) g[i] += a.wg1 * R;
+            }
 #pragma unroll
             for (int i = 0; i < 5; ++i) at(v[i], k) = g[i];
             if (fluid) {

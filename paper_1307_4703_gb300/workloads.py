@@ -21,7 +21,7 @@ steps, u_max.
 import numpy as np
 
 WEST, EAST = 0, 1
-VELOCITY, PRESSURE = 0, 1
+VELOCITY, PRESSURE, PRESSURE_RESCALE, INLET_RESCALE = 0, 1, 2, 3
 SEED = 0x1307
 
 
@@ -45,13 +45,20 @@ def valve_word(problem, t):
 
 
 def two_channel_chip(nx, ny, ch_w, ch_len, chamber_w, tau, tau_c, u_max, period, steps,
-                     x0=0, C_top=1.0, C_bottom=0.0, w0=1.0 / 3.0, name="chip"):
+                     x0=0, C_top=1.0, C_bottom=0.0, w0=1.0 / 3.0, name="chip", paper_ports=False, decay=0.0):
     """Two channels of ``ch_w`` rows along x (rows [0, ch_w) and
     [ny - ch_w, ny), columns [x0, x0 + ch_len)) joined by a chamber of
     ``chamber_w`` columns centred in the grid.  Channel 0 is the top channel
     (largest y, fed with C_top) and opens first; channel 1 is the bottom
     channel (C_bottom).  Each channel has a velocity inlet on its west end
-    and a pressure outlet (rho = 1) on its east end."""
+    and a pressure outlet (rho = 1) on its east end.
+
+    paper_ports: the paper's pressure-driven channels instead (section
+    "Boundary Conditions"): a rescaling inlet at density 1 + drho / 2 holding
+    C_in and a rescaling outlet at 1 - drho / 2, with drho = 3 dp and dp the
+    Poiseuille pressure drop 8 nu u_max L / W^2 of a channel of length L and
+    width W (section "Choice of Parameter Values").  decay: rate k of the
+    compound."""
     assert 0 < ch_w and 2 * ch_w < ny and 0 <= x0 and x0 + ch_len <= nx
     solid = np.ones((ny, nx), dtype=np.uint8)
     solid[0:ch_w, x0:x0 + ch_len] = 0
@@ -62,16 +69,23 @@ def two_channel_chip(nx, ny, ch_w, ch_len, chamber_w, tau, tau_c, u_max, period,
     edge_C = np.zeros((2, ny))
     prof = parabolic_profile(ch_w, u_max)
     ports = []
+    drho = 3 * 8 * (tau - 0.5) / 3 * u_max * (ch_len - 1) / ch_w ** 2
     for chan, (y0, c_in) in enumerate(((ny - ch_w, C_top), (0, C_bottom))):
-        ports.append(dict(channel=chan, side=WEST, x=x0, y0=y0, y1=y0 + ch_w, kind=VELOCITY, rho=1.0))
-        ports.append(dict(channel=chan, side=EAST, x=x0 + ch_len - 1, y0=y0, y1=y0 + ch_w,
-                          kind=PRESSURE, rho=1.0))
-        edge_u[WEST, y0:y0 + ch_w] = prof
+        if paper_ports:
+            ports.append(dict(channel=chan, side=WEST, x=x0, y0=y0, y1=y0 + ch_w, kind=INLET_RESCALE,
+                              rho=1.0 + drho / 2))
+            ports.append(dict(channel=chan, side=EAST, x=x0 + ch_len - 1, y0=y0, y1=y0 + ch_w,
+                              kind=PRESSURE_RESCALE, rho=1.0 - drho / 2))
+        else:
+            ports.append(dict(channel=chan, side=WEST, x=x0, y0=y0, y1=y0 + ch_w, kind=VELOCITY, rho=1.0))
+            ports.append(dict(channel=chan, side=EAST, x=x0 + ch_len - 1, y0=y0, y1=y0 + ch_w,
+                              kind=PRESSURE, rho=1.0))
+            edge_u[WEST, y0:y0 + ch_w] = prof
         edge_C[WEST, y0:y0 + ch_w] = c_in
     return dict(name=name, nx=nx, ny=ny, solid=solid, tau=float(tau), tau_c=float(tau_c),
                 w0=float(w0), ports=ports, edge_u=edge_u, edge_C=edge_C, period=int(period),
                 states=[1, 2], steps=int(steps), u_max=float(u_max),
-                chamber=(cx0, cx0 + chamber_w, ch_w, ny - ch_w))
+                chamber=(cx0, cx0 + chamber_w, ch_w, ny - ch_w), decay=float(decay))
 
 
 def config_small():
@@ -142,14 +156,16 @@ def has_isolated_fluid(solid):
     return bool(np.any(fl & ~nb))
 
 
-def random_case(seed, nx, ny, solid_frac=0.2):
+def random_case(seed, nx, ny, solid_frac=0.2, paper_ports=False, decay=0.0):
     """A small lattice with every kind of node: random solid obstacles, one
     port of each (side, kind) pair on three valve channels, random inlet
     profiles and concentrations, and random initial fields near rest.
 
     Returns (problem, init) where init = dict(rho, ux, uy, C) of (ny, nx)
     arrays, and problem["states"] holds a random valve word per step
-    (period 1)."""
+    (period 1).  paper_ports: the velocity ports become the paper's
+    rescaling inlets and the pressure ports its rescaling outlets (the same
+    random draws otherwise).  decay: rate k of the compound."""
     r = rng(seed)
     assert nx >= 4 and ny >= 8
     solid = (r.random((ny, nx)) < solid_frac).astype(np.uint8)
@@ -167,7 +183,8 @@ def random_case(seed, nx, ny, solid_frac=0.2):
         x = 0 if side == WEST else nx - 1
         solid[y0:y1, x] = 0
         solid[y0:y1, x + (1 if side == WEST else -1)] = 0
-        ports.append(dict(channel=chan, side=side, x=x, y0=y0, y1=y1, kind=kind,
+        ports.append(dict(channel=chan, side=side, kind=kind if not paper_ports else
+                          (INLET_RESCALE if kind == VELOCITY else PRESSURE_RESCALE), x=x, y0=y0, y1=y1,
                           rho=float(1.0 + 0.01 * (r.random() - 0.5))))
         if kind == VELOCITY:
             sgn = 1.0 if side == WEST else -1.0
@@ -192,7 +209,7 @@ def random_case(seed, nx, ny, solid_frac=0.2):
     prob = dict(name="random-%dx%d-s%d" % (nx, ny, seed), nx=nx, ny=ny, solid=solid,
                 tau=float(0.55 + 0.5 * r.random()), tau_c=float(0.52 + 0.5 * r.random()),
                 w0=1.0 / 3.0, ports=ports, edge_u=edge_u, edge_C=edge_C, period=1,
-                states=states, steps=len(states), u_max=0.04)
+                states=states, steps=len(states), u_max=0.04, decay=float(decay))
     return prob, init
 
 
