@@ -141,6 +141,40 @@ def config_batch(n=64, steps=10000, seed=SEED):
     return chips
 
 
+STEP_ADVECTION_CASES = {  # Table 3: (U_lb, D_lb, T_phys / dt)
+    "a": (0.5, 0.00244, 400),
+    "b": (0.05, 0.000244, 4000),
+    "c": (0.1, 0.00244, 2000),
+    "d": (0.01, 0.000244, 20000),
+}
+
+
+def step_advection(case, length=400, width=20):
+    """The step-profile advection test of Table 3 (cases a-d): a straight
+    channel `width` nodes wide (the paper resolves the 100 um channel by 20
+    nodes) between halfway walls, at rest with C = 0, opened at t = 0 with a
+    prescribed-density inlet holding C = 1 (the paper's rescaling inlet) and
+    a do-nothing outlet.  The stored velocity field is the Poiseuille
+    profile u(s) = 4 U s (W - s) / W^2 (s = y + 1/2) with the case's maximal
+    speed U, standing in for the pre-computed channel flow; the scalar runs
+    on the paper's D2Q4 lattice (w0 = 0) with tau_g = 2 D + 1/2.  Every case
+    advects the front 200 nodes."""
+    U, D, steps = STEP_ADVECTION_CASES[case]
+    ny, nx = width, length
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    edge_u = np.zeros((2, ny))
+    edge_C = np.zeros((2, ny))
+    edge_C[WEST, :] = 1.0
+    ports = [dict(channel=0, side=WEST, x=0, y0=0, y1=ny, kind=INLET_RESCALE, rho=1.0),
+             dict(channel=0, side=EAST, x=nx - 1, y0=0, y1=ny, kind=PRESSURE_RESCALE, rho=1.0)]
+    s = np.arange(ny) + 0.5
+    ux = np.repeat((4 * U * s * (ny - s) / ny ** 2)[:, None], nx, axis=1)
+    return dict(name="step-advection-%s" % case, nx=nx, ny=ny, solid=solid, tau=0.8,
+                tau_c=float(2 * D + 0.5), w0=0.0, ports=ports, edge_u=edge_u, edge_C=edge_C,
+                period=int(steps), states=[1], steps=int(steps), u_max=float(U), D=float(D),
+                velocity=(ux, np.zeros((ny, nx))))
+
+
 def has_isolated_fluid(solid):
     """True when some fluid cell has no fluid cell among its 8 neighbours
     inside the grid (such masks are rejected by the library)."""
