@@ -542,6 +542,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     lbm::StepLaunch& L = h->launch;
     L.variant = opt.variant == 1 ? lbm::kVariantRegs : opt.variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
     L.precision = opt.precision;
+    L.pdl = true;  // consecutive steps overlap launch and set-up with the previous step's tail
     if (L.variant == lbm::kVariantBulk) {
         const int nc = opt.consumer_warps ? opt.consumer_warps : kDefaultConsumers;
         L.stages = nc * (opt.pipeline_stages                ? opt.pipeline_stages
@@ -1466,6 +1467,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         if (e != cudaSuccess) break;
         lbm::StepLaunch L{};
         L.precision = h->precision;
+        L.pdl = true;
         if (c.variant == 1) {
             L.variant = lbm::kVariantRegs;
             L.block = 32 * c.warps;

@@ -65,6 +65,17 @@ __device__ __forceinline__ float at(const float4& v, int k)
     return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
 }
 
+// Programmatic dependent launch: wait until the previous kernel of the
+// stream has completed and its writes are visible (a no-op for a launch
+// without that dependency), then allow the next kernel to launch, so that its
+// blocks are placed and set up while this grid's last blocks finish.  Every
+// thread calls it before its first access to data that another kernel writes.
+__device__ __forceinline__ void grid_dependency_sync()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Storage of the populations.  FP32 keeps them as they are (fluid planes as
 // f_i - w_i, scalar planes as g_i).  FP16 and BF16 hold deviations from a
 // reference: the fluid planes the same f_i - w_i, the scalar planes
@@ -312,13 +323,76 @@ __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, c
 //               C_in; a node without compound takes g_eq(C_in, u) instead.
 // Post-collision values of the previous step are read from the source
 // buffer at index own.  Returns true for an outlet node (kinds 1, 2).
+struct PortNode {
+    float f[9];
+    float g[5];
+};
+
+// Kinds 2 and 3 of complete_port, kept out of line: they are rare, and
+// inlined into every node of the step kernels' unrolled loops they would
+// crowd the instruction cache of the hot path.
+template <typename T>
+__device__ __noinline__ bool rescaling_port(PortNode& n, bool west, const RowBC& b, const T* S, long long P,
+                                            long long own, float gref1, float wg1, float inv_cs2g)
+{
+    float* f = n.f;
+    float* g = n.g;
+    const int kind = (b.chan_kind >> 8) & 0xFF;
+    if (west) {
+        f[1] = Codec<T>::ld1(S + 1 * P + own, 0.f);
+        f[5] = Codec<T>::ld1(S + 5 * P + own, 0.f);
+        f[8] = Codec<T>::ld1(S + 8 * P + own, 0.f);
+    } else {
+        f[3] = Codec<T>::ld1(S + 3 * P + own, 0.f);
+        f[6] = Codec<T>::ld1(S + 6 * P + own, 0.f);
+        f[7] = Codec<T>::ld1(S + 7 * P + own, 0.f);
+    }
+    const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    // gamma - 1 = (rho_port - rho) / rho; f_i' <- f_i' + (gamma - 1) (w_i + f_i')
+    const float gm1 = (b.a - rd) / (1.f + rd);
+    for (int i = 0; i < 9; ++i) f[i] += gm1 * ((i == 0 ? kWr : i <= 4 ? kWa : kWd) + f[i]);
+    // do-nothing for the scalar's unknown population
+    if (west) g[1] = Codec<T>::ld1(S + 10 * P + own, gref1);
+    else g[3] = Codec<T>::ld1(S + 12 * P + own, gref1);
+    if (kind != 3) return true;
+    const float Cs = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+    if (Cs > 0.f) {
+        const float gc = b.c / Cs;
+        for (int i = 0; i < 5; ++i) g[i] *= gc;
+    } else {
+        const float rho = 1.f + (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]);
+        const float ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7])) / rho;
+        const float uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8])) / rho;
+        const float c1 = wg1 * b.c, cx = c1 * inv_cs2g * ux, cy = c1 * inv_cs2g * uy;
+        g[0] = b.c - 4.f * c1;
+        g[1] = c1 + cx;
+        g[3] = c1 - cx;
+        g[2] = c1 + cy;
+        g[4] = c1 - cy;
+    }
+    return false;
+}
+
 template <typename T>
 __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool west, const RowBC& b,
                                               const T* S, long long P, long long own, float gref1 = 0.f,
                                               float wg1 = 0.f, float inv_cs2g = 0.f)
 {
     const int kind = (b.chan_kind >> 8) & 0xFF;
-    if (kind <= 1) {
+    if (kind >= 2) {
+        PortNode n;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) n.f[i] = f[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) n.g[i] = g[i];
+        const bool outlet = rescaling_port(n, west, b, S, P, own, gref1, wg1, inv_cs2g);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = n.f[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = n.g[i];
+        return outlet;
+    }
+    {
         const float s = west ? 1.f : -1.f;
         // populations leaving through the port: e = (-s, 0), (-s, -1), (-s, +1)
         const float fo_ax = west ? f[3] : f[1];
@@ -343,21 +417,6 @@ __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool
             f[6] = fi_up;
             f[7] = fi_dn;
         }
-    } else {
-        if (west) {
-            f[1] = Codec<T>::ld1(S + 1 * P + own, 0.f);
-            f[5] = Codec<T>::ld1(S + 5 * P + own, 0.f);
-            f[8] = Codec<T>::ld1(S + 8 * P + own, 0.f);
-        } else {
-            f[3] = Codec<T>::ld1(S + 3 * P + own, 0.f);
-            f[6] = Codec<T>::ld1(S + 6 * P + own, 0.f);
-            f[7] = Codec<T>::ld1(S + 7 * P + own, 0.f);
-        }
-        const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        // gamma - 1 = (rho_port - rho) / rho; f_i' <- f_i' + (gamma - 1) (w_i + f_i')
-        const float gm1 = (b.a - rd) / (1.f + rd);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] += gm1 * ((i == 0 ? kWr : i <= 4 ? kWa : kWd) + f[i]);
     }
     if (kind == 0) {
         if (west) g[1] = b.c - (g[0] + g[2] + g[3] + g[4]);
@@ -367,24 +426,7 @@ __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool
     // do-nothing: the node keeps its own post-collision value
     if (west) g[1] = Codec<T>::ld1(S + 10 * P + own, gref1);
     else g[3] = Codec<T>::ld1(S + 12 * P + own, gref1);
-    if (kind != 3) return true;
-    const float Cs = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
-    if (Cs > 0.f) {
-        const float gc = b.c / Cs;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] *= gc;
-    } else {
-        const float rho = 1.f + (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]);
-        const float ux = ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7])) / rho;
-        const float uy = ((f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8])) / rho;
-        const float c1 = wg1 * b.c, cx = c1 * inv_cs2g * ux, cy = c1 * inv_cs2g * uy;
-        g[0] = b.c - 4.f * c1;
-        g[1] = c1 + cx;
-        g[3] = c1 - cx;
-        g[2] = c1 + cy;
-        g[4] = c1 - cy;
-    }
-    return false;
+    return true;
 }
 
 // Free flight (pull) of one lane's four nodes x0..x0+3 with 128-bit loads:
@@ -456,6 +498,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     const long long P = a.plane;
     const bool open_w = bw.x >= 0 && valve_open(a, bw.chan_kind);
     const bool open_e = be.x >= 0 && valve_open(a, be.chan_kind);
+    const float dfac = a.decay != 0.f ? 1.f - a.decay / omega.y : 1.f;
 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -510,20 +553,19 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
         {
             const float wg = omega.y;
+            // the reaction term R = -k C of Eq. cde enters as w_i R, which is
+            // omega (w_i R / omega): the equilibrium's isotropic part scaled by
+            // dfac = 1 - k / omega (exactly 1 without decay)
+            const float Cd = C * dfac;
             const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
+            const float c1d = a.wg1 * Cd;
             // rest equilibrium w0 C formed as the remainder, so that the five
             // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)
-            g[0] += wg * ((C - 4.f * c1) - g[0]);
-            g[1] += wg * ((c1 + cx) - g[1]);
-            g[3] += wg * ((c1 - cx) - g[3]);
-            g[2] += wg * ((c1 + cy) - g[2]);
-            g[4] += wg * ((c1 - cy) - g[4]);
-            if (a.decay != 0.f) {  // reaction term R = -k C of Eq. cde, as w_i R
-                const float R = -a.decay * C;
-                g[0] += a.wg0 * R;
-#pragma unroll
-                for (int i = 1; i < 5; ++i) g[i] += a.wg1 * R;
-            }
+            g[0] += wg * ((Cd - 4.f * c1d) - g[0]);
+            g[1] += wg * ((c1d + cx) - g[1]);
+            g[3] += wg * ((c1d - cx) - g[3]);
+            g[2] += wg * ((c1d + cy) - g[2]);
+            g[4] += wg * ((c1d - cy) - g[4]);
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) at(v[i], k) = f[i];

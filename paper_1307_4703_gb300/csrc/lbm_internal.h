@@ -45,7 +45,8 @@ struct StepLaunch {
     int grid;
     int block;
     int stages;   // shared-memory stages per block (computing warps x stages per warp)
-    int precision = kFP32;  // storage of the populations; 16-bit runs the register variant
+    int precision = kFP32;  // storage of the populations
+    bool pdl = false;       // launch as a programmatic dependent of the previous kernel
 };
 
 struct RowBC {

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
     const int stride = gridDim.x * wpb;
     int t = blockIdx.x * wpb + warp;
     uint2 next = t < a.n_tiles ? a.tiles[t] : make_uint2(0u, 0u);
+    grid_dependency_sync();
     for (; t < a.n_tiles; t += stride) {
         const uint2 tile = next;  // the following entry is fetched one tile ahead
         if (t + stride < a.n_tiles) next = a.tiles[t + stride];
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
         mbar_fence_init();
     }
     __syncthreads();
+    grid_dependency_sync();
 
     LaneDiag diag;
     bool bad = false;
@@ -369,6 +371,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
         mbar_fence_init();
     }
     __syncwarp();
+    grid_dependency_sync();
 
     LaneDiag diag;
     bool bad = false;
@@ -566,22 +569,34 @@ cudaError_t prepare_step_kernels()
 
 cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
 {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(l.grid);
+    cfg.blockDim = dim3(l.block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = l.pdl ? 1 : 0;
+    cudaError_t e;
     if (l.variant == kVariantBulk) {
         const int per = l.stages / (l.block / 32 - 1);
-        const size_t smem = bulk_smem_bytes(l.stages, l.precision);
-        if (l.precision == kFP16) coupled_step_bulk<__half><<<l.grid, l.block, smem, s>>>(a, per);
-        else if (l.precision == kBF16) coupled_step_bulk<__nv_bfloat16><<<l.grid, l.block, smem, s>>>(a, per);
-        else coupled_step_bulk<float><<<l.grid, l.block, smem, s>>>(a, per);
+        cfg.dynamicSmemBytes = bulk_smem_bytes(l.stages, l.precision);
+        if (l.precision == kFP16) e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<__half>, a, per);
+        else if (l.precision == kBF16) e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<__nv_bfloat16>, a, per);
+        else e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<float>, a, per);
     } else if (l.variant == kVariantPipe) {
         const int per = l.stages / (l.block / 32);
-        coupled_step_pipe<<<l.grid, l.block, bulk_smem_bytes(l.stages), s>>>(a, per);
+        cfg.dynamicSmemBytes = bulk_smem_bytes(l.stages);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_pipe, a, per);
     } else if (l.precision == kFP16) {
-        coupled_step_regs<__half><<<l.grid, l.block, 0, s>>>(a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__half>, a);
     } else if (l.precision == kBF16) {
-        coupled_step_regs<__nv_bfloat16><<<l.grid, l.block, 0, s>>>(a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__nv_bfloat16>, a);
     } else {
-        coupled_step_regs<float><<<l.grid, l.block, 0, s>>>(a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<float>, a);
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

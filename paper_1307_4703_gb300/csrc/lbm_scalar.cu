@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(256) scalar_frozen_step(const ScalarArgs a)
     const float* __restrict__ S = a.src;  // scalar plane 0 of the source buffer
     KahanF sc, sq;
     bool bad = false;
+    grid_dependency_sync();
     for (int t = blockIdx.x * wpb + warp; t < a.n_tiles; t += gridDim.x * wpb) {
         const uint2 tile = a.tiles[t];
         const int y = int(tile.x >> kSegBits);
@@ -197,7 +198,18 @@ __global__ void velocity_of_state(const float* pop, const uint8_t* links, long l
 
 cudaError_t launch_scalar_step(const ScalarArgs& a, int grid, int block, cudaStream_t s)
 {
-    scalar_frozen_step<<<grid, block, 0, s>>>(a);
+    // a programmatic dependent of the previous kernel (see grid_dependency_sync)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, scalar_frozen_step, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
