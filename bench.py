@@ -205,9 +205,12 @@ def _reference(args):
 
 def _adjoint_ratio(device):
     """Cost of the gradient relative to the forward run on the gradient
-    workload (1024 x 512 chip, 4000 steps, two valve toggles, checkpoints
-    every 250 steps): (time of lbm_adjoint - time of 4000 plain steps) /
-    time of 4000 plain steps, wall clock with the stream synchronised."""
+    workload (1024 x 512 chip, 4000 steps, two valve toggles): (time of
+    lbm_adjoint - time of 4000 plain steps) / time of 4000 plain steps, wall
+    clock with the stream synchronised, best of two calls (device memory from
+    PyTorch's caching allocator, so the second call allocates nothing).  With
+    every state kept in HBM (ckpt_every = 1, 117 GB) nothing is recomputed;
+    with a checkpoint every 250 steps each segment is recomputed once."""
     import numpy as np
     from paper_1307_4703_gb300 import lbm, workloads as W
     prob = W.config_adjoint_chip()
@@ -216,24 +219,30 @@ def _adjoint_ratio(device):
     ox = np.full_like(oy, (cx0 + cx1) // 2)
     target = (oy - cy0) / max(1, cy1 - 1 - cy0)
     n = prob["steps"]
-    best = None
-    for _ in range(2):
-        chip = lbm.Chip.from_problem(prob, device=device)
-        chip.set_valve_schedule(prob["period"], prob["states"])
-        chip.step(10)
-        chip.synchronize()
-        t0 = time.perf_counter()
-        chip.step(n)
-        chip.synchronize()
-        tf = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        chip.adjoint(n, ox, oy, target, ckpt_every=250)
-        ta = time.perf_counter() - t0
-        chip.close()
-        r = (ta - tf) / tf
-        best = r if best is None else min(best, r)
-    return {"value": best, "workload": "chip-1024x512, 4000 steps, checkpoints every 250",
-            "definition": "(adjoint call - forward steps) / forward steps"}
+    out = {}
+    for K in (1, 250):
+        best = None
+        for _ in range(2):
+            chip = lbm.Chip.from_problem(prob, device=device, torch_alloc=True)
+            chip.set_valve_schedule(prob["period"], prob["states"])
+            chip.step(10)
+            chip.synchronize()
+            t0 = time.perf_counter()
+            chip.step(n)
+            chip.synchronize()
+            tf = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            chip.adjoint(n, ox, oy, target, ckpt_every=K)
+            ta = time.perf_counter() - t0
+            chip.close()
+            r = (ta - tf) / tf
+            best = r if best is None else min(best, r)
+        out[K] = best
+    import torch
+    torch.cuda.empty_cache()
+    return {"value": out[1], "workload": "chip-1024x512, 4000 steps",
+            "ckpt_every_1": out[1], "ckpt_every_250": out[250],
+            "definition": "(adjoint call - forward steps) / forward steps; value: every state kept (ckpt_every 1)"}
 
 
 def _frozen_scalar(chip, prob, steps, stream, peak):

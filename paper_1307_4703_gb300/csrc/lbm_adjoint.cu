@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(256) adjoint_collide(const AdjointArgs A)
     const long long P = A.plane;
     const float* __restrict__ S = A.state;
     KahanF dwg;
+    grid_dependency_sync();
     for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
         const uint2 tile = A.tiles[t];
         const int y = int(tile.x >> kSegBits);
@@ -237,6 +238,7 @@ __global__ void __launch_bounds__(256) adjoint_stream(const AdjointArgs A)
     const int wpb = blockDim.x >> 5;
     const long long P = A.plane;
     const float* __restrict__ S = A.adj_mid;
+    grid_dependency_sync();
     for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
         const uint2 tile = A.tiles[t];
         const int y = int(tile.x >> kSegBits);
@@ -356,10 +358,20 @@ cudaError_t adjoint_occupancy(int block, int* blocks_per_sm)
 
 cudaError_t launch_adjoint_step(const AdjointArgs& a, int grid, int block, cudaStream_t s)
 {
-    adjoint_collide<<<grid, block, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    // both as programmatic dependents of the kernel before them (each waits
+    // for it in grid_dependency_sync before touching any buffer)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, adjoint_collide, a);
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, adjoint_stream, a);
     if (e != cudaSuccess) return e;
-    adjoint_stream<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

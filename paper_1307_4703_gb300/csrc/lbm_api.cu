@@ -1206,18 +1206,35 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     a.err = h->err;
     const int64_t t0 = h->step;
     if (lbm_status js = join_scalar(h)) return js;
-    for (int64_t t = 0; t < n; ++t) {
-        if (t % K == 0)
-            LBM_CUDA(h, cudaMemcpyAsync(ckpt + size_t(t / K) * S, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
-        a.src = h->pop[h->cur];
-        a.dst = h->pop[1 - h->cur];
-        a.open_mask[0] = h->mask_at(t0 + t);
-        cudaError_t e = lbm::launch_step(a, h->launch, st);
-        if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+    if (K == 1) {
+        // every state kept: the steps write straight into the state array
+        // (no copies, no recomputation), the last one into the other buffer
+        LBM_CUDA(h, cudaMemcpyAsync(ckpt, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
+        for (int64_t t = 0; t < n; ++t) {
+            a.src = t == 0 ? h->pop[h->cur] : reinterpret_cast<float*>(ckpt + size_t(t) * S);
+            a.dst = t + 1 < n ? reinterpret_cast<float*>(ckpt + size_t(t + 1) * S) : h->pop[1 - h->cur];
+            a.open_mask[0] = h->mask_at(t0 + t);
+            cudaError_t e = lbm::launch_step(a, h->launch, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+        }
         h->cur = 1 - h->cur;
         h->gbuf = h->cur;
         h->diag_grid = h->launch.grid;
-        ++h->step;
+        h->step += n;
+    } else {
+        for (int64_t t = 0; t < n; ++t) {
+            if (t % K == 0)
+                LBM_CUDA(h, cudaMemcpyAsync(ckpt + size_t(t / K) * S, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
+            a.src = h->pop[h->cur];
+            a.dst = h->pop[1 - h->cur];
+            a.open_mask[0] = h->mask_at(t0 + t);
+            cudaError_t e = lbm::launch_step(a, h->launch, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+            h->cur = 1 - h->cur;
+            h->gbuf = h->cur;
+            h->diag_grid = h->launch.grid;
+            ++h->step;
+        }
     }
 
     // J and dJ/dP(n)

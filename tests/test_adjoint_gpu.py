@@ -41,7 +41,7 @@ def _check(gpu, ref):
     assert _rel(dc, rc) < GRAD_TOL
 
 
-@pytest.mark.parametrize("ckpt", [50, 7])
+@pytest.mark.parametrize("ckpt", [50, 7, 1])
 def test_adjoint_matches_oracle_on_small_chip(ckpt):
     prob = W.config_large_chip(96, 48)
     prob["period"] = 40
@@ -113,8 +113,33 @@ def test_adjoint_leaves_the_forward_state_and_diagnostics():
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
     assert np.array_equal(a.diagnostics(), b.diagnostics())
     assert a.step_count() == b.step_count() == 90
+    # every state kept: the same final state, step count and gradients
+    a.adjoint(31, obj[0], obj[1], obj[2], obj[3], ckpt_every=1)
+    b.step(31)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert a.step_count() == b.step_count() == 121
     a.close()
     b.close()
+
+
+def test_adjoint_keeping_every_state_equals_checkpointed():
+    prob = W.config_large_chip(96, 48)
+    prob["period"] = 30
+    obj = _objective(prob)
+    res = []
+    for K in (1, 13):
+        c = lbm.Chip.from_problem(prob)
+        c.set_valve_schedule(prob["period"], prob["states"])
+        res.append(c.adjoint(70, obj[0], obj[1], obj[2], obj[3], ckpt_every=K))
+        c.close()
+    # the same kernels on the same states: identical up to the order of the
+    # FP64 gradient atomics
+    (J1, t1, u1, c1), (J2, t2, u2, c2) = res
+    assert J1 == J2
+    assert abs(t1 - t2) <= 1e-9 * abs(t2)
+    assert np.allclose(u1, u2, rtol=1e-9, atol=0) and np.allclose(c1, c2, rtol=1e-9, atol=0)
 
 
 def test_adjoint_rejects_bad_objectives():
