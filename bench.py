@@ -50,6 +50,9 @@ def _args():
                    help="step kernel: 0 library default, 1 registers, 2 bulk-copy pipeline")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                    help="storage of the populations of the timed chip (profiling runs)")
+    p.add_argument("--kernel", default="step", choices=["step", "scalar", "adjoint"],
+                   help="profiling runs: time the scalar-only step or the adjoint instead of the coupled step "
+                        "(prints a short JSON line)")
     return p.parse_args()
 
 
@@ -431,6 +434,48 @@ def aggregate_glups(per_rank_units, seconds, world_size):
     return world_size * per_rank_units / reduce_max(seconds, world_size) / 1e9
 
 
+def _profile_target(args, device):
+    """The scalar-only step (after `warmup` coupled steps, on the velocity
+    field of the chip at that point) or the adjoint of `steps` steps of the
+    gradient chip with every state kept, for kernel profiles."""
+    import numpy as np
+    import torch
+    from paper_1307_4703_gb300 import lbm, workloads as W
+    stream = torch.cuda.Stream()
+    if args.kernel == "scalar":
+        prob = _problem(args.workload)
+        chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=device)
+        chip.set_valve_schedule(prob["period"], prob["states"])
+        chip.step(max(args.warmup, 1))
+        for w in sorted(set(prob["states"])):
+            chip.store_velocity(w)
+        chip.scalar_step(max(args.warmup, 1), 2.0)
+        chip.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            chip.scalar_step(1, 2.0)
+        e1.record(stream)
+        stream.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / max(args.steps, 1)
+        out = {"kernel": "scalar_frozen_step", "workload": prob["name"], "us_per_step": us,
+               "glups": W.fluid_count(prob) / us / 1e3}
+    else:
+        prob = W.config_adjoint_chip()
+        cx0, cx1, cy0, cy1 = prob["chamber"]
+        oy = np.arange(cy0, cy1)
+        ox = np.full_like(oy, (cx0 + cx1) // 2)
+        chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=device)
+        chip.set_valve_schedule(prob["period"], prob["states"])
+        t0 = time.perf_counter()
+        chip.adjoint(args.steps, ox, oy, (oy - cy0) / max(1, cy1 - 1 - cy0), ckpt_every=1)
+        out = {"kernel": "adjoint", "workload": prob["name"], "steps": args.steps,
+               "seconds": time.perf_counter() - t0}
+    chip.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -445,6 +490,9 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     build.build()
     torch.cuda.set_device(local)
+    if args.kernel != "step":
+        _profile_target(args, local)
+        return
     prob = _problem(args.workload)
     fluid = W.fluid_count(prob)
     stream = torch.cuda.Stream()
