@@ -50,6 +50,8 @@ def _load():
         lib.orc_adjoint_step.argtypes = [ctypes.c_void_p, ctypes.c_uint, d, d, d, d, d, d, d]
         lib.orc_scalar_step.argtypes = [ctypes.c_void_p, ctypes.c_uint, d, d]
         lib.orc_set_decay.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        lib.orc_set_wall_scheme.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.orc_set_wall_scheme.restype = ctypes.c_int
         lib.orc_adjoint.restype = ctypes.c_double
         lib.orc_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_uint), ctypes.c_int,
                                     P(ctypes.c_int), P(ctypes.c_int), d, d, d, d, d]
@@ -82,7 +84,7 @@ class OracleLattice:
     """
 
     def __init__(self, solid, tau_f, tau_g, w0=1.0 / 3.0, periodic=False, ports=(),
-                 edge_u=None, edge_C=None, decay=0.0):
+                 edge_u=None, edge_C=None, decay=0.0, wall_scheme=0):
         lib = _load()
         solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
         self.ny, self.nx = solid.shape
@@ -107,6 +109,8 @@ class OracleLattice:
         self.t = 0
         if decay:
             lib.orc_set_decay(self._h, float(decay))
+        if wall_scheme and lib.orc_set_wall_scheme(self._h, int(wall_scheme)) != 0:
+            raise ValueError("oracle: wall scheme %r" % wall_scheme)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -215,6 +219,6 @@ def from_problem(prob, **over):
     """Build an OracleLattice from a problem dict of the seeded generators."""
     kw = dict(tau_f=prob["tau"], tau_g=prob["tau_c"], w0=prob.get("w0", 1.0 / 3.0),
               ports=prob["ports"], edge_u=prob["edge_u"], edge_C=prob["edge_C"],
-              decay=prob.get("decay", 0.0))
+              decay=prob.get("decay", 0.0), wall_scheme=prob.get("wall_scheme", 0))
     kw.update(over)
     return OracleLattice(prob["solid"], **kw)

@@ -36,6 +36,8 @@ struct orc_lattice {
     int nx, ny, periodic;
     double tau_f, tau_g, w0;
     double decay;          /* k of the reaction term R = -k C */
+    int wall_scheme;       /* 0 halfway bounce-back, 1 equilibrium interpolation */
+    double* mom;           /* rho, j_x, j_y of every node at the start of a step (scheme 1) */
     unsigned char* solid;  /* ny*nx */
     double* f;             /* pre-collision f_i(x,t), [node*9 + i] */
     double* g;             /* pre-collision g_i(x,t), [node*5 + i] */
@@ -181,10 +183,53 @@ void orc_free(orc_lattice* L)
     free(L->edge_u);
     free(L->edge_C);
     free(L->ports);
+    free(L->mom);
     free(L);
 }
 
 void orc_set_decay(orc_lattice* L, double k) { L->decay = k; }
+
+int orc_set_wall_scheme(orc_lattice* L, int scheme)
+{
+    if (scheme != 0 && scheme != 1) return -1;
+    if (scheme == 1 && !L->mom) {
+        L->mom = (double*)calloc((size_t)L->nx * (size_t)L->ny * 3, sizeof(double));
+        if (!L->mom) return -1;
+    }
+    L->wall_scheme = scheme;
+    return 0;
+}
+
+/* The paper's wall ("Boundary Conditions"): the population f_m missing at
+ * fluid node (x, y) -- its source (x, y) - e_m is not fluid -- becomes the
+ * equilibrium of a density extrapolated to first order from the fluid in
+ * the direction e_m, 2 rho(x + e_m) - rho(x + 2 e_m), and a momentum
+ * interpolated linearly between zero at the wall, half a link behind the
+ * node, and the fluid node x + e_m one and a half links from it:
+ * j = j(x + e_m) / 3.  Moments are those at the start of the step.  Where
+ * x + 2 e_m is not fluid the density is that of x + e_m; where x + e_m is
+ * not fluid either, the node's own density with zero momentum. */
+static double wall_population(const orc_lattice* L, int x, int y, int m)
+{
+    const double* M = L->mom;
+    int x1 = x + EX[m], y1 = y + EY[m], x2 = x + 2 * EX[m], y2 = y + 2 * EY[m];
+    if (L->periodic) {
+        x1 = (x1 + L->nx) % L->nx;
+        y1 = (y1 + L->ny) % L->ny;
+        x2 = (x2 + L->nx) % L->nx;
+        y2 = (y2 + L->ny) % L->ny;
+    }
+    double rho, jx = 0.0, jy = 0.0;
+    if (is_fluid(L, x1, y1)) {
+        const double* m1 = M + (size_t)node(L, x1, y1) * 3;
+        rho = is_fluid(L, x2, y2) ? 2.0 * m1[0] - M[(size_t)node(L, x2, y2) * 3] : m1[0];
+        jx = m1[1] / 3.0;
+        jy = m1[2] / 3.0;
+    } else {
+        rho = M[(size_t)node(L, x, y) * 3];
+    }
+    return feq(m, rho, jx / rho, jy / rho);
+}
 
 void orc_init_equilibrium(orc_lattice* L, const double* rho, const double* ux,
                           const double* uy, const double* C)
@@ -290,6 +335,19 @@ void orc_step(orc_lattice* L, unsigned open_mask)
 {
     const int nx = L->nx, ny = L->ny;
 
+    /* moments at the start of the step, for the paper's wall scheme */
+    if (L->wall_scheme == 1)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                if (!is_fluid(L, x, y)) continue;
+                int c = node(L, x, y);
+                double r, ux, uy;
+                moments(L->f + (size_t)c * 9, &r, &ux, &uy);
+                L->mom[(size_t)c * 3] = r;
+                L->mom[(size_t)c * 3 + 1] = r * ux;
+                L->mom[(size_t)c * 3 + 2] = r * uy;
+            }
+
     /* 1. collision (moments of Eq. moments, relaxation of Eq. lbequation) */
     collide_all(L, L->fp, L->gp);
 
@@ -310,6 +368,8 @@ void orc_step(orc_lattice* L, unsigned open_mask)
                 }
                 if (is_fluid(L, xn, yn))
                     L->f[node(L, xn, yn) * 9 + i] = L->fp[c * 9 + i];
+                else if (L->wall_scheme == 1)
+                    L->f[c * 9 + OPP[i]] = wall_population(L, x, y, OPP[i]);
                 else
                     L->f[c * 9 + OPP[i]] = L->fp[c * 9 + i];
             }
@@ -637,7 +697,7 @@ double orc_adjoint(orc_lattice* L, int n, const unsigned* masks, int n_obj,
                    double* dJ_dC_in)
 {
     const int ny = L->ny;
-    if (L->decay != 0.0) return -1.0;
+    if (L->decay != 0.0 || L->wall_scheme != 0) return -1.0;
     for (int p = 0; p < L->n_ports; ++p)
         if (L->ports[p].kind != ORC_VELOCITY && L->ports[p].kind != ORC_PRESSURE) return -1.0;
     size_t nodes = (size_t)L->nx * (size_t)ny;

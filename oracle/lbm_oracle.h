@@ -86,6 +86,15 @@ void orc_free(orc_lattice* L);
 /* Decay rate k >= 0 of the compound (default 0). */
 void orc_set_decay(orc_lattice* L, double k);
 
+/* Fluid wall scheme: 0 halfway bounce-back (default); 1 the paper's
+ * equilibrium interpolation ("Boundary Conditions"): a population missing at
+ * a fluid node because its source is not fluid becomes the equilibrium of a
+ * density extrapolated to first order from the fluid along its direction
+ * and a momentum interpolated between zero at the wall (half a link behind
+ * the node) and the next fluid node.  The scalar keeps bounce-back (zero
+ * flux).  Returns 0, or -1 for an unknown scheme or no memory. */
+int orc_set_wall_scheme(orc_lattice* L, int scheme);
+
 /* Set every fluid node to the equilibrium of the given fields (ny*nx). */
 void orc_init_equilibrium(orc_lattice* L, const double* rho, const double* ux,
                           const double* uy, const double* C);
@@ -137,7 +146,8 @@ void orc_adjoint_step(const orc_lattice* L, unsigned open_mask, const double* f_
                       double* af, double* ag, double* grad);
 
 /* Adjoint of lattices whose ports are of kinds ORC_VELOCITY and
- * ORC_PRESSURE and without decay (orc_adjoint returns -1 otherwise).
+ * ORC_PRESSURE, without decay and with bounce-back walls (orc_adjoint
+ * returns -1 otherwise).
  * Run n steps forward from the current state with the given valve words
  * (the lattice ends at S_n, as after n calls of orc_step), then the reverse
  * pass for J = sum_k weight_k (C(x_k, y_k, n) - target_k)^2.  Returns J and

@@ -101,6 +101,12 @@ PAPER_BC_MUTANTS = [
     ("scalar rescaled to 1", "double gamma = C_in / sum;", "double gamma = 1.0 / sum;"),
     ("scalar fallback at rest", "for (int i = 0; i < 5; ++i) gn[i] = geq(L, i, C_in, ux, uy);",
      "for (int i = 0; i < 5; ++i) gn[i] = geq(L, i, C_in, 0.0, 0.0);"),
+    ("wall momentum halved instead of a third", "jx = m1[1] / 3.0;\n        jy = m1[2] / 3.0;",
+     "jx = m1[1] / 2.0;\n        jy = m1[2] / 2.0;"),
+    ("wall density not extrapolated", "rho = is_fluid(L, x2, y2) ? 2.0 * m1[0] - M[(size_t)node(L, x2, y2) * 3] : m1[0];",
+     "rho = m1[0];"),
+    ("wall neighbours behind the node", "int x1 = x + EX[m], y1 = y + EY[m], x2 = x + 2 * EX[m], y2 = y + 2 * EY[m];",
+     "int x1 = x - EX[m], y1 = y - EY[m], x2 = x - 2 * EX[m], y2 = y - 2 * EY[m];"),
 ]
 
 CASES = [m + ("tests/test_oracle_pins.py",) for m in MUTANTS] + \

@@ -159,3 +159,76 @@ def test_rescaling_port_node_from_first_principles():
     col = np.array([gp[y, x, 0], gp[y, x, 1], gp[y - 1, x, 2], gp[y, x + 1, 3], gp[y + 1, x, 4]])
     assert np.abs(g2[y, x] - col * 0.8 / col.sum()).max() < 1e-15
     assert np.abs(L.fields()[3][1:5, 0] - 0.8).max() < 1e-15
+
+
+def test_equilibrium_wall_keeps_a_fluid_at_rest_exactly():
+    solid = np.zeros((20, 30), np.uint8)
+    solid[8:12, 10:14] = 1
+    L = oracle.OracleLattice(solid, 0.8, 0.7, wall_scheme=1)
+    L.step(0, 50)
+    f = L.populations()[0]
+    assert np.abs(f[solid == 0] - W9).max() < 1e-15
+
+
+def test_equilibrium_wall_node_from_first_principles():
+    """One step from known fields: at a fluid node next to an obstacle, every
+    population whose source is solid equals f_eq of rho = 2 rho(x + e_m) -
+    rho(x + 2 e_m) and j = j(x + e_m) / 3 (the paper's first-order
+    extrapolation and interpolation), the other populations arrive by free
+    flight."""
+    ny, nx = 12, 16
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[5:7, 6:9] = 1
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    rho = 1.0 + 0.01 * np.sin(0.7 * xx + 0.3 * yy)
+    ux = 0.03 * np.cos(0.5 * yy)
+    uy = 0.02 * np.sin(0.4 * xx)
+    L = oracle.OracleLattice(solid, 0.75, 0.6, wall_scheme=1)
+    L.init_equilibrium(rho, ux, uy, 0.0)
+    fp, _ = L.post_collision()
+    L.step(0)
+    f = L.populations()[0]
+
+    def feq(i, r, vx, vy):
+        eu = EX[i] * vx + EY[i] * vy
+        return W9[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * (vx * vx + vy * vy))
+
+    checked = 0
+    for (x, y) in ((5, 5), (9, 6), (7, 4), (7, 7), (5, 7)):
+        assert not solid[y, x]
+        for m in range(9):
+            xs, ys = x - EX[m], y - EY[m]
+            if solid[ys, xs]:
+                x1, y1, x2, y2 = x + EX[m], y + EY[m], x + 2 * EX[m], y + 2 * EY[m]
+                r = 2 * rho[y1, x1] - rho[y2, x2]
+                jx, jy = rho[y1, x1] * ux[y1, x1] / 3, rho[y1, x1] * uy[y1, x1] / 3
+                assert abs(f[y, x, m] - feq(m, r, jx / r, jy / r)) < 1e-15, (x, y, m)
+                checked += 1
+            else:
+                assert abs(f[y, x, m] - fp[ys, xs, m]) < 1e-15
+    assert checked >= 8
+
+
+def test_equilibrium_wall_channel_profile():
+    """Pressure-driven channel with the paper's walls and ports: the steady
+    profile is a symmetric parabola (residual < 1e-3 of its maximum) whose
+    zeros lie 0.5 to 1.2 nodes beyond the halfway positions at tau = 0.65
+    (the equilibrium wall's slip; the paper tuned its pressure difference to
+    reach U within 1%)."""
+    tau, W_, Lc, U = 0.65, 20, 200, 0.00125
+    nx, ny = Lc + 1, W_
+    nu = (tau - 0.5) / 3
+    dp = 8 * nu * U * Lc / W_ ** 2
+    ports = [dict(channel=0, side=0, x=0, y0=0, y1=ny, kind=oracle.INLET_RESCALE, rho=1 + 1.5 * dp),
+             dict(channel=0, side=1, x=nx - 1, y0=0, y1=ny, kind=oracle.PRESSURE_RESCALE, rho=1 - 1.5 * dp)]
+    eu, ec = np.zeros((2, ny)), np.zeros((2, ny))
+    ec[0] = 1.0
+    L = oracle.OracleLattice(np.zeros((ny, nx)), tau, 0.6, ports=ports, edge_u=eu, edge_C=ec, wall_scheme=1)
+    L.step(1, 12000)
+    u = L.fields()[1][:, 100]
+    y = np.arange(ny) + 0.5
+    c = np.polyfit(y, u, 2)
+    assert np.abs(np.polyval(c, y) - u).max() < 1e-3 * u.max()
+    lo, hi = np.sort(np.roots(c).real)
+    assert abs((lo + hi) / 2 - W_ / 2) < 1e-6
+    assert -1.2 < lo < -0.5 and W_ + 0.5 < hi < W_ + 1.2
