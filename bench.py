@@ -32,7 +32,7 @@ METRIC = "coupled D2Q9+D2Q5 GLUPS and % HBM roofline; adjoint/forward time ratio
 UNIT = "GLUPS"
 BYTES_PER_NODE = 112  # 14 FP32 populations read + written per fluid node and step
 KERNEL_SRC = [os.path.join(ROOT, "paper_1307_4703_gb300", "csrc", f)
-              for f in ("lbm_device.cuh", "lbm_internal.h", "lbm_kernels.cu")]
+              for f in ("lbm_device.cuh", "lbm_internal.h", "lbm_step.cuh", "lbm_kernels.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "coupled_step_chip-4096x2048.md")
 
 

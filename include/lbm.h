@@ -129,6 +129,7 @@ typedef struct {
     double decay;           /* decay rate k >= 0 of the compound: the reaction term R = -k C of the
                                advection-diffusion equation ("Introduction", "Results"), added to
                                the scalar collision as w_i R (default 0); not with lbm_adjoint */
+    int32_t wall_scheme;    /* fluid walls: LBM_WALL_BOUNCE_BACK (default) or LBM_WALL_EQUILIBRIUM, see below */
     int32_t graph_steps;    /* 0 = off; else an even number <= 4096: lbm_step replays runs of this many
                                steps with unchanged valve words as one cached CUDA graph (captured
                                on first use, at most 16 per handle), which removes the per-launch
@@ -148,6 +149,18 @@ typedef struct {
  * lbm_save_state / lbm_load_state (which keep the 16-bit values bit for
  * bit); lbm_adjoint, lbm_store_velocity, lbm_set_velocity_field and
  * lbm_scalar_step need FP32 storage and return LBM_ERR_STATE. */
+/* Fluid wall scheme.  LBM_WALL_BOUNCE_BACK: halfway bounce-back (the wall
+ * half a link behind the node, exact mass conservation).
+ * LBM_WALL_EQUILIBRIUM: the paper's wall ("Boundary Conditions"): a
+ * population whose source is not fluid becomes the equilibrium of a density
+ * extrapolated to first order from the fluid along its direction,
+ * 2 rho(x + e_i) - rho(x + 2 e_i), and a momentum interpolated between zero
+ * at the wall (half a link behind the node) and the fluid node x + e_i:
+ * j(x + e_i) / 3; moments of the start of the step.  The scalar keeps
+ * bounce-back (zero flux) in both.  Not with lbm_adjoint. */
+#define LBM_WALL_BOUNCE_BACK 0
+#define LBM_WALL_EQUILIBRIUM 1
+
 #define LBM_FP32 0
 #define LBM_FP16 1
 #define LBM_BF16 2

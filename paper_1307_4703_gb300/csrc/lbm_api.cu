@@ -112,6 +112,10 @@ struct lbm_ctx {
     int graph_steps = 0;
     cudaStream_t cap_stream = nullptr;
     float decay = 0.f;         // k of the reaction term R = -k C
+    int wall_scheme = 0;       // LBM_WALL_BOUNCE_BACK or LBM_WALL_EQUILIBRIUM
+    void* wallv = nullptr;     // the paper's walls: 8 planes of wall values for the step
+    long long* woff = nullptr; // offsets of the fluid nodes with wall links
+    int n_wall = 0;
     bool paper_ports = false;  // some port has a rescaling kind (no adjoint)
     std::vector<Graph> graphs;
 
@@ -226,6 +230,18 @@ bool is_fluid(const uint8_t* mask, int nx, int ny, int x, int y)
 constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
+// One step: the paper's wall values first (when that wall scheme is on),
+// then the step kernel.
+cudaError_t launch_full_step(const lbm_ctx* h, const lbm::StepArgs& a, const lbm::StepLaunch& L, cudaStream_t s)
+{
+    if (h->wallv) {
+        cudaError_t e = lbm::launch_wall_values(a.src, h->wallv, h->links, h->woff, h->n_wall, h->plane, h->pitch,
+                                                h->precision, s);
+        if (e != cudaSuccess) return e;
+    }
+    return lbm::launch_step(a, L, s);
+}
+
 // The cached graph of graph_steps launches for the valve words in
 // a.open_mask starting from buffer cur, captured on first use.
 lbm_status step_graph(lbm_ctx* h, lbm::StepArgs a, cudaGraphExec_t* out)
@@ -245,7 +261,7 @@ lbm_status step_graph(lbm_ctx* h, lbm::StepArgs a, cudaGraphExec_t* out)
     for (int j = 0; j < h->graph_steps && e == cudaSuccess; ++j) {
         a.src = h->pop[(h->cur + j) & 1];
         a.dst = h->pop[(h->cur + j + 1) & 1];
-        e = lbm::launch_step(a, h->launch, h->cap_stream);
+        e = launch_full_step(h, a, h->launch, h->cap_stream);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e_end = cudaStreamEndCapture(h->cap_stream, &graph);
@@ -393,6 +409,11 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     }
     if ((opt.alloc == nullptr) != (opt.free == nullptr))
         return fail(nullptr, LBM_ERR_ARG, "alloc and free hooks must be given together");
+    if (opt.wall_scheme != LBM_WALL_BOUNCE_BACK && opt.wall_scheme != LBM_WALL_EQUILIBRIUM)
+        return fail(nullptr, LBM_ERR_ARG, "wall_scheme = %d: use LBM_WALL_BOUNCE_BACK or LBM_WALL_EQUILIBRIUM",
+                    opt.wall_scheme);
+    if (opt.wall_scheme == LBM_WALL_EQUILIBRIUM && opt.variant == 3)
+        return fail(nullptr, LBM_ERR_ARG, "wall_scheme = LBM_WALL_EQUILIBRIUM runs variants 1 and 2, not 3");
     if (!(opt.decay >= 0.0 && opt.decay < 1.0))
         return fail(nullptr, LBM_ERR_ARG, "decay = %g outside [0, 1)", opt.decay);
     if (opt.graph_steps < 0 || opt.graph_steps % 2 != 0 || opt.graph_steps > kMaxGraphSteps)
@@ -520,6 +541,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->elem = opt.precision == LBM_FP32 ? sizeof(float) : sizeof(uint16_t);
     h->graph_steps = opt.graph_steps;
     h->decay = float(opt.decay);
+    h->wall_scheme = opt.wall_scheme;
     for (int p = 0; p < n_ports; ++p) h->paper_ports |= ports[p].kind >= LBM_PORT_PRESSURE_RESCALE;
 
     auto bail = [&](lbm_status s) {
@@ -543,6 +565,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     L.variant = opt.variant == 1 ? lbm::kVariantRegs : opt.variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
     L.precision = opt.precision;
     L.pdl = true;  // consecutive steps overlap launch and set-up with the previous step's tail
+    L.walls = opt.wall_scheme == LBM_WALL_EQUILIBRIUM;
     if (L.variant == lbm::kVariantBulk) {
         const int nc = opt.consumer_warps ? opt.consumer_warps : kDefaultConsumers;
         L.stages = nc * (opt.pipeline_stages                ? opt.pipeline_stages
@@ -580,8 +603,17 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->diag = static_cast<double*>(dev_alloc(h, 4 * sizeof(double)));
     h->fields_tmp = static_cast<float*>(dev_alloc(h, size_t(4) * nx * ny * sizeof(float)));
     if (batch) h->rates = static_cast<float4*>(dev_alloc(h, size_t(ny) * sizeof(float4)));
+    std::vector<long long> woff;
+    if (opt.wall_scheme == LBM_WALL_EQUILIBRIUM) {
+        for (size_t o = 0; o < links.size(); ++o)
+            if (links[o] != 0 && links[o] != lbm::kSolid) woff.push_back((long long)o);
+        h->n_wall = int(woff.size());
+        h->wallv = dev_alloc(h, size_t(8) * h->plane * h->elem);
+        h->woff = static_cast<long long*>(dev_alloc(h, std::max<size_t>(1, woff.size()) * sizeof(long long)));
+    }
     if (!h->pop[0] || !h->pop[1] || !h->links || !h->rowbc || !h->tiles || !h->partials ||
-        !h->err || !h->diag || !h->fields_tmp || (batch && !h->rates))
+        !h->err || !h->diag || !h->fields_tmp || (batch && !h->rates) ||
+        (opt.wall_scheme == LBM_WALL_EQUILIBRIUM && (!h->wallv || !h->woff)))
         return bail(fail(h, LBM_ERR_OOM, "device allocation of %zu bytes failed", 2 * pop_bytes));
     if (batch) h->inst = batch->inst;
 
@@ -594,6 +626,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         e = cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && batch)
         e = cudaMemcpyAsync(h->rates, batch->rates.data(), size_t(ny) * sizeof(float4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !woff.empty())
+        e = cudaMemcpyAsync(h->woff, woff.data(), woff.size() * sizeof(long long), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->partials, 0, size_t(h->partials_cap) * 4 * sizeof(double), st);
@@ -811,6 +845,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
     a.decay = h->decay;
+    a.wallv = h->wallv;
     a.partials = h->partials;
     a.err = h->err;
     a.rates = h->rates;
@@ -835,7 +870,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
         }
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
-        cudaError_t e = lbm::launch_step(a, h->launch, h->stream);
+        cudaError_t e = launch_full_step(h, a, h->launch, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
         h->gbuf = h->cur;
@@ -1145,8 +1180,8 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_adjoint");
     if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_adjoint");
-    if (h->decay != 0.f || h->paper_ports)
-        return fail(h, LBM_ERR_STATE, "lbm_adjoint needs Zou-He ports and no decay");
+    if (h->decay != 0.f || h->paper_ports || h->wall_scheme != LBM_WALL_BOUNCE_BACK)
+        return fail(h, LBM_ERR_STATE, "lbm_adjoint needs Zou-He ports, bounce-back walls and no decay");
     if (!obj || !J || !dJ_dtau_c) return fail(h, LBM_ERR_ARG, "objective, J or dJ_dtau_c is NULL");
     if (n < 1 || K < 1) return fail(h, LBM_ERR_ARG, "n_steps = %lld and ckpt_every = %d must be >= 1", (long long)n, K);
     if (obj->n < 1 || !obj->x || !obj->y || !obj->target || !obj->weight)
@@ -1468,6 +1503,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
     a.decay = h->decay;
+    a.wallv = h->wallv;
     a.partials = part;
     a.err = err;
     if (h->precision != LBM_FP32) {
@@ -1475,6 +1511,9 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         a.gref1 = h->wg1 * lbm::kCRef;
     }
     h->mask_words(h->step, a.open_mask);
+    if (h->wallv)
+        LBM_CUDA(h, lbm::launch_wall_values(a.src, h->wallv, h->links, h->woff, h->n_wall, h->plane, h->pitch,
+                                            h->precision, h->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     LBM_CUDA(h, cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
@@ -1485,6 +1524,8 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         lbm::StepLaunch L{};
         L.precision = h->precision;
         L.pdl = true;
+        L.walls = h->wallv != nullptr;
+        if (L.walls && c.variant == 3) continue;
         if (c.variant == 1) {
             L.variant = lbm::kVariantRegs;
             L.block = 32 * c.warps;
@@ -1505,6 +1546,8 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         }
         L.grid = std::min(wave_grid(h, L, per_sm), h->partials_cap);
         e = cudaMemsetAsync(err, 0, sizeof(unsigned), h->stream);
+        // the step kernel alone (the wall values, when used, are computed
+        // once below from the current state)
         for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = lbm::launch_step(a, L, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
         for (int j = 0; j < trial_steps && e == cudaSuccess; ++j) e = lbm::launch_step(a, L, h->stream);

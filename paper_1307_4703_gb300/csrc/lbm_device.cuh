@@ -279,9 +279,12 @@ struct LaneDiag {
 // Halfway bounce-back: a link from a wall returns the node's own
 // post-collision population of the opposite direction (row y of the source
 // buffer).  Only lanes next to a wall load anything here.
-template <typename T>
+// kWalls: the fluid planes take the paper's wall values that
+// launch_wall_values left in plane i - 1 of Wb instead (the scalar keeps
+// bounce-back).
+template <typename T, bool kWalls = false>
 __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, const T* S, long long P,
-                                            long long oC, float gref1 = 0.f)
+                                            long long oC, float gref1 = 0.f, const T* Wb = nullptr)
 {
     unsigned wall = 0;  // union of the wall links of the fluid nodes
 #pragma unroll
@@ -293,7 +296,9 @@ __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, c
 #pragma unroll
     for (int i = 1; i <= 8; ++i) {
         if (wall & (1u << (i - 1))) {
-            const float4 own = Codec<T>::ld4(S + opp(i) * P + oC, 0.f);
+            const T* src = S + opp(i) * P;  // the node's own opposite population
+            if constexpr (kWalls) src = Wb + (i - 1) * P;
+            const float4 own = Codec<T>::ld4(src + oC, 0.f);
             const float4 ownc = i <= 4 ? Codec<T>::ld4(S + (9 + opp(i)) * P + oC, gref1) : own;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -371,6 +376,68 @@ __device__ __noinline__ bool rescaling_port(PortNode& n, bool west, const RowBC&
         g[4] = c1 - cy;
     }
     return false;
+}
+
+// Lattice direction components (Eq. lattice).
+__device__ __forceinline__ constexpr int dir_x(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__device__ __forceinline__ constexpr int dir_y(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+
+// rho - 1 and the momentum of the stored populations (deviations) of one node.
+template <typename T>
+__device__ __forceinline__ void node_moments(const T* S, long long P, long long o, float& rd, float& jx, float& jy)
+{
+    float f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = Codec<T>::ld1(S + i * P + o, 0.f);
+    rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+}
+
+// The paper's wall ("Boundary Conditions") for population i of the fluid
+// node at offset own, whose source x - e_i is not fluid (lb: the node's
+// wall-link byte, bit j-1 set = the source x - e_j is not fluid): the
+// equilibrium, as a deviation f_eq - w_i, of a density extrapolated to first
+// order from the fluid along e_i, 2 rho(x + e_i) - rho(x + 2 e_i), and the
+// momentum interpolated between zero at the wall, half a link behind the
+// node, and x + e_i, one and a half links from it: j(x + e_i) / 3.  Moments
+// of the stored state S (the start of the step).  Where x + 2 e_i is not
+// fluid the density is that of x + e_i; where x + e_i is not fluid either,
+// the node's own density with zero momentum.
+template <typename T>
+__device__ __forceinline__ float equilibrium_wall(int i, unsigned lb, const T* S, const uint8_t* links, long long P,
+                                                  long long own, int pitch)
+{
+    const int back = opp(i) - 1;  // bit of "x + e_i is not fluid"
+    float rd, jx = 0.f, jy = 0.f;
+    if (!((lb >> back) & 1u)) {
+        const long long o1 = own + dir_x(i) + (long long)dir_y(i) * pitch;
+        float r1, x1, y1;
+        node_moments(S, P, o1, r1, x1, y1);
+        if (!((links[o1] >> back) & 1u)) {
+            float r2, x2, y2;
+            node_moments(S, P, o1 + dir_x(i) + (long long)dir_y(i) * pitch, r2, x2, y2);
+            rd = 2.f * r1 - r2;  // 2 rho1 - rho2 - 1
+        } else {
+            rd = r1;
+        }
+        jx = x1 * (1.f / 3.f);
+        jy = y1 * (1.f / 3.f);
+    } else {
+        float ox, oy;
+        node_moments(S, P, own, rd, ox, oy);
+    }
+    const float rho = 1.f + rd;
+    const float ux = jx / rho, uy = jy / rho;
+    const float eu = float(dir_x(i)) * ux + float(dir_y(i)) * uy;
+    const float w = i <= 4 ? kWa : kWd;
+    return w * (rd + rho * (3.f * eu + 4.5f * eu * eu - 1.5f * (ux * ux + uy * uy)));
 }
 
 template <typename T>

@@ -47,6 +47,7 @@ struct StepLaunch {
     int stages;   // shared-memory stages per block (computing warps x stages per warp)
     int precision = kFP32;  // storage of the populations
     bool pdl = false;       // launch as a programmatic dependent of the previous kernel
+    bool walls = false;     // the paper's walls (variants 1 and 2; see StepArgs::wallv)
 };
 
 struct RowBC {
@@ -75,6 +76,9 @@ struct StepArgs {
     float wg1;              // scalar axis weight (1 - wg0) / 4
     float inv_cs2g;         // 1 / c_s^2 of the scalar lattice
     float decay;            // k of the reaction term R = -k C (0: none)
+    const void* wallv;      // the paper's walls: 8 planes (population i in plane i - 1, storage type) of
+                            // the wall values launch_wall_values computed for this step; null: halfway
+                            // bounce-back
     uint32_t open_mask[kMaskWords];  // valve bits of this step: channel c is bit c % 32 of word c / 32
     double* partials;       // 4 diagnostics partial sums per block (scratch)
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
@@ -142,6 +146,20 @@ int bulk_stage_bytes(int precision = 0);
 cudaError_t prepare_step_kernels();
 cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s);
 // out[0..3] = sum of the n_blocks x 4 block partials, in a fixed order.
+// The paper's wall values for the step that reads src (lbm_device.cuh,
+// equilibrium_wall): for every fluid node with wall links (offsets
+// woff[0..n)), the value of each population i whose source is not fluid
+// goes to plane i - 1 of W (8 planes of the storage type), which the step
+// kernels' kWalls instantiations read instead of bounce-back.  A
+// programmatic dependent of the previous kernel.
+cudaError_t launch_wall_values(const void* src, void* W, const uint8_t* links, const long long* woff, int n,
+                               long long plane, int pitch, int precision, cudaStream_t s);
+
+// The step kernels with the paper's walls (lbm_walls.cu): variants 1 and 2.
+cudaError_t launch_step_walls(const StepArgs& a, const StepLaunch& l, cudaStream_t s);
+cudaError_t step_walls_occupancy(const StepLaunch& l, int* blocks_per_sm);
+cudaError_t prepare_walls_kernels();
+
 cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s);
 cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm);
 

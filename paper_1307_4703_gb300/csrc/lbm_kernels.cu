@@ -32,7 +32,9 @@
 //                      deviations, FP32 arithmetic); so is the bulk variant.
 // All share the per-node arithmetic of lbm_device.cuh; the FP32 variants give
 // identical results.
-#include "lbm_device.cuh"
+#include <algorithm>
+
+#include "lbm_step.cuh"
 
 namespace lbm {
 namespace {
@@ -57,245 +59,6 @@ __global__ void diag_finish(const double* partials, int n_blocks, double* out)
         for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
-}
-
-// ---------------------------------------------------------------------------
-// Variant 1: registers and warp shuffles
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
-{
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    const long long P = a.plane;
-    const T* __restrict__ S = reinterpret_cast<const T*>(a.src);
-    T* __restrict__ D = reinterpret_cast<T*>(a.dst);
-
-    LaneDiag diag;
-    bool bad = false;
-
-    const int stride = gridDim.x * wpb;
-    int t = blockIdx.x * wpb + warp;
-    uint2 next = t < a.n_tiles ? a.tiles[t] : make_uint2(0u, 0u);
-    grid_dependency_sync();
-    for (; t < a.n_tiles; t += stride) {
-        const uint2 tile = next;  // the following entry is fetched one tile ahead
-        if (t + stride < a.n_tiles) next = a.tiles[t + stride];
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
-        const long long oC = (long long)y * a.pitch + x0;
-        // Rows outside the grid are clamped to a valid row: every link that
-        // crosses y = -1/2 or y = ny - 1/2 is a wall link, so the value read
-        // there is never used.
-        const long long oS = (long long)(y > 0 ? y - 1 : y) * a.pitch + x0;
-        const long long oN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + x0;
-        const int halo_w = x0 > 0 ? -1 : 0;
-        const int halo_e = x0 + 4 < a.pitch ? 4 : 3;
-        const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
-        const bool act = lk != 0xFFFFFFFFu;  // some node of this lane is fluid
-        // A shifted plane's edge value also feeds the neighbouring lane (its
-        // pull source may be fluid in row y -+ 1 even where this lane's own
-        // nodes are all solid), so a lane loads it when it or that
-        // neighbour is active.
-        const unsigned ball = __ballot_sync(kFull, act);
-        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;  // feeds lane + 1
-        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;  // feeds lane - 1
-
-        // ---- free flight (pull): v[p] component k = plane p at (x0+k) - e ----
-        float4 v[kPlanes];
-        pull_quad<false>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane, a.gref0, a.gref1);
-        if (act) {
-            bounce_back(v, lk, S, P, oC, a.gref1);
-            const RowBC bw = a.rowbc[y];
-            const RowBC be = a.rowbc[a.ny + y];
-            QuadAcc q;
-            collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
-#pragma unroll
-            for (int p = 0; p < kPlanes; ++p)
-                Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
-            bad |= q.bad;
-            diag.add(q);
-        }
-    }
-
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
-    block_partials(a, diag);
-}
-
-// ---------------------------------------------------------------------------
-// Variant 2: bulk-copy pipeline through shared memory
-// ---------------------------------------------------------------------------
-// One staged tile: the 14 plane rows the tile pulls from, each with a
-// 16-byte halo on both sides (4 FP32 or 8 16-bit elements, so that every copy
-// starts on a 16-byte boundary), the tile's 128 wall-link bytes, the port
-// entries of its row and the tile's table entry.
-template <typename T>
-struct __align__(16) StageT {
-    static constexpr int kHalo = 16 / int(sizeof(T));  // elements per 16 bytes
-    T pl[kPlanes][kTileNodes + 2 * kHalo];
-    unsigned links[kTileNodes / 4];
-    RowBC bc[2];
-    float4 rates;  // the row's relaxation rates (copied only for batches of chips)
-    uint2 tile;
-    uint2 pad;
-};
-using Stage = StageT<float>;
-static_assert(sizeof(Stage) % 16 == 0 && sizeof(StageT<__half>) % 16 == 0,
-              "stage size must keep 16-byte alignment");
-static_assert(offsetof(Stage, links) % 16 == 0 && offsetof(Stage, bc) % 16 == 0 &&
-                  offsetof(Stage, rates) % 16 == 0,
-              "bulk-copy targets");
-static_assert(offsetof(StageT<__half>, links) % 16 == 0 && offsetof(StageT<__half>, bc) % 16 == 0 &&
-                  offsetof(StageT<__half>, rates) % 16 == 0,
-              "bulk-copy targets");
-static_assert(sizeof(StageT<__half>) == sizeof(StageT<__nv_bfloat16>), "16-bit stages");
-
-// Stage ring: consumer warp c owns stages [c * per, (c + 1) * per) and takes
-// the block's tiles c, c + nc, c + 2 nc, ...; its k-th tile goes to stage
-// c * per + k % per as that stage's use k / per.  Every stage is therefore
-// filled and drained in order by one producer and one consumer, so the
-// parity waits on its two mbarriers never skip a phase.
-//
-// Copies must start and end on 16-byte boundaries: a row's copied span is
-// widened to whole multiples of Q = 16 / sizeof(T) elements (4 FP32 or 8
-// 16-bit), and the shifted planes take Q more on each side.
-template <typename T>
-__global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const StepArgs a, int per)
-{
-    using StageX = StageT<T>;
-    constexpr int Q = StageX::kHalo;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nc = (blockDim.x >> 5) - 1;  // consumer warps; the last warp produces
-    const int n_stages = nc * per;
-    StageX* st = reinterpret_cast<StageX*>(smem);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(n_stages) * sizeof(StageX));
-    uint64_t* empty = full + n_stages;
-    const long long P = a.plane;
-    const T* __restrict__ S = reinterpret_cast<const T*>(a.src);
-    T* __restrict__ D = reinterpret_cast<T*>(a.dst);
-    const int G = int(gridDim.x);
-    // this block's tiles: blockIdx.x, blockIdx.x + G, ...
-    const int n_items = int(blockIdx.x) < a.n_tiles ? (a.n_tiles - 1 - int(blockIdx.x)) / G + 1 : 0;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < n_stages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
-    grid_dependency_sync();
-
-    LaneDiag diag;
-    bool bad = false;
-
-    if (warp == nc) {
-        // ---------------- producer warp: lane l owns stage
-        //   s_l = (l % nc) * per + l / nc and fills it with tile base + l of
-        //   every batch of n_stages consecutive tiles (that tile is use `batch`
-        //   of s_l), so up to n_stages tiles are issued in parallel ----------------
-        const bool mine = lane < n_stages;
-        const int s = (lane % nc) * per + lane / nc;
-        int last_use = -1;
-        for (int batch = 0, base = 0; base < n_items; ++batch, base += n_stages) {
-            const int j = base + lane;
-            bool good = true;
-            if (mine && j < n_items) {
-                const uint2 tile = a.tiles[blockIdx.x + size_t(j) * G];
-                if (batch > 0 && !mbar_wait(&empty[s], uint32_t(batch - 1) & 1u)) {
-                    good = false;
-                } else {
-                    const int y = int(tile.x >> kSegBits);
-                    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
-                    const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
-                    // columns of the lanes that hold fluid (widened to whole
-                    // 16-byte units), and one unit more on each side for the
-                    // planes that pull from x -+ 1
-                    const int us = x0 + ((4 * q0) & ~(Q - 1));
-                    const int ue = x0 + ((4 * q1 + 4 + Q - 1) & ~(Q - 1));
-                    const int ss = us - Q > 0 ? us - Q : 0;
-                    const int se = ue + Q < a.pitch ? ue + Q : a.pitch;
-                    const long long rC = (long long)y * a.pitch;
-                    const long long rS = (long long)(y > 0 ? y - 1 : y) * a.pitch;
-                    const long long rN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch;
-                    const uint32_t bytes = uint32_t(6 * (ue - us) + 8 * (se - ss)) * uint32_t(sizeof(T)) +
-                                           kTileNodes + 2 * sizeof(RowBC) + (a.rates ? sizeof(float4) : 0);
-                    st[s].tile = tile;  // ordered before the consumer by the arrive below
-                    mbar_arrive_expect_tx(&full[s], bytes);
-#pragma unroll
-                    for (int p = 0; p < kPlanes; ++p) {
-                        const long long r = src_row(p) == 0 ? rC : src_row(p) == 1 ? rS : rN;
-                        const int b = src_col(p) == 0 ? us : ss;
-                        const int e = src_col(p) == 0 ? ue : se;
-                        bulk_g2s(&st[s].pl[p][b - x0 + Q], S + p * P + r + b, uint32_t(e - b) * uint32_t(sizeof(T)),
-                                 &full[s]);
-                    }
-                    bulk_g2s(st[s].links, a.links + rC + x0, kTileNodes, &full[s]);
-                    bulk_g2s(&st[s].bc[0], a.rowbc + y, sizeof(RowBC), &full[s]);
-                    bulk_g2s(&st[s].bc[1], a.rowbc + a.ny + y, sizeof(RowBC), &full[s]);
-                    if (a.rates) bulk_g2s(&st[s].rates, a.rates + y, sizeof(float4), &full[s]);
-                    last_use = batch;
-                }
-            }
-            if (!__all_sync(kFull, good)) {
-                if (lane == 0) atomicOr(a.err, 2u);
-                break;
-            }
-        }
-        // no copy may still be writing this block's shared memory at exit
-        if (mine && last_use >= 0 && !mbar_wait(&full[s], uint32_t(last_use) & 1u)) atomicOr(a.err, 2u);
-        __syncwarp();
-    } else {
-        // ---------------- consumers ----------------
-        for (int k = 0, j = warp; j < n_items; ++k, j += nc) {
-            const int s = warp * per + k % per;
-            const uint32_t use = uint32_t(k / per);
-            if (!__all_sync(kFull, mbar_wait(&full[s], use & 1u))) {
-                if (lane == 0) atomicOr(a.err, 2u);
-                break;
-            }
-            const StageX& sg = st[s];
-            const uint2 tile = sg.tile;
-            const int y = int(tile.x >> kSegBits);
-            const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
-            const long long oC = (long long)y * a.pitch + x0;
-            const unsigned lk = sg.links[lane];
-            const bool act = lk != 0xFFFFFFFFu;
-            const RowBC bw = sg.bc[0], be = sg.bc[1];
-            const float2 omega = a.rates ? make_float2(sg.rates.x, sg.rates.y) : make_float2(a.omega_f, a.omega_g);
-            // ---- free flight (pull) from the staged rows ----
-            float4 v[kPlanes];
-            if (act) {
-#pragma unroll
-                for (int p = 0; p < kPlanes; ++p) {
-                    const T* row = sg.pl[p] + 4 * lane;
-                    const float off = plane_offset(p, a.gref0, a.gref1);
-                    const float4 c = Codec<T>::lds4(row + Q, off);
-                    if (src_col(p) == 0) v[p] = c;
-                    else if (src_col(p) == 1) v[p] = make_float4(Codec<T>::lds1(row + Q - 1, off), c.x, c.y, c.z);
-                    else v[p] = make_float4(c.y, c.z, c.w, Codec<T>::lds1(row + Q + 4, off));
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be refilled
-            if (act) {
-                bounce_back(v, lk, S, P, oC, a.gref1);
-                QuadAcc q;
-                collide_quad(v, lk, x0, bw, be, a, S, oC, omega, q);
-#pragma unroll
-                for (int p = 0; p < kPlanes; ++p)
-                    Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
-                bad |= q.bad;
-                diag.add(q);
-            }
-        }
-        if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
-    }
-    block_partials(a, diag);
 }
 
 // ---------------------------------------------------------------------------
@@ -418,7 +181,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
             if (issued < n_items) pending = a.tiles[gw + size_t(issued) * W];
         }
         if (act) {
-            bounce_back(v, lk, S, P, oC);
+            bounce_back<float, false>(v, lk, S, P, oC);
             QuadAcc q;
             collide_quad(v, lk, x0, bw, be, a, S, oC, omega, q);
 #pragma unroll
@@ -536,7 +299,48 @@ int elementwise_grid(long long n)
     return int(want < 65536 ? want : 65536);
 }
 
+// The paper's wall values of one step (see launch_wall_values).
+template <typename T>
+__global__ void wall_values(const T* S, T* W, const uint8_t* links, const long long* woff, int n, long long P,
+                            int pitch)
+{
+    grid_dependency_sync();
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long o = woff[e];
+        const unsigned lb = links[o];
+        for (int i = 1; i < 9; ++i)
+            if ((lb >> (i - 1)) & 1u)
+                Codec<T>::st1(W + (i - 1) * P + o, equilibrium_wall(i, lb, S, links, P, o, pitch), 0.f);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wall_values(const void* src, void* W, const uint8_t* links, const long long* woff, int n,
+                               long long plane, int pitch, int precision, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(std::max(1, std::min((n + 255) / 256, 4096))));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (precision == kFP16)
+        e = cudaLaunchKernelEx(&cfg, wall_values<__half>, static_cast<const __half*>(src), static_cast<__half*>(W),
+                               links, woff, n, plane, pitch);
+    else if (precision == kBF16)
+        e = cudaLaunchKernelEx(&cfg, wall_values<__nv_bfloat16>, static_cast<const __nv_bfloat16*>(src),
+                               static_cast<__nv_bfloat16*>(W), links, woff, n, plane, pitch);
+    else
+        e = cudaLaunchKernelEx(&cfg, wall_values<float>, static_cast<const float*>(src), static_cast<float*>(W), links,
+                               woff, n, plane, pitch);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
 
 size_t bulk_smem_bytes(int stages, int precision)
 {
@@ -553,17 +357,18 @@ cudaError_t prepare_step_kernels()
 {
     // The attribute belongs to the kernel, not to a handle: allow the largest
     // ring any handle may ask for, so handles of different shapes coexist.
-    cudaError_t e = cudaFuncSetAttribute(coupled_step_bulk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(coupled_step_bulk<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(bulk_smem_bytes(kMaxStages)));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(coupled_step_bulk<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(coupled_step_bulk<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(bulk_smem_bytes(kMaxStages, kFP16)));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(coupled_step_bulk<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(coupled_step_bulk<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(bulk_smem_bytes(kMaxStages, kBF16)));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(coupled_step_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(bulk_smem_bytes(kMaxStages)));
+    if (e == cudaSuccess) e = prepare_walls_kernels();
     return e;
 }
 
@@ -578,23 +383,24 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = l.pdl ? 1 : 0;
+    if (a.wallv) return launch_step_walls(a, l, s);
     cudaError_t e;
     if (l.variant == kVariantBulk) {
         const int per = l.stages / (l.block / 32 - 1);
         cfg.dynamicSmemBytes = bulk_smem_bytes(l.stages, l.precision);
-        if (l.precision == kFP16) e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<__half>, a, per);
-        else if (l.precision == kBF16) e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<__nv_bfloat16>, a, per);
-        else e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<float>, a, per);
+        if (l.precision == kFP16) e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<__half, false>, a, per);
+        else if (l.precision == kBF16) e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<__nv_bfloat16, false>, a, per);
+        else e = cudaLaunchKernelEx(&cfg, coupled_step_bulk<float, false>, a, per);
     } else if (l.variant == kVariantPipe) {
         const int per = l.stages / (l.block / 32);
         cfg.dynamicSmemBytes = bulk_smem_bytes(l.stages);
         e = cudaLaunchKernelEx(&cfg, coupled_step_pipe, a, per);
     } else if (l.precision == kFP16) {
-        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__half>, a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__half, false>, a);
     } else if (l.precision == kBF16) {
-        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__nv_bfloat16>, a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__nv_bfloat16, false>, a);
     } else {
-        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<float>, a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<float, false>, a);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -608,25 +414,26 @@ cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out
 
 cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm)
 {
+    if (l.walls) return step_walls_occupancy(l, blocks_per_sm);
     if (l.variant == kVariantBulk) {
         const size_t smem = bulk_smem_bytes(l.stages, l.precision);
         if (l.precision == kFP16)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<__half>, l.block,
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<__half, false>, l.block,
                                                                  smem);
         if (l.precision == kBF16)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<__nv_bfloat16>,
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<__nv_bfloat16, false>,
                                                                  l.block, smem);
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<float>, l.block, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_bulk<float, false>, l.block, smem);
     }
     if (l.variant == kVariantPipe)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_pipe, l.block,
                                                              bulk_smem_bytes(l.stages));
     if (l.precision == kFP16)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__half>, l.block, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__half, false>, l.block, 0);
     if (l.precision == kBF16)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__nv_bfloat16>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__nv_bfloat16, false>,
                                                              l.block, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<float>, l.block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<float, false>, l.block, 0);
 }
 
 cudaError_t launch_init_rest(void* pop, int ny, int pitch, float rho0, float wg0, float wg1,

@@ -17,6 +17,7 @@ VELOCITY, PRESSURE = 0, 1
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_NUMERIC, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(7)
 LBM_FP32, LBM_FP16, LBM_BF16 = range(3)
 LBM_PORT_VELOCITY, LBM_PORT_PRESSURE, LBM_PORT_PRESSURE_RESCALE, LBM_PORT_INLET_RESCALE = range(4)
+LBM_WALL_BOUNCE_BACK, LBM_WALL_EQUILIBRIUM = range(2)
 PRECISIONS = {"fp32": LBM_FP32, "fp16": LBM_FP16, "bf16": LBM_BF16}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -50,7 +51,8 @@ class lbm_options(ctypes.Structure):
                 ("alloc_user", ctypes.c_void_p), ("block_threads", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("consumer_warps", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("decay", ctypes.c_double), ("graph_steps", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("decay", ctypes.c_double), ("wall_scheme", ctypes.c_int32),
+                ("graph_steps", ctypes.c_int32)]
 
 
 class lbm_info(ctypes.Structure):
@@ -213,7 +215,7 @@ class Chip:
     def __init__(self, solid, tau, tau_c, ports=(), edge_u=None, edge_C=None, w0=1.0 / 3.0,
                  rho0=1.0, C0=0.0, stream=None, torch_alloc=False, device=-1, block_threads=0,
                  max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0, precision="fp32",
-                 graph_steps=0, decay=0.0, _batch=None):
+                 graph_steps=0, decay=0.0, wall_scheme=0, _batch=None):
         self._lib = load()
         if _batch is None:
             solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
@@ -233,6 +235,7 @@ class Chip:
         opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opt.graph_steps = int(graph_steps)
         opt.decay = float(decay)
+        opt.wall_scheme = int(wall_scheme)
         self.stream = stream
         if stream is not None:
             opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
@@ -266,6 +269,7 @@ class Chip:
     @classmethod
     def from_problem(cls, prob, **kw):
         kw.setdefault("decay", prob.get("decay", 0.0))
+        kw.setdefault("wall_scheme", prob.get("wall_scheme", 0))
         return cls(prob["solid"], prob["tau"], prob["tau_c"], ports=prob["ports"],
                    edge_u=prob["edge_u"], edge_C=prob["edge_C"], w0=prob.get("w0", 1.0 / 3.0), **kw)
 

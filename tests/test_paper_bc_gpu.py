@@ -157,3 +157,90 @@ def test_scalar_only_step_with_the_paper_inlet():
     fl = ~ref.solid
     assert np.abs(chip.fields()[3] - ref.fields()[3])[fl].max() < 1e-5
     chip.close()
+
+
+@pytest.mark.parametrize("variant,precision", [(1, "fp32"), (2, "fp32"), (1, "bf16"), (2, "fp16")])
+@pytest.mark.parametrize("paper_ports", [False, True])
+def test_equilibrium_walls_match_oracle(variant, precision, paper_ports):
+    """The paper's equilibrium-interpolation walls (random obstacles, every
+    port kind), 10 steps from random fields: populations against the oracle
+    (FP32 bound, or the 16-bit bound n u / 4)."""
+    prob, init = W.random_case(7, 300, 20, paper_ports=paper_ports)
+    prob["wall_scheme"] = 1
+    chip = lbm.Chip.from_problem(prob, variant=variant, precision=precision)
+    ref = oracle.from_problem(prob)
+    chip.init_equilibrium(**init)
+    ref.init_equilibrium(**init)
+    chip.set_valve_schedule(1, prob["states"])
+    for t in range(10):
+        chip.step(1)
+        ref.step(prob["states"][t])
+    f, g = chip.populations()
+    fp, gp = ref.post_collision()
+    fl = ~ref.solid
+    u = {"fp32": 0.0, "fp16": 2.0 ** -11, "bf16": 2.0 ** -8}[precision]
+    tol = 10 * u / 4 + POP_ATOL
+    assert np.abs(f - np.moveaxis(fp, -1, 0))[:, fl].max() <= tol
+    assert np.abs(g - np.moveaxis(gp, -1, 0))[:, fl].max() <= tol
+    chip.close()
+
+
+def test_equilibrium_wall_chip_run_matches_oracle():
+    prob = W.two_channel_chip(256, 128, 16, 256, 64, 0.8, 0.55, 0.01, 500, 1000, paper_ports=True,
+                              name="paper-walls-256x128")
+    prob["wall_scheme"] = 1
+    chip = lbm.Chip.from_problem(prob)
+    chip.set_valve_schedule(prob["period"], prob["states"])
+    ref = oracle.from_problem(prob)
+    chip.step(1000)
+    ref.run(1000, lambda t: W.valve_word(prob, t))
+    rho, ux, uy, C = chip.fields()
+    r_rho, r_ux, r_uy, r_C = ref.fields()
+    fl = ~ref.solid
+    du = max(np.abs(ux - r_ux)[fl].max(), np.abs(uy - r_uy)[fl].max()) / prob["u_max"]
+    dC = np.abs(C - r_C)[fl].max()
+    dm = abs(rho[fl].astype(np.float64).sum() - r_rho[fl].sum()) / r_rho[fl].sum()
+    assert du <= 1e-4 and dC <= 1e-4 and dm <= 1e-6, (du, dC, dm)
+    with pytest.raises(lbm.LbmError) as e:
+        chip.adjoint(10, [128], [64], [0.0])
+    assert e.value.status == lbm.LBM_ERR_STATE
+    chip.close()
+
+
+def test_equilibrium_walls_with_graphs_and_batches():
+    """The wall values are written by two extra kernels per step: CUDA-graph
+    replay and a batch of two chips give the same bits as direct steps of
+    single chips."""
+    prob, init = W.random_case(3, 130, 16)
+    prob["wall_scheme"] = 1
+    prob["states"] = [7, 7, 3, 1]
+    a = lbm.Chip.from_problem(prob)
+    b = lbm.Chip.from_problem(prob, graph_steps=6)
+    for c in (a, b):
+        c.init_equilibrium(**init)
+        c.set_valve_schedule(20, prob["states"])
+        c.step(90)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    chips = W.config_batch(2, seed=3)
+    for p in chips:
+        p["wall_scheme"] = 1
+    batch = lbm.Chip.batch(chips, wall_scheme=1)
+    alone = [lbm.Chip.from_problem(p) for p in chips]
+    for c in alone:
+        c.set_valves(1)
+        c.step(60)
+    batch.set_valves(1)
+    batch.step(60)
+    f, g = batch.populations()
+    for k, c in enumerate(alone):
+        i = batch.instance(k)
+        fk = f[:, i["row0"]:i["row0"] + i["ny"], :i["nx"]]
+        fa = c.populations()[0]
+        fl = ~c.solid
+        assert np.array_equal(fa[:, fl], fk[:, fl])
+        c.close()
+    a.close()
+    b.close()
+    batch.close()
