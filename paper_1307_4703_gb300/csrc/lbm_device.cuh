@@ -81,6 +81,15 @@ __device__ __forceinline__ void grid_dependency_sync()
 // reference: the fluid planes the same f_i - w_i, the scalar planes
 // g_i - w_i C_ref; the codec adds the plane's offset on loading and
 // subtracts it on storing, so all arithmetic stays FP32.
+// x + off, skipped when off is zero: the fluid planes have no offset, and
+// x + 0.0f cannot be folded away (it turns -0 into +0), while this test
+// folds when off is a constant after inlining.
+__device__ __forceinline__ float add_offset(float x, float off) { return off != 0.f ? x + off : x; }
+__device__ __forceinline__ float4 add_offset(float4 v, float off)
+{
+    return off != 0.f ? make_float4(v.x + off, v.y + off, v.z + off, v.w + off) : v;
+}
+
 template <typename T>
 struct Codec;
 
@@ -101,9 +110,9 @@ struct Codec<__half> {
         const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
-        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+        return add_offset(make_float4(a.x, a.y, b.x, b.y), off);
     }
-    static __device__ __forceinline__ float ld1(const __half* p, float off) { return __half2float(__ldg(p)) + off; }
+    static __device__ __forceinline__ float ld1(const __half* p, float off) { return add_offset(__half2float(__ldg(p)), off); }
     static __device__ __forceinline__ void st4(__half* p, const float4& v, float off)
     {
         const __half2 a = __floats2half2_rn(v.x - off, v.y - off);
@@ -119,9 +128,9 @@ struct Codec<__half> {
         const uint2 r = *reinterpret_cast<const uint2*>(p);
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
-        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+        return add_offset(make_float4(a.x, a.y, b.x, b.y), off);
     }
-    static __device__ __forceinline__ float lds1(const __half* p, float off) { return __half2float(*p) + off; }
+    static __device__ __forceinline__ float lds1(const __half* p, float off) { return add_offset(__half2float(*p), off); }
 };
 
 template <>
@@ -131,11 +140,11 @@ struct Codec<__nv_bfloat16> {
         const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
         const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
-        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+        return add_offset(make_float4(a.x, a.y, b.x, b.y), off);
     }
     static __device__ __forceinline__ float ld1(const __nv_bfloat16* p, float off)
     {
-        return __bfloat162float(__ldg(p)) + off;
+        return add_offset(__bfloat162float(__ldg(p)), off);
     }
     static __device__ __forceinline__ void st4(__nv_bfloat16* p, const float4& v, float off)
     {
@@ -155,11 +164,11 @@ struct Codec<__nv_bfloat16> {
         const uint2 r = *reinterpret_cast<const uint2*>(p);
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
         const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
-        return make_float4(a.x + off, a.y + off, b.x + off, b.y + off);
+        return add_offset(make_float4(a.x, a.y, b.x, b.y), off);
     }
     static __device__ __forceinline__ float lds1(const __nv_bfloat16* p, float off)
     {
-        return __bfloat162float(*p) + off;
+        return add_offset(__bfloat162float(*p), off);
     }
 };
 
