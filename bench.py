@@ -459,7 +459,7 @@ def _profile_target(args, device):
         e1.record(stream)
         stream.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / max(args.steps, 1)
-        out = {"kernel": "scalar_frozen_step", "workload": prob["name"], "us_per_step": us,
+        out = {"kernel": "scalar_frozen_bulk", "workload": prob["name"], "us_per_step": us,
                "glups": W.fluid_count(prob) / us / 1e3}
     else:
         prob = W.config_adjoint_chip()

@@ -34,6 +34,8 @@ constexpr int kDefaultConsumers = 3;
 constexpr int kDefaultStagesPerConsumer = 1;
 constexpr int kDefaultStagesPerConsumer16 = 2;  // 16-bit stages are half as large
 constexpr int kDefaultPipeWarps = 4;
+constexpr int kScalarConsumers = 3;   // scalar-only step: computing warps per block
+constexpr int kScalarStagesPer = 3;   // and shared-memory stages per computing warp
 
 struct Alloc {
     void* ptr = nullptr;
@@ -1425,17 +1427,16 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
     a.inv_cs2g = h->inv_cs2g;
     a.decay = h->decay;
     a.partials = h->partials;
-    a.n_partials = h->diag_grid;
+    a.fluid_blocks = h->diag_grid;
     a.err = h->err;
     if (h->scalar_grid == 0) {
-        // one wave of resident blocks (at most the coupled step's grid, whose
-        // partials buffer the kernel writes)
+        // one wave of resident blocks of the bulk-copy kernel
         int per_sm = 0;
-        LBM_CUDA(h, lbm::scalar_step_occupancy(256, &per_sm));
-        const int need = (h->n_tiles + 7) / 8;
-        h->scalar_grid = std::max(1, std::min(need, std::max(1, per_sm) * h->sms));
+        LBM_CUDA(h, lbm::scalar_bulk_occupancy(kScalarConsumers, kScalarStagesPer, &per_sm));
+        h->scalar_grid = std::max(1, std::min(h->n_tiles, std::max(1, per_sm) * h->sms));
     }
-    const int scalar_grid = std::min(h->scalar_grid, h->diag_grid);  // its partials go to the last step's slots
+    const int scalar_grid = std::min(h->scalar_grid, h->partials_cap);
+    a.n_partials = std::max(h->diag_grid, scalar_grid);
     int g = h->gbuf;  // buffer holding the current scalar planes
     for (int64_t k = 0; k < n; ++k) {
         const uint32_t w = h->mask_at(h->step);
@@ -1449,7 +1450,7 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
         a.ux = u;
         a.uy = u + h->plane;
         a.open_mask = w;
-        cudaError_t e = lbm::launch_scalar_step(a, scalar_grid, 256, h->stream);
+        cudaError_t e = lbm::launch_scalar_step_bulk(a, scalar_grid, kScalarConsumers, kScalarStagesPer, h->stream);
         if (e != cudaSuccess) {
             h->gbuf = g;
             return cuda_fail(h, e, "scalar step launch");
@@ -1458,6 +1459,7 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
         ++h->step;
     }
     h->gbuf = g;  // joined with the fluid planes when a call needs both
+    if (n > 0) h->diag_grid = std::max(h->diag_grid, scalar_grid);
     return pending_numeric(h);
 }
 

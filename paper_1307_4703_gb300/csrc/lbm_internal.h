@@ -132,11 +132,15 @@ struct ScalarArgs {
     uint32_t open_mask;
     double* partials;       // writes slots 1 and 3 of each block's four
     int n_partials;         // entries of `partials` (>= grid); those beyond the grid get 0
+    int fluid_blocks;       // entries holding the last coupled step's fluid partials (slots 0, 2);
+                            // blocks at or beyond it zero their slots 0 and 2
     unsigned int* err;
 };
 
-cudaError_t launch_scalar_step(const ScalarArgs& a, int grid, int block, cudaStream_t s);
-cudaError_t scalar_step_occupancy(int block, int* blocks_per_sm);
+// The scalar-only step (bulk-copy pipeline): blocks of `consumers` computing
+// warps and a producer warp, `per` shared-memory stages per computing warp.
+cudaError_t launch_scalar_step_bulk(const ScalarArgs& a, int grid, int consumers, int per, cudaStream_t s);
+cudaError_t scalar_bulk_occupancy(int consumers, int per, int* blocks_per_sm);
 cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, long long plane, float* ux, float* uy,
                                      cudaStream_t s);
 

@@ -15,147 +15,232 @@
 namespace lbm {
 namespace {
 
-__global__ void __launch_bounds__(256) scalar_frozen_step(const ScalarArgs a)
+// Bounce-back, ports, relaxation and stores of one lane's quad.  v: the
+// streamed scalar populations; ux4, uy4: the stored field at the quad; sc,
+// sq: the lane's scalar and outlet-flux sums.
+__device__ __forceinline__ void scalar_quad(float4 (&v)[5], unsigned lk, int x0, const RowBC& bw, const RowBC& be,
+                                            float4 ux4, float4 uy4, const ScalarArgs& a, const float* S, long long P,
+                                            long long oC, KahanF& sc, KahanF& sq, bool& bad)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    const long long P = a.plane;
-    const float* __restrict__ S = a.src;  // scalar plane 0 of the source buffer
-    KahanF sc, sq;
-    bool bad = false;
-    grid_dependency_sync();
-    for (int t = blockIdx.x * wpb + warp; t < a.n_tiles; t += gridDim.x * wpb) {
-        const uint2 tile = a.tiles[t];
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
-        const long long oC = (long long)y * a.pitch + x0;
-        const long long oS = (long long)(y > 0 ? y - 1 : y) * a.pitch + x0;
-        const long long oN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + x0;
-        const int halo_w = x0 > 0 ? -1 : 0;
-        const int halo_e = x0 + 4 < a.pitch ? 4 : 3;
-        const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
-        const bool act = lk != 0xFFFFFFFFu;
-        const unsigned ball = __ballot_sync(kFull, act);
-        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;
-        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;
-        // ---- free flight of g (directions 0..4 use the shifts of planes 9..13) ----
-        float4 v[5];
+    // ---- no-flux walls: halfway bounce-back of g ----
+    unsigned wall = 0;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const int p = 9 + i;
-            const long long o = i * P + (src_row(p) == 0 ? oC : src_row(p) == 1 ? oS : oN);
-            const bool ld = src_col(p) == 0 ? act : src_col(p) == 1 ? ld_w : ld_e;
-            float4 r = ld ? ldg4(S + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (src_col(p) == 1) {
-                float h = 0.f;
-                if (act && lane == 0) h = __ldg(S + o + halo_w);
-                float w = __shfl_up_sync(kFull, r.w, 1);
-                if (lane == 0) w = h;
-                r = make_float4(w, r.x, r.y, r.z);
-            } else if (src_col(p) == 2) {
-                float h = 0.f;
-                if (act && lane == 31) h = __ldg(S + o + halo_e);
-                float e = __shfl_down_sync(kFull, r.x, 1);
-                if (lane == 31) e = h;
-                r = make_float4(r.y, r.z, r.w, e);
-            }
-            v[i] = r;
+    for (int k = 0; k < 4; ++k) {
+        const unsigned lb = (lk >> (8 * k)) & 0xFFu;
+        if (lb != kSolid) wall |= lb;
+    }
+#pragma unroll
+    for (int i = 1; i <= 4; ++i) {
+        if (wall & (1u << (i - 1))) {
+            const float4 own = ldg4(S + opp(i) * P + oC);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((lk >> (8 * k + i - 1)) & 1u) at(v[i], k) = at(own, k);
         }
-        if (!act) continue;
-        // ---- no-flux walls: halfway bounce-back of g ----
-        unsigned wall = 0;
+    }
+    const bool open_w = bw.x >= 0 && ((a.open_mask >> (bw.chan_kind & 31)) & 1u);
+    const bool open_e = be.x >= 0 && ((a.open_mask >> (be.chan_kind & 31)) & 1u);
+    float tc = 0.f, tq = 0.f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const unsigned lb = (lk >> (8 * k)) & 0xFFu;
-            if (lb != kSolid) wall |= lb;
-        }
+    for (int k = 0; k < 4; ++k) {
+        const bool fluid = ((lk >> (8 * k)) & 0xFFu) != kSolid;
+        float g[5];
 #pragma unroll
-        for (int i = 1; i <= 4; ++i) {
-            if (wall & (1u << (i - 1))) {
-                const float4 own = ldg4(S + opp(i) * P + oC);
+        for (int i = 0; i < 5; ++i) g[i] = fluid ? at(v[i], k) : 0.f;
+        const int xk = x0 + k;
+        const bool pw = open_w && bw.x == xk;
+        const bool pe = !pw && open_e && be.x == xk;
+        bool pressure_node = false;
+        const float ux = a.u_scale * at(ux4, k), uy = a.u_scale * at(uy4, k);
+        if (pw || pe) {
+            const RowBC b = pw ? bw : be;
+            const int gi = pw ? 1 : 3;
+            const int kind = (b.chan_kind >> 8) & 0xFF;
+            if (kind == 0) {  // held concentration
+                float others = 0.f;
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if ((lk >> (8 * k + i - 1)) & 1u) at(v[i], k) = at(own, k);
-            }
-        }
-        const float4 ux4 = ldg4(a.ux + oC), uy4 = ldg4(a.uy + oC);
-        const RowBC bw = a.rowbc[y];
-        const RowBC be = a.rowbc[a.ny + y];
-        const bool open_w = bw.x >= 0 && ((a.open_mask >> (bw.chan_kind & 31)) & 1u);
-        const bool open_e = be.x >= 0 && ((a.open_mask >> (be.chan_kind & 31)) & 1u);
-        float tc = 0.f, tq = 0.f;
+                for (int i = 0; i < 5; ++i)
+                    if (i != gi) others += g[i];
+                g[gi] = b.c - others;
+            } else {          // do-nothing
+                g[gi] = __ldg(S + gi * P + oC + k);
+                pressure_node = kind != 3;
+                if (kind == 3) {  // the paper's inlet: scaled to C_in
+                    const float Cs = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+                    if (Cs > 0.f) {
+                        const float gc = b.c / Cs;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const bool fluid = ((lk >> (8 * k)) & 0xFFu) != kSolid;
-            float g[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) g[i] = fluid ? at(v[i], k) : 0.f;
-            const int xk = x0 + k;
-            const bool pw = open_w && bw.x == xk;
-            const bool pe = !pw && open_e && be.x == xk;
-            bool pressure_node = false;
-            const float ux = a.u_scale * at(ux4, k), uy = a.u_scale * at(uy4, k);
-            if (pw || pe) {
-                const RowBC b = pw ? bw : be;
-                const int gi = pw ? 1 : 3;
-                const int kind = (b.chan_kind >> 8) & 0xFF;
-                if (kind == 0) {  // held concentration
-                    float others = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 5; ++i)
-                        if (i != gi) others += g[i];
-                    g[gi] = b.c - others;
-                } else {          // do-nothing
-                    g[gi] = __ldg(S + gi * P + oC + k);
-                    pressure_node = kind != 3;
-                    if (kind == 3) {  // the paper's inlet: scaled to C_in
-                        const float Cs = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
-                        if (Cs > 0.f) {
-                            const float gc = b.c / Cs;
-#pragma unroll
-                            for (int i = 0; i < 5; ++i) g[i] *= gc;
-                        } else {
-                            const float c1 = a.wg1 * b.c, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
-                            g[0] = b.c - 4.f * c1;
-                            g[1] = c1 + cx;
-                            g[3] = c1 - cx;
-                            g[2] = c1 + cy;
-                            g[4] = c1 - cy;
-                        }
+                        for (int i = 0; i < 5; ++i) g[i] *= gc;
+                    } else {
+                        const float c1 = a.wg1 * b.c, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
+                        g[0] = b.c - 4.f * c1;
+                        g[1] = c1 + cx;
+                        g[3] = c1 - cx;
+                        g[2] = c1 + cy;
+                        g[4] = c1 - cy;
                     }
                 }
             }
-            const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
-            const float wg = a.omega_g;
-            const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
-            g[0] += wg * ((C - 4.f * c1) - g[0]);
-            g[1] += wg * ((c1 + cx) - g[1]);
-            g[3] += wg * ((c1 - cx) - g[3]);
-            g[2] += wg * ((c1 + cy) - g[2]);
-            g[4] += wg * ((c1 - cy) - g[4]);
-            if (a.decay != 0.f) {  // reaction term R = -k C of Eq. cde, as w_i R
-                const float R = -a.decay * C;
-                g[0] += a.wg0 * R;
+        }
+        const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+        const float wg = a.omega_g;
+        const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
+        g[0] += wg * ((C - 4.f * c1) - g[0]);
+        g[1] += wg * ((c1 + cx) - g[1]);
+        g[3] += wg * ((c1 - cx) - g[3]);
+        g[2] += wg * ((c1 + cy) - g[2]);
+        g[4] += wg * ((c1 - cy) - g[4]);
+        if (a.decay != 0.f) {  // reaction term R = -k C of Eq. cde, as w_i R
+            const float R = -a.decay * C;
+            g[0] += a.wg0 * R;
 #pragma unroll
-                for (int i = 1; i < 5; ++i) g[i] += a.wg1 * R;
+            for (int i = 1; i < 5; ++i) g[i] += a.wg1 * R;
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) at(v[i], k) = g[i];
+        if (fluid) {
+            bad |= !(fabsf(C) < INFINITY);
+            tc += C;
+            if (pressure_node) tq += C * ux;
+        }
+    }
+    sc.add(tc);
+    if (tq != 0.f) sq.add(tq);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) stg4(a.dst + i * P + oC, v[i]);
+}
+
+// The kernel: a producer warp streams each tile's 5 scalar plane rows
+// (with the halos of the shifted directions), its 2 stored velocity rows,
+// its wall-link bytes and port entries into a ring of shared-memory stages
+// with cp.async.bulk copies completing on mbarriers; consumer warps compute
+// from shared memory.  The same stage ring as the coupled step's
+// coupled_step_bulk (each consumer owns its stages; bounded waits set bit 1
+// of the error word).
+struct __align__(16) ScalarStage {
+    float pl[5][kRowFloats];
+    float u[2][kTileNodes];
+    unsigned links[kTileNodes / 4];
+    RowBC bc[2];
+    uint2 tile;
+    uint2 pad;
+};
+static_assert(sizeof(ScalarStage) % 16 == 0 && offsetof(ScalarStage, u) % 16 == 0 &&
+                  offsetof(ScalarStage, links) % 16 == 0 && offsetof(ScalarStage, bc) % 16 == 0,
+              "bulk-copy targets");
+
+__global__ void __launch_bounds__(kBulkMaxThreads, 2) scalar_frozen_bulk(const ScalarArgs a, int per)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nc = (blockDim.x >> 5) - 1;  // consumer warps; the last warp produces
+    const int n_stages = nc * per;
+    ScalarStage* st = reinterpret_cast<ScalarStage*>(smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(n_stages) * sizeof(ScalarStage));
+    uint64_t* empty = full + n_stages;
+    const long long P = a.plane;
+    const float* __restrict__ S = a.src;
+    const int G = int(gridDim.x);
+    const int n_items = int(blockIdx.x) < a.n_tiles ? (a.n_tiles - 1 - int(blockIdx.x)) / G + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < n_stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    grid_dependency_sync();
+
+    KahanF sc, sq;
+    bool bad = false;
+    if (warp == nc) {
+        // producer: lane l owns stage (l % nc) * per + l / nc (see coupled_step_bulk)
+        const bool mine = lane < n_stages;
+        const int s = (lane % nc) * per + lane / nc;
+        int last_use = -1;
+        for (int batch = 0, base = 0; base < n_items; ++batch, base += n_stages) {
+            const int j = base + lane;
+            bool good = true;
+            if (mine && j < n_items) {
+                const uint2 tile = a.tiles[blockIdx.x + size_t(j) * G];
+                if (batch > 0 && !mbar_wait(&empty[s], uint32_t(batch - 1) & 1u)) {
+                    good = false;
+                } else {
+                    const int y = int(tile.x >> kSegBits);
+                    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
+                    const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
+                    const int us = x0 + 4 * q0, ue = x0 + 4 * q1 + 4;
+                    const int ss = us - 4 > 0 ? us - 4 : 0;
+                    const int se = ue + 4 < a.pitch ? ue + 4 : a.pitch;
+                    const long long rC = (long long)y * a.pitch;
+                    const long long rS = (long long)(y > 0 ? y - 1 : y) * a.pitch;
+                    const long long rN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch;
+                    // directions 0, 2, 4 copy the lanes' span, 1 and 3 one quad more on
+                    // each side; the two velocity rows the lanes' span
+                    const uint32_t bytes = uint32_t(5 * (ue - us) + 2 * (se - ss)) * 4u + kTileNodes + 2 * sizeof(RowBC);
+                    st[s].tile = tile;
+                    mbar_arrive_expect_tx(&full[s], bytes);
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const int p = 9 + i;
+                        const long long r = src_row(p) == 0 ? rC : src_row(p) == 1 ? rS : rN;
+                        const int b = src_col(p) == 0 ? us : ss;
+                        const int e = src_col(p) == 0 ? ue : se;
+                        bulk_g2s(&st[s].pl[i][b - x0 + 4], S + i * P + r + b, uint32_t(e - b) * 4u, &full[s]);
+                    }
+                    bulk_g2s(&st[s].u[0][us - x0], a.ux + rC + us, uint32_t(ue - us) * 4u, &full[s]);
+                    bulk_g2s(&st[s].u[1][us - x0], a.uy + rC + us, uint32_t(ue - us) * 4u, &full[s]);
+                    bulk_g2s(st[s].links, a.links + rC + x0, kTileNodes, &full[s]);
+                    bulk_g2s(&st[s].bc[0], a.rowbc + y, sizeof(RowBC), &full[s]);
+                    bulk_g2s(&st[s].bc[1], a.rowbc + a.ny + y, sizeof(RowBC), &full[s]);
+                    last_use = batch;
+                }
             }
-#pragma unroll
-            for (int i = 0; i < 5; ++i) at(v[i], k) = g[i];
-            if (fluid) {
-                bad |= !(fabsf(C) < INFINITY);
-                tc += C;
-                if (pressure_node) tq += C * ux;
+            if (!__all_sync(kFull, good)) {
+                if (lane == 0) atomicOr(a.err, 2u);
+                break;
             }
         }
-        sc.add(tc);
-        if (tq != 0.f) sq.add(tq);
+        if (mine && last_use >= 0 && !mbar_wait(&full[s], uint32_t(last_use) & 1u)) atomicOr(a.err, 2u);
+        __syncwarp();
+    } else {
+        for (int k = 0, j = warp; j < n_items; ++k, j += nc) {
+            const int s = warp * per + k % per;
+            const uint32_t use = uint32_t(k / per);
+            if (!__all_sync(kFull, mbar_wait(&full[s], use & 1u))) {
+                if (lane == 0) atomicOr(a.err, 2u);
+                break;
+            }
+            const ScalarStage& sg = st[s];
+            const uint2 tile = sg.tile;
+            const int y = int(tile.x >> kSegBits);
+            const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+            const long long oC = (long long)y * a.pitch + x0;
+            const unsigned lk = sg.links[lane];
+            const bool act = lk != 0xFFFFFFFFu;
+            const RowBC bw = sg.bc[0], be = sg.bc[1];
+            float4 v[5], ux4 = make_float4(0.f, 0.f, 0.f, 0.f), uy4 = ux4;
+            if (act) {
 #pragma unroll
-        for (int i = 0; i < 5; ++i) stg4(a.dst + i * P + oC, v[i]);
+                for (int i = 0; i < 5; ++i) {
+                    const float* row = sg.pl[i] + 4 * lane;
+                    const float4 c = *reinterpret_cast<const float4*>(row + 4);
+                    if (src_col(9 + i) == 0) v[i] = c;
+                    else if (src_col(9 + i) == 1) v[i] = make_float4(row[3], c.x, c.y, c.z);
+                    else v[i] = make_float4(c.y, c.z, c.w, row[8]);
+                }
+                ux4 = *reinterpret_cast<const float4*>(&sg.u[0][4 * lane]);
+                uy4 = *reinterpret_cast<const float4*>(&sg.u[1][4 * lane]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be refilled
+            if (act) scalar_quad(v, lk, x0, bw, be, ux4, uy4, a, S, P, oC, sc, sq, bad);
+        }
+        if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
     }
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
-    // block partials of the scalar diagnostics (slots 1 and 3); the fluid's
-    // slots 0 and 2 keep the values of the last coupled step
     __shared__ double red[32][2];
     double s1 = warp_sum(sc.value()), s3 = warp_sum(sq.value());
     if (lane == 0) {
@@ -164,12 +249,13 @@ __global__ void __launch_bounds__(256) scalar_frozen_step(const ScalarArgs a)
     }
     __syncthreads();
     if (threadIdx.x < 2) {
-        double s = 0.0;
-        for (int w = 0; w < wpb; ++w) s += red[w][threadIdx.x];
-        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = s;
-        // entries of the coupled step's larger grid hold no scalar partial now
+        double sum = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
+        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = sum;
         for (int b = blockIdx.x + gridDim.x; b < a.n_partials; b += gridDim.x)
             a.partials[b * 4 + 1 + 2 * threadIdx.x] = 0.0;
+        // blocks beyond the last coupled step's grid hold no fluid partial
+        if (int(blockIdx.x) >= a.fluid_blocks) a.partials[blockIdx.x * 4 + 2 * threadIdx.x] = 0.0;
     }
 }
 
@@ -196,26 +282,39 @@ __global__ void velocity_of_state(const float* pop, const uint8_t* links, long l
 
 }  // namespace
 
-cudaError_t launch_scalar_step(const ScalarArgs& a, int grid, int block, cudaStream_t s)
+size_t scalar_bulk_smem_bytes(int stages)
 {
-    // a programmatic dependent of the previous kernel (see grid_dependency_sync)
+    return size_t(stages) * (sizeof(ScalarStage) + 2 * sizeof(uint64_t));
+}
+
+cudaError_t launch_scalar_step_bulk(const ScalarArgs& a, int grid, int consumers, int per, cudaStream_t s)
+{
+    static_assert(kBulkMaxThreads >= 32 * 8, "block of up to 7 consumers and a producer");
+    cudaError_t e = cudaFuncSetAttribute(scalar_frozen_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(scalar_bulk_smem_bytes(kMaxStages)));
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
+    cfg.blockDim = dim3(32 * (consumers + 1));
+    cfg.dynamicSmemBytes = scalar_bulk_smem_bytes(consumers * per);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, scalar_frozen_step, a);
+    e = cudaLaunchKernelEx(&cfg, scalar_frozen_bulk, a, per);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-cudaError_t scalar_step_occupancy(int block, int* blocks_per_sm)
+cudaError_t scalar_bulk_occupancy(int consumers, int per, int* blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, scalar_frozen_step, block, 0);
+    cudaError_t e = cudaFuncSetAttribute(scalar_frozen_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(scalar_bulk_smem_bytes(kMaxStages)));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, scalar_frozen_bulk, 32 * (consumers + 1),
+                                                         scalar_bulk_smem_bytes(consumers * per));
 }
 
 cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, long long plane, float* ux, float* uy,
