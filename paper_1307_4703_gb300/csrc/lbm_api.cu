@@ -34,6 +34,7 @@ constexpr int kDefaultConsumers = 3;
 constexpr int kDefaultStagesPerConsumer = 1;
 constexpr int kDefaultStagesPerConsumer16 = 2;  // 16-bit stages are half as large
 constexpr int kDefaultPipeWarps = 4;
+constexpr int kDefaultRegsBlock = 128;
 constexpr int kScalarConsumers = 3;   // scalar-only step: computing warps per block
 constexpr int kScalarStagesPer = 3;   // and shared-memory stages per computing warp
 
@@ -263,6 +264,7 @@ lbm_status step_graph(lbm_ctx* h, lbm::StepArgs a, cudaGraphExec_t* out)
     for (int j = 0; j < h->graph_steps && e == cudaSuccess; ++j) {
         a.src = h->pop[(h->cur + j) & 1];
         a.dst = h->pop[(h->cur + j + 1) & 1];
+        a.reverse = (h->cur + j) & 1;
         e = launch_full_step(h, a, h->launch, h->cap_stream);
     }
     cudaGraph_t graph = nullptr;
@@ -564,7 +566,10 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
     h->sms = sms;
     lbm::StepLaunch& L = h->launch;
-    L.variant = opt.variant == 1 ? lbm::kVariantRegs : opt.variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
+    // default: the register variant for FP32 storage, the bulk-copy pipeline
+    // for 16-bit storage (the faster of the two on each, see profiles)
+    const int variant = opt.variant ? opt.variant : opt.precision == LBM_FP32 ? 1 : 2;
+    L.variant = variant == 1 ? lbm::kVariantRegs : variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
     L.precision = opt.precision;
     L.pdl = true;  // consecutive steps overlap launch and set-up with the previous step's tail
     L.walls = opt.wall_scheme == LBM_WALL_EQUILIBRIUM;
@@ -584,7 +589,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         if (e != cudaSuccess) return bail(cuda_fail(h, e, "shared-memory attribute"));
     } else {
         L.stages = 0;
-        L.block = opt.block_threads ? opt.block_threads : 256;
+        L.block = opt.block_threads ? opt.block_threads : kDefaultRegsBlock;
     }
     e = lbm::step_kernel_occupancy(L, &per_sm);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
@@ -872,6 +877,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
         }
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
+        a.reverse = h->cur;  // alternate the tile order from step to step
         cudaError_t e = launch_full_step(h, a, h->launch, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
@@ -1250,6 +1256,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         for (int64_t t = 0; t < n; ++t) {
             a.src = t == 0 ? h->pop[h->cur] : reinterpret_cast<float*>(ckpt + size_t(t) * S);
             a.dst = t + 1 < n ? reinterpret_cast<float*>(ckpt + size_t(t + 1) * S) : h->pop[1 - h->cur];
+            a.reverse = int(t & 1);
             a.open_mask[0] = h->mask_at(t0 + t);
             cudaError_t e = lbm::launch_step(a, h->launch, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
@@ -1264,6 +1271,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
                 LBM_CUDA(h, cudaMemcpyAsync(ckpt + size_t(t / K) * S, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
             a.src = h->pop[h->cur];
             a.dst = h->pop[1 - h->cur];
+            a.reverse = h->cur;
             a.open_mask[0] = h->mask_at(t0 + t);
             cudaError_t e = lbm::launch_step(a, h->launch, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
@@ -1323,6 +1331,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         for (int j = 1; j < len; ++j) {
             r.src = state(j - 1);
             r.dst = state(j);
+            r.reverse = j & 1;
             r.open_mask[0] = h->mask_at(t0 + s0 + j - 1);
             cudaError_t e = lbm::launch_step(r, h->launch, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "recompute step launch");
@@ -1447,6 +1456,7 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
         }
         a.src = h->pop[g] + 9 * h->plane;
         a.dst = h->pop[1 - g] + 9 * h->plane;
+        a.reverse = g;
         a.ux = u;
         a.uy = u + h->plane;
         a.open_mask = w;

@@ -76,6 +76,14 @@ __device__ __forceinline__ void grid_dependency_sync()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Entry t of the tile table, counted from its end when `reverse` is set.
+// Consecutive steps alternate the direction, so a step starts on the rows
+// the previous step wrote last, which are still in L2.
+__device__ __forceinline__ uint2 tile_at(const uint2* tiles, int n, int t, int reverse)
+{
+    return tiles[reverse ? n - 1 - t : t];
+}
+
 // Storage of the populations.  FP32 keeps them as they are (fluid planes as
 // f_i - w_i, scalar planes as g_i).  FP16 and BF16 hold deviations from a
 // reference: the fluid planes the same f_i - w_i, the scalar planes

@@ -65,6 +65,7 @@ struct StepArgs {
     const RowBC* rowbc;
     const uint2* tiles;
     int n_tiles;
+    int reverse;            // 1: take the tiles from the end of the table (see tile_at)
     int ny;
     int pitch;
     long long plane;        // ny * pitch
@@ -121,6 +122,7 @@ struct ScalarArgs {
     const RowBC* rowbc;
     const uint2* tiles;
     int n_tiles;
+    int reverse;            // 1: take the tiles from the end of the table (see tile_at)
     int ny;
     int pitch;
     long long plane;

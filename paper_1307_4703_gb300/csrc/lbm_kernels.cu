@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
     bool bad = false;
     int issued = 0;  // items whose copies were started
     for (; issued < n_items && issued < per; ++issued)
-        issue_tile(a, a.tiles[gw + size_t(issued) * W], st[issued], &full[issued], lane);
-    uint2 pending = issued < n_items ? a.tiles[gw + size_t(issued) * W] : make_uint2(0u, 0u);
+        issue_tile(a, tile_at(a.tiles, a.n_tiles, gw + issued * W, a.reverse), st[issued], &full[issued], lane);
+    uint2 pending = issued < n_items ? tile_at(a.tiles, a.n_tiles, gw + issued * W, a.reverse) : make_uint2(0u, 0u);
 
     int k = 0;
     for (; k < n_items; ++k) {
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
         if (issued < n_items) {
             issue_tile(a, pending, st[s], &full[s], lane);
             ++issued;
-            if (issued < n_items) pending = a.tiles[gw + size_t(issued) * W];
+            if (issued < n_items) pending = tile_at(a.tiles, a.n_tiles, gw + issued * W, a.reverse);
         }
         if (act) {
             bounce_back<float, false>(v, lk, S, P, oC);

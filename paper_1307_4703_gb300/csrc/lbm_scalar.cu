@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) scalar_frozen_bulk(const S
             const int j = base + lane;
             bool good = true;
             if (mine && j < n_items) {
-                const uint2 tile = a.tiles[blockIdx.x + size_t(j) * G];
+                const uint2 tile = tile_at(a.tiles, a.n_tiles, int(blockIdx.x) + j * G, a.reverse);
                 if (batch > 0 && !mbar_wait(&empty[s], uint32_t(batch - 1) & 1u)) {
                     good = false;
                 } else {

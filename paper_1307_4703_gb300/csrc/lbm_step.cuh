@@ -15,7 +15,7 @@ namespace {
 // Variant 1: registers and warp shuffles
 // ---------------------------------------------------------------------------
 template <typename T, bool kWalls>
-__global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
+__global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -29,11 +29,11 @@ __global__ void __launch_bounds__(256) coupled_step_regs(const StepArgs a)
 
     const int stride = gridDim.x * wpb;
     int t = blockIdx.x * wpb + warp;
-    uint2 next = t < a.n_tiles ? a.tiles[t] : make_uint2(0u, 0u);
+    uint2 next = t < a.n_tiles ? tile_at(a.tiles, a.n_tiles, t, a.reverse) : make_uint2(0u, 0u);
     grid_dependency_sync();
     for (; t < a.n_tiles; t += stride) {
         const uint2 tile = next;  // the following entry is fetched one tile ahead
-        if (t + stride < a.n_tiles) next = a.tiles[t + stride];
+        if (t + stride < a.n_tiles) next = tile_at(a.tiles, a.n_tiles, t + stride, a.reverse);
         const int y = int(tile.x >> kSegBits);
         const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
             const int j = base + lane;
             bool good = true;
             if (mine && j < n_items) {
-                const uint2 tile = a.tiles[blockIdx.x + size_t(j) * G];
+                const uint2 tile = tile_at(a.tiles, a.n_tiles, int(blockIdx.x) + j * G, a.reverse);
                 if (batch > 0 && !mbar_wait(&empty[s], uint32_t(batch - 1) & 1u)) {
                     good = false;
                 } else {
