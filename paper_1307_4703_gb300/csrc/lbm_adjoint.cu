@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(256) adjoint_stream(const AdjointArgs A)
     const float* __restrict__ S = A.adj_mid;
     grid_dependency_sync();
     for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
-        const uint2 tile = A.tiles[t];
+        // the reverse of adjoint_collide's order: start where it ended (in L2)
+        const uint2 tile = tile_at(A.tiles, A.n_tiles, t, 1);
         const int y = int(tile.x >> kSegBits);
         const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
         const long long oC = (long long)y * A.pitch + x0;
