@@ -233,6 +233,15 @@ lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy,
  * LBM_ERR_NUMERIC / LBM_ERR_TIMEOUT if the error word is set. */
 lbm_status lbm_get_diagnostics(lbm_handle h, double out[4]);
 
+/* The same diagnostics, read without waiting: enqueues the reduction and a
+ * copy of the 4 doubles into `out` on the handle's stream and returns.  out
+ * (host memory, page-locked for the copy to be asynchronous) is valid after
+ * the stream is synchronised (lbm_synchronize, or any synchronising call).
+ * A set error word is reported by the next lbm_get_diagnostics or
+ * lbm_synchronize.  For a driver loop that reads every step's result while
+ * the GPU keeps stepping. */
+lbm_status lbm_get_diagnostics_async(lbm_handle h, double* out);
+
 /* Current post-collision populations into HOST arrays: f = 9*nx*ny floats,
  * g = 5*nx*ny floats, layout [i][y][x].  Either may be NULL.  Synchronises. */
 lbm_status lbm_get_populations(lbm_handle h, float* f, float* g);

@@ -889,12 +889,14 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     return pending_numeric(h);
 }
 
+static lbm_status read_err_word(lbm_handle h);
+
 lbm_status lbm_synchronize(lbm_handle h)
 {
     if (check_ctx(h)) return LBM_ERR_ARG;
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     LBM_CUDA(h, cudaGetLastError());
-    return LBM_OK;
+    return read_err_word(h);
 }
 
 static lbm_status read_err_word(lbm_handle h)
@@ -955,6 +957,15 @@ lbm_status lbm_get_diagnostics(lbm_handle h, double out[4])
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics reduction launch");
     LBM_CUDA(h, cudaMemcpyAsync(out, h->diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return read_err_word(h);
+}
+
+lbm_status lbm_get_diagnostics_async(lbm_handle h, double* out)
+{
+    if (check_ctx(h) || !out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    cudaError_t e = lbm::launch_diag_finish(h->partials, h->diag_grid, h->diag, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics reduction launch");
+    LBM_CUDA(h, cudaMemcpyAsync(out, h->diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return pending_numeric(h);
 }
 
 }  // extern "C"

@@ -119,6 +119,7 @@ SIGNATURES = {
     "lbm_get_fields_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_get_diagnostics": (ctypes.c_int, [ctypes.c_void_p, _f64p]),
+    "lbm_get_diagnostics_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_get_populations": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p]),
     "lbm_set_populations": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p]),
     "lbm_init_equilibrium": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p, _f32p, _f32p]),
@@ -439,6 +440,12 @@ class Chip:
         """Keep the fastest launch shape of the step kernel (lbm_autotune)."""
         self._check(self._lib.lbm_autotune(self._h, int(trial_steps)))
         return self.info()
+
+    def diagnostics_async(self, out_ptr):
+        """Enqueue the diagnostics read into host memory at out_ptr (4
+        doubles, page-locked, e.g. a pinned torch tensor's data_ptr());
+        valid after synchronize()."""
+        self._check(self._lib.lbm_get_diagnostics_async(self._h, ctypes.c_void_p(int(out_ptr))))
 
     def info(self):
         i = lbm_info()

@@ -295,3 +295,34 @@ def test_degenerate_single_row_channel_and_odd_widths():
         du, dC, dm = _field_errors(prob, chip, ref)
         assert du <= U_TOL and dC <= C_TOL and dm <= MASS_TOL, (nx, ny, du, dC, dm)
         chip.close()
+
+
+def test_async_diagnostics_match_the_synchronous_read():
+    """lbm_get_diagnostics_async queues each step's diagnostics into pinned
+    host memory without waiting; after one synchronisation every row equals
+    what the synchronous read gives step by step; a set error word is
+    reported by lbm_synchronize."""
+    prob = W.config_small()
+    a = lbm.Chip.from_problem(prob)
+    b = lbm.Chip.from_problem(prob)
+    for c in (a, b):
+        c.set_valve_schedule(3, prob["states"])
+    ring = torch.zeros((6, 4), dtype=torch.float64, pin_memory=True)
+    want = []
+    for k in range(6):
+        a.step(1)
+        a.diagnostics_async(ring[k].data_ptr())
+        b.step(1)
+        want.append(b.diagnostics())
+    a.synchronize()
+    assert np.array_equal(ring.numpy(), np.array(want))
+    f, g = a.populations()
+    f[0, 5, 40] = np.nan
+    a.set_populations(f, g)
+    a.step(1)
+    a.diagnostics_async(ring[0].data_ptr())
+    with pytest.raises(lbm.LbmError) as ei:
+        a.synchronize()
+    assert ei.value.status == lbm.LBM_ERR_NUMERIC
+    a.close()
+    b.close()
