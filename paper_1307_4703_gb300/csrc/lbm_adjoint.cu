@@ -4,26 +4,46 @@
 // K(B(F(P(t)))): F the free flight with bounce-back, B the completion of open
 // port nodes, K the collision of f and of g (whose equilibrium reads the
 // velocity of the same node, Eq. cdeequilibrium).  Given A(t+1) = dJ/dP(t+1)
-// the adjoint step forms A(t) = F^T B^T K'^T A(t+1) in two launches:
-//   adjoint_collide  per node: recomputes X = B(F(P(t))) exactly as the step
-//                    kernel does, applies K'(X)^T to A(t+1) and the transpose
-//                    of the port completion, and stores the result A*;
-//   adjoint_stream   per node: the transposed free flight, which is a pull
+// the adjoint step is A(t) = F^T M(t) with M(t) = B^T K'^T A(t+1).  The
+// reverse sweep carries M instead of A, so that each reverse step is one
+// launch that reads its neighbours' M(t+1) once:
+//   adjoint_collide  the first reverse step (t = n - 1): A(n) comes from the
+//                    objective; recomputes X = B(F(P(t))) exactly as the step
+//                    kernel does, applies K'(X)^T and B^T, stores M(t);
+//   adjoint_fused    every other step: A(t+1) = F^T M(t+1) per node, a pull
 //                    from x + e_i (bounce-back links return the node's own
-//                    opposite entry), plus the do-nothing outlet term.
-// Derivatives with respect to the parameters accumulate in FP64: d/d(1/tau_g)
-// per block, d/du_in and d/dC_in per port row.
+//                    opposite entry) plus the do-nothing outlet term, kept
+//                    in shared memory, then the same work as adjoint_collide.
+// A(0) itself is not formed: the parameter derivatives are complete once
+// M(0) is.  They accumulate in FP64: d/d(1/tau_g) per block, d/du_in and
+// d/dC_in per port row.
 #include "lbm_device.cuh"
 
 namespace lbm {
 namespace {
 
+// A(t+1) of a lane's four nodes in global memory (the first reverse step).
+struct NextGlobal {
+    const float* p;  // entry (plane 0, node x0)
+    long long P;
+    __device__ __forceinline__ float operator()(int i, int k) const { return __ldg(p + i * P + k); }
+};
+
+// A(t+1) of a thread's four nodes in shared memory, entry (i, k) at
+// s[(4 i + k) * stride] (stride = threads per block: conflict-free).
+struct NextShared {
+    float* s;
+    int stride;
+    __device__ __forceinline__ float& operator()(int i, int k) const { return s[(4 * i + k) * stride]; }
+};
+
 // Transpose of the collision and of the port completion for the four nodes
 // of one lane.  x holds X (fluid planes as deviations); A(t+1) is read and
-// A* written one node at a time (fewer live registers than whole quads).
+// M(t) written one node at a time (fewer live registers than whole quads).
+template <typename Next>
 __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes], unsigned lk, int x0, int y,
                                                      long long oC, const RowBC& bw, const RowBC& be,
-                                                     const AdjointArgs& A, KahanF& dwg)
+                                                     const AdjointArgs& A, const Next& next, KahanF& dwg)
 {
     const long long P = A.plane;
     const bool open_w = bw.x >= 0 && ((A.open_mask >> (bw.chan_kind & 31)) & 1u);
@@ -43,12 +63,12 @@ __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes],
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             f[i] = at(x[i], k);
-            af[i] = __ldg(A.adj_next + i * P + o);
+            af[i] = next(i, k);
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             g[i] = at(x[9 + i], k);
-            ag[i] = __ldg(A.adj_next + (9 + i) * P + o);
+            ag[i] = next(9 + i, k);
         }
         const int xk = x0 + k;
         const bool pw = open_w && bw.x == xk;
@@ -172,134 +192,169 @@ __device__ __forceinline__ void block_add(double* slot, double v)
     }
 }
 
-__global__ void __launch_bounds__(256) adjoint_collide(const AdjointArgs A)
+// Where a lane's four nodes sit and which neighbouring quads hold fluid
+// (every lane of the warp calls this: it votes).
+struct QuadPos {
+    int y, x0, halo_w, halo_e;
+    long long oC, oS, oN;
+    unsigned lk;
+    bool act, ld_w, ld_e;
+};
+
+__device__ __forceinline__ QuadPos quad_pos(const AdjointArgs& A, uint2 tile, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    const long long P = A.plane;
-    const float* __restrict__ S = A.state;
-    KahanF dwg;
-    grid_dependency_sync();
-    for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
-        const uint2 tile = A.tiles[t];
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
-        const long long oC = (long long)y * A.pitch + x0;
-        const long long oS = (long long)(y > 0 ? y - 1 : y) * A.pitch + x0;
-        const long long oN = (long long)(y + 1 < A.ny ? y + 1 : y) * A.pitch + x0;
-        const int halo_w = x0 > 0 ? -1 : 0;
-        const int halo_e = x0 + 4 < A.pitch ? 4 : 3;
-        const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(A.links + oC));
-        const bool act = lk != 0xFFFFFFFFu;
-        const unsigned ball = __ballot_sync(kFull, act);
-        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;
-        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;
-        float4 x[kPlanes];
-        pull_quad<false>(x, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
-        if (!act) continue;
-        bounce_back(x, lk, S, P, oC);
-        const RowBC bw = A.rowbc[y];
-        const RowBC be = A.rowbc[A.ny + y];
-        // the forward's port completion, so that x is exactly X
-        {
-            const bool open_w = bw.x >= 0 && ((A.open_mask >> (bw.chan_kind & 31)) & 1u);
-            const bool open_e = be.x >= 0 && ((A.open_mask >> (be.chan_kind & 31)) & 1u);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const bool pw = open_w && bw.x == x0 + k;
-                const bool pe = !pw && open_e && be.x == x0 + k;
-                if ((pw || pe) && ((lk >> (8 * k)) & 0xFFu) != kSolid) {
-                    float f[9], g[5];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) f[i] = at(x[i], k);
-#pragma unroll
-                    for (int i = 0; i < 5; ++i) g[i] = at(x[9 + i], k);
-                    complete_port(f, g, pw, pw ? bw : be, S, P, oC + k);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) at(x[i], k) = f[i];
-#pragma unroll
-                    for (int i = 0; i < 5; ++i) at(x[9 + i], k) = g[i];
-                }
-            }
-        }
-        collide_adjoint_quad(x, lk, x0, y, oC, bw, be, A, dwg);
-    }
-    block_add(A.grad_w, dwg.value());
+    QuadPos q;
+    q.y = int(tile.x >> kSegBits);
+    q.x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+    q.oC = (long long)q.y * A.pitch + q.x0;
+    q.oS = (long long)(q.y > 0 ? q.y - 1 : q.y) * A.pitch + q.x0;
+    q.oN = (long long)(q.y + 1 < A.ny ? q.y + 1 : q.y) * A.pitch + q.x0;
+    q.halo_w = q.x0 > 0 ? -1 : 0;
+    q.halo_e = q.x0 + 4 < A.pitch ? 4 : 3;
+    q.lk = __ldg(reinterpret_cast<const unsigned*>(A.links + q.oC));
+    q.act = q.lk != 0xFFFFFFFFu;
+    const unsigned ball = __ballot_sync(kFull, q.act);
+    q.ld_w = ((ball | (ball >> 1)) >> lane) & 1u;
+    q.ld_e = ((ball | (ball << 1)) >> lane) & 1u;
+    return q;
 }
 
-// Transposed free flight: A(t)_i(y) = A*_i(y + e_i) when y + e_i is fluid,
-// else A*_opp(i)(y) (the bounce-back link), plus, at an open pressure-port
-// node, the do-nothing term of the scalar population with e_x = s.
-__global__ void __launch_bounds__(256) adjoint_stream(const AdjointArgs A)
+// X = B(F(P(t))) for an active lane: bounce-back, then the forward's port
+// completion, so that x is exactly the pre-collision state of the step.
+__device__ __forceinline__ void complete_quad(float4 (&x)[kPlanes], const QuadPos& q, const RowBC& bw,
+                                              const RowBC& be, const AdjointArgs& A)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
     const long long P = A.plane;
-    const float* __restrict__ S = A.adj_mid;
-    grid_dependency_sync();
-    for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
-        // the reverse of adjoint_collide's order: start where it ended (in L2)
-        const uint2 tile = tile_at(A.tiles, A.n_tiles, t, 1);
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
-        const long long oC = (long long)y * A.pitch + x0;
-        const long long oS = (long long)(y > 0 ? y - 1 : y) * A.pitch + x0;
-        const long long oN = (long long)(y + 1 < A.ny ? y + 1 : y) * A.pitch + x0;
-        const int halo_w = x0 > 0 ? -1 : 0;
-        const int halo_e = x0 + 4 < A.pitch ? 4 : 3;
-        const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(A.links + oC));
-        const bool act = lk != 0xFFFFFFFFu;
-        const unsigned ball = __ballot_sync(kFull, act);
-        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;
-        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;
-        float4 v[kPlanes];
-        pull_quad<true>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
-        if (!act) continue;
-        // bounce-back links: the link of direction i from y is a wall when
-        // the pull source of direction opp(i) at y is not fluid
-        unsigned wall = 0;
+    bounce_back(x, q.lk, A.state, P, q.oC);
+    const bool open_w = bw.x >= 0 && ((A.open_mask >> (bw.chan_kind & 31)) & 1u);
+    const bool open_e = be.x >= 0 && ((A.open_mask >> (be.chan_kind & 31)) & 1u);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const unsigned lb = (lk >> (8 * k)) & 0xFFu;
-            if (lb != kSolid) wall |= lb;
+    for (int k = 0; k < 4; ++k) {
+        const bool pw = open_w && bw.x == q.x0 + k;
+        const bool pe = !pw && open_e && be.x == q.x0 + k;
+        if ((pw || pe) && ((q.lk >> (8 * k)) & 0xFFu) != kSolid) {
+            float f[9], g[5];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = at(x[i], k);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) g[i] = at(x[9 + i], k);
+            complete_port(f, g, pw, pw ? bw : be, A.state, P, q.oC + k);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) at(x[i], k) = f[i];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) at(x[9 + i], k) = g[i];
         }
-        if (wall) {
+    }
+}
+
+// A(t+1) = F^T M(t+1) for an active lane, v holding M(t+1) pulled from
+// x + e_i: a bounce-back link of direction i (the pull source of opp(i) is
+// not fluid) returns the node's own opposite entry; at an open pressure-port
+// node the scalar population with e_x = s gets the do-nothing term of step
+// t+1; solid nodes are zero.
+__device__ __forceinline__ void transposed_flight(float4 (&v)[kPlanes], const QuadPos& q, const RowBC& bw,
+                                                  const RowBC& be, const AdjointArgs& A)
+{
+    const long long P = A.plane;
+    const float* __restrict__ M = A.mid_next;
+    unsigned wall = 0;
 #pragma unroll
-            for (int i = 1; i <= 8; ++i) {
-                const int o = opp(i);
-                if (wall & (1u << (o - 1))) {
-                    const float4 own = ldg4(S + o * P + oC);
-                    const float4 ownc = i <= 4 ? ldg4(S + (9 + o) * P + oC) : own;
+    for (int k = 0; k < 4; ++k) {
+        const unsigned lb = (q.lk >> (8 * k)) & 0xFFu;
+        if (lb != kSolid) wall |= lb;
+    }
+    if (wall) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if ((lk >> (8 * k + o - 1)) & 1u) {
-                            at(v[i], k) = at(own, k);
-                            if (i <= 4) at(v[9 + i], k) = at(ownc, k);
-                        }
+        for (int i = 1; i <= 8; ++i) {
+            const int o = opp(i);
+            if (wall & (1u << (o - 1))) {
+                const float4 own = ldg4(M + o * P + q.oC);
+                const float4 ownc = i <= 4 ? ldg4(M + (9 + o) * P + q.oC) : own;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if ((q.lk >> (8 * k + o - 1)) & 1u) {
+                        at(v[i], k) = at(own, k);
+                        if (i <= 4) at(v[9 + i], k) = at(ownc, k);
                     }
                 }
             }
         }
-        const RowBC bw = A.rowbc[y];
-        const RowBC be = A.rowbc[A.ny + y];
-        const bool dn_w = bw.x >= 0 && ((A.open_mask >> (bw.chan_kind & 31)) & 1u) && (bw.chan_kind >> 8) == 1;
-        const bool dn_e = be.x >= 0 && ((A.open_mask >> (be.chan_kind & 31)) & 1u) && (be.chan_kind >> 8) == 1;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const unsigned lb = (lk >> (8 * k)) & 0xFFu;
-            if (lb == kSolid) {
-#pragma unroll
-                for (int p = 0; p < kPlanes; ++p) at(v[p], k) = 0.f;
-                continue;
-            }
-            if (dn_w && bw.x == x0 + k) at(v[10], k) += A.dn[y];
-            else if (dn_e && be.x == x0 + k) at(v[12], k) += A.dn[A.ny + y];
-        }
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) stg4(A.adj_out + p * P + oC, v[p]);
     }
+    const uint32_t m = A.open_mask_next;
+    const bool dn_w = bw.x >= 0 && ((m >> (bw.chan_kind & 31)) & 1u) && (bw.chan_kind >> 8) == 1;
+    const bool dn_e = be.x >= 0 && ((m >> (be.chan_kind & 31)) & 1u) && (be.chan_kind >> 8) == 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned lb = (q.lk >> (8 * k)) & 0xFFu;
+        if (lb == kSolid) {
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) at(v[p], k) = 0.f;
+            continue;
+        }
+        if (dn_w && bw.x == q.x0 + k) at(v[10], k) += A.dn[q.y];
+        else if (dn_e && be.x == q.x0 + k) at(v[12], k) += A.dn[A.ny + q.y];
+    }
+}
+
+// The first reverse step: A(t+1) = A(n) is read from global memory.
+__global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_collide(const AdjointArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const long long P = A.plane;
+    KahanF dwg;
+    grid_dependency_sync();
+    for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
+        const QuadPos q = quad_pos(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane);
+        float4 x[kPlanes];
+        pull_quad<false>(x, A.state, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
+        if (!q.act) continue;
+        const RowBC bw = A.rowbc[q.y];
+        const RowBC be = A.rowbc[A.ny + q.y];
+        complete_quad(x, q, bw, be, A);
+        collide_adjoint_quad(x, q.lk, q.x0, q.y, q.oC, bw, be, A, NextGlobal{A.adj_next + q.oC, P}, dwg);
+    }
+    block_add(A.grad_w, dwg.value());
+}
+
+// Every later reverse step: A(t+1) = F^T M(t+1) gathered into shared memory
+// (each thread reads back only its own entries, so no barrier), then X,
+// K'^T and B^T as in adjoint_collide.  dn carries the do-nothing terms from
+// one step to the next: the node that reads the entry of step t+1 is the
+// node that then writes the one of step t.
+__global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_fused(const AdjointArgs A)
+{
+    extern __shared__ float next_smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const long long P = A.plane;
+    const NextShared next{next_smem + threadIdx.x, int(blockDim.x)};
+    KahanF dwg;
+    grid_dependency_sync();
+    for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
+        const QuadPos q = quad_pos(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane);
+        const RowBC bw = A.rowbc[q.y];
+        const RowBC be = A.rowbc[A.ny + q.y];
+        {
+            float4 v[kPlanes];
+            pull_quad<true>(v, A.mid_next, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
+            if (q.act) {
+                transposed_flight(v, q, bw, be, A);
+#pragma unroll
+                for (int p = 0; p < kPlanes; ++p)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) next(p, k) = at(v[p], k);
+            }
+        }
+        float4 x[kPlanes];
+        pull_quad<false>(x, A.state, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
+        if (!q.act) continue;
+        complete_quad(x, q, bw, be, A);
+        collide_adjoint_quad(x, q.lk, q.x0, q.y, q.oC, bw, be, A, next, dwg);
+    }
+    block_add(A.grad_w, dwg.value());
 }
 
 // J = sum w (C - target)^2 at the final state, and its derivative with
@@ -348,30 +403,32 @@ __global__ void sum_doubles(const double* v, int n, double* out)
 
 }  // namespace
 
-cudaError_t adjoint_occupancy(int block, int* blocks_per_sm)
+cudaError_t adjoint_occupancy(int* blocks_per_sm)
 {
+    const size_t smem = adjoint_fused_smem(kAdjointBlock);
+    cudaError_t e = cudaFuncSetAttribute(adjoint_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int a = 0, b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, adjoint_collide, block, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adjoint_stream, block, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, adjoint_collide, kAdjointBlock, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adjoint_fused, kAdjointBlock, smem);
     *blocks_per_sm = a < b ? a : b;
     return e;
 }
 
-cudaError_t launch_adjoint_step(const AdjointArgs& a, int grid, int block, cudaStream_t s)
+cudaError_t launch_adjoint_step(const AdjointArgs& a, bool first, int grid, cudaStream_t s)
 {
-    // both as programmatic dependents of the kernel before them (each waits
-    // for it in grid_dependency_sync before touching any buffer)
+    // a programmatic dependent of the kernel before it (waits for it in
+    // grid_dependency_sync before touching any buffer)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
+    cfg.blockDim = dim3(kAdjointBlock);
+    cfg.dynamicSmemBytes = first ? 0 : adjoint_fused_smem(kAdjointBlock);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, adjoint_collide, a);
-    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, adjoint_stream, a);
+    cudaError_t e = first ? cudaLaunchKernelEx(&cfg, adjoint_collide, a) : cudaLaunchKernelEx(&cfg, adjoint_fused, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -1219,8 +1219,8 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
 
     int sms = 0, per_sm = 0;
     LBM_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    const int ablock = 256;
-    LBM_CUDA(h, lbm::adjoint_occupancy(ablock, &per_sm));
+    const int ablock = lbm::kAdjointBlock;
+    LBM_CUDA(h, lbm::adjoint_occupancy(&per_sm));
     const int agrid = std::max(1, std::min((h->n_tiles + ablock / 32 - 1) / (ablock / 32), std::max(1, per_sm) * sms));
 
     Scratch tmp(h);
@@ -1299,8 +1299,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     LBM_CUDA(h, cudaMemcpyAsync(oy, hy.data(), hy.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     LBM_CUDA(h, cudaMemcpyAsync(ot, obj->target, size_t(obj->n) * sizeof(float), cudaMemcpyHostToDevice, st));
     LBM_CUDA(h, cudaMemcpyAsync(ow, obj->weight, size_t(obj->n) * sizeof(float), cudaMemcpyHostToDevice, st));
-    LBM_CUDA(h, cudaMemsetAsync(adj[0], 0, S, st));
-    LBM_CUDA(h, cudaMemsetAsync(adj[2], 0, S, st));
+    for (float* b : adj) LBM_CUDA(h, cudaMemsetAsync(b, 0, S, st));
     LBM_CUDA(h, cudaMemsetAsync(gw, 0, size_t(agrid) * sizeof(double), st));
     LBM_CUDA(h, cudaMemsetAsync(gu, 0, size_t(2) * h->ny * sizeof(double), st));
     LBM_CUDA(h, cudaMemsetAsync(gc, 0, size_t(2) * h->ny * sizeof(double), st));
@@ -1329,10 +1328,10 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     A.grad_w = gw;
     A.grad_u = gu;
     A.grad_c = gc;
-    A.adj_mid = adj[2];
     lbm::StepArgs r = a;
     r.partials = rp;  // keep the diagnostics of the last forward step
-    int cur = 0;      // adj[cur] holds A(t+1)
+    // adj[0] holds A(n); M(t) alternates between adj[1] and adj[2]
+    int mid = 0;  // 0 before the first reverse step, else adj[mid] holds M(t+1)
     for (long long sg = n_ck - 1; sg >= 0; --sg) {
         const int64_t s0 = sg * K;
         const int len = int(std::min<int64_t>(K, n - s0));
@@ -1348,13 +1347,17 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
             if (e != cudaSuccess) return cuda_fail(h, e, "recompute step launch");
         }
         for (int j = len - 1; j >= 0; --j) {
+            const int64_t t = s0 + j;
             A.state = state(j);
-            A.adj_next = adj[cur];
-            A.adj_out = adj[1 - cur];
-            A.open_mask = h->mask_at(t0 + s0 + j);
-            cudaError_t e = lbm::launch_adjoint_step(A, agrid, ablock, st);
+            A.adj_next = adj[0];
+            A.mid_next = mid ? adj[mid] : nullptr;
+            A.adj_mid = adj[mid == 1 ? 2 : 1];
+            A.open_mask = h->mask_at(t0 + t);
+            A.open_mask_next = h->mask_at(t0 + t + 1);
+            A.reverse = int((n - 1 - t) & 1);
+            cudaError_t e = lbm::launch_adjoint_step(A, mid == 0, agrid, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
-            cur = 1 - cur;
+            mid = mid == 1 ? 2 : 1;
         }
     }
     {

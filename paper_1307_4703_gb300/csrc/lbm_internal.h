@@ -89,9 +89,9 @@ struct StepArgs {
 // One adjoint step (lbm_adjoint.cu): A(t) from A(t+1) and the state P(t).
 struct AdjointArgs {
     const float* state;     // P(t), post-collision populations (fluid planes as deviations)
-    const float* adj_next;  // A(t+1) = dJ/dP(t+1), same layout
-    float* adj_mid;         // scratch: adjoint of the completed pre-collision values
-    float* adj_out;         // A(t)
+    const float* adj_next;  // A(t+1) = dJ/dP(t+1), same layout (first reverse step only)
+    const float* mid_next;  // M(t+1), the adjoint of the completed pre-collision values of step t+1
+    float* adj_mid;         // M(t), written
     const uint8_t* links;
     const RowBC* rowbc;
     const uint2* tiles;
@@ -100,15 +100,24 @@ struct AdjointArgs {
     int pitch;
     long long plane;
     float omega_f, omega_g, wg0, wg1, inv_cs2g;
-    uint32_t open_mask;     // valve word of step t
-    float* dn;              // 2*ny: do-nothing terms passed from the first launch to the second
-    double* grad_w;         // one running sum of dJ/d(1/tau_g) per block of adjoint_collide
+    uint32_t open_mask;       // valve word of step t
+    uint32_t open_mask_next;  // valve word of step t+1
+    int reverse;              // take the tile table from its end (alternates from launch to launch)
+    float* dn;              // 2*ny: do-nothing terms passed from step t+1 to step t
+    double* grad_w;         // one running sum of dJ/d(1/tau_g) per block
     double* grad_u;         // 2*ny running sums of dJ/du_in
     double* grad_c;         // 2*ny running sums of dJ/dC_in
 };
 
-cudaError_t adjoint_occupancy(int block, int* blocks_per_sm);
-cudaError_t launch_adjoint_step(const AdjointArgs& a, int grid, int block, cudaStream_t s);
+// Threads per block of the reverse-step kernels; the fused one keeps A(t+1)
+// of its threads' nodes in shared memory (14 planes x 4 nodes x 4 B each).
+constexpr int kAdjointBlock = 128;
+inline size_t adjoint_fused_smem(int block) { return size_t(kPlanes) * 4 * sizeof(float) * size_t(block); }
+
+cudaError_t adjoint_occupancy(int* blocks_per_sm);
+// first: the first reverse step (A(n) from adj_next); else the fused step
+// (A(t+1) gathered from mid_next)
+cudaError_t launch_adjoint_step(const AdjointArgs& a, bool first, int grid, cudaStream_t s);
 cudaError_t launch_adjoint_seed(const float* state, long long plane, int pitch, const int* ox, const int* oy,
                                 const float* target, const float* weight, int n, float* adj, double* J,
                                 cudaStream_t s);
