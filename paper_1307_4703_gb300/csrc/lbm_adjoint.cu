@@ -81,49 +81,57 @@ __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes],
             Kd = f[0] + f[2] + f[4] + 2.f * (fo_ax + fo_dn + fo_up);
         }
         // ---- K'^T: the collision's Jacobian at X, transposed ----
+        // f_eq_q = w_q rho [1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u^2] with u = j / rho:
+        //   d f_eq_q / d rho  = w_q (1 - 9/2 (e.u)^2 + 3/2 u^2)
+        //   d f_eq_q / d j    = w_q (e (3 + 9 e.u) - 3 u)
+        // and d rho / d f_i = 1, d j / d f_i = e_i.  The sums over q are
+        // written out per direction pair (e.u of q and of opp(q) differ in sign).
         const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const float rho = 1.f + rd;
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        const float ux = jx / rho, uy = jy / rho;
-        const float uu = ux * ux + uy * uy;
+        const float irho = 1.f / rho;
+        const float ux = jx * irho, uy = jy * irho;
+        const float uu15 = 1.5f * (ux * ux + uy * uy);
         const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
-        // f_eq_k = w_k [rho + 3 e.j + 9/2 (e.j)^2 / rho - 3/2 j^2 / rho]
-        float Ar = 0.f, Ax = 0.f, Ay = 0.f;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float ex = float(q == 1 || q == 5 || q == 8) - float(q == 3 || q == 6 || q == 7);
-            const float ey = float(q == 2 || q == 5 || q == 6) - float(q == 4 || q == 7 || q == 8);
-            const float wq = q == 0 ? kWr : q <= 4 ? kWa : kWd;
-            const float eu = ex * ux + ey * uy;
-            Ar += af[q] * wq * (1.f - 4.5f * eu * eu + 1.5f * uu);
-            Ax += af[q] * wq * (3.f * ex + 9.f * eu * ex - 3.f * ux);
-            Ay += af[q] * wq * (3.f * ey + 9.f * eu * ey - 3.f * uy);
-        }
-        // g_eq_k = w_k C [1 + e.j / (rho c_s^2)]; the rest entry is C - 4 w_1 C
-        float Bc = ag[0] * (1.f - 4.f * A.wg1), Br = 0.f, Bx = 0.f, By = 0.f;
-        float dw = ag[0] * ((C - 4.f * A.wg1 * C) - g[0]);
-        {
-            const float c1 = A.wg1 * C;
-            const float e4[4][2] = {{1.f, 0.f}, {0.f, 1.f}, {-1.f, 0.f}, {0.f, -1.f}};
-#pragma unroll
-            for (int q = 1; q <= 4; ++q) {
-                const float ex = e4[q - 1][0], ey = e4[q - 1][1];
-                const float eu = ex * ux + ey * uy;
-                Bc += ag[q] * A.wg1 * (1.f + eu * A.inv_cs2g);
-                Br += ag[q] * c1 * (-eu * A.inv_cs2g / rho);
-                Bx += ag[q] * c1 * ex * A.inv_cs2g / rho;
-                By += ag[q] * c1 * ey * A.inv_cs2g / rho;
-                dw += ag[q] * (c1 * (1.f + eu * A.inv_cs2g) - g[q]);
-            }
-        }
+        const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;  // e.u of q = 1, 2, 5, 6
+        const float b0 = kWr * af[0];
+        const float b1 = kWa * af[1], b2 = kWa * af[2], b3 = kWa * af[3], b4 = kWa * af[4];
+        const float b5 = kWd * af[5], b6 = kWd * af[6], b7 = kWd * af[7], b8 = kWd * af[8];
+        const float s13 = b1 + b3, s24 = b2 + b4, s57 = b5 + b7, s68 = b6 + b8;
+        const float sb = b0 + (s13 + s24) + (s57 + s68);
+        const float Ar = b0 * (1.f + uu15) + s13 * (1.f + uu15 - 4.5f * e1 * e1) + s24 * (1.f + uu15 - 4.5f * e2 * e2) +
+                         s57 * (1.f + uu15 - 4.5f * e5 * e5) + s68 * (1.f + uu15 - 4.5f * e6 * e6);
+        const float Ax = -3.f * ux * sb + 3.f * ((b1 - b3) + (b5 - b7) + (b8 - b6)) +
+                         9.f * (e1 * s13 + e5 * s57 - e6 * s68);
+        const float Ay = -3.f * uy * sb + 3.f * ((b2 - b4) + (b5 - b7) + (b6 - b8)) +
+                         9.f * (e2 * s24 + e5 * s57 + e6 * s68);
+        // g_eq_q = w_1 C (1 + e.u / c_s^2) for q = 1..4, the rest entry C - 4 w_1 C:
+        //   d/dC = w_1 (1 + e.u / c_s^2) (1 - 4 w_1 at rest), d/d rho = -w_1 C e.u / (c_s^2 rho),
+        //   d/dj = w_1 C e / (c_s^2 rho)
+        const float c1 = A.wg1 * C;
+        const float d13 = ag[1] - ag[3], d24 = ag[2] - ag[4];
+        const float seu = ux * d13 + uy * d24;  // sum_q ag_q e.u
+        const float sag = (ag[1] + ag[2]) + (ag[3] + ag[4]);
+        const float Bc = ag[0] * (1.f - 4.f * A.wg1) + A.wg1 * (sag + A.inv_cs2g * seu);
+        const float cr = c1 * A.inv_cs2g * irho;
+        const float Br = -cr * seu, Bx = cr * d13, By = cr * d24;
+        const float dw = ag[0] * ((C - 4.f * c1) - g[0]) + c1 * (sag + A.inv_cs2g * seu) -
+                         ((ag[1] * g[1] + ag[2] * g[2]) + (ag[3] * g[3] + ag[4] * g[4]));
         dwg.add(dw);
         float nf[9], ng[5];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float ex = float(q == 1 || q == 5 || q == 8) - float(q == 3 || q == 6 || q == 7);
-            const float ey = float(q == 2 || q == 5 || q == 6) - float(q == 4 || q == 7 || q == 8);
-            nf[q] = (1.f - w) * af[q] + w * (Ar + Ax * ex + Ay * ey) + wgr * (Br + Bx * ex + By * ey);
+        {
+            const float R = w * Ar + wgr * Br, X = w * Ax + wgr * Bx, Y = w * Ay + wgr * By;
+            const float w1 = 1.f - w;
+            nf[0] = w1 * af[0] + R;
+            nf[1] = w1 * af[1] + (R + X);
+            nf[3] = w1 * af[3] + (R - X);
+            nf[2] = w1 * af[2] + (R + Y);
+            nf[4] = w1 * af[4] + (R - Y);
+            nf[5] = w1 * af[5] + (R + (X + Y));
+            nf[7] = w1 * af[7] + (R - (X + Y));
+            nf[6] = w1 * af[6] + (R + (Y - X));
+            nf[8] = w1 * af[8] + (R - (Y - X));
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) ng[q] = (1.f - wgr) * ag[q] + wgr * Bc;
