@@ -474,10 +474,18 @@ def _profile_target(args, device):
         ox = np.full_like(oy, (cx0 + cx1) // 2)
         chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=device)
         chip.set_valve_schedule(prob["period"], prob["states"])
+        chip.step(max(args.warmup, 1))
+        chip.synchronize()
+        t0 = time.perf_counter()
+        chip.step(args.steps)
+        chip.synchronize()
+        tf = time.perf_counter() - t0
         t0 = time.perf_counter()
         chip.adjoint(args.steps, ox, oy, (oy - cy0) / max(1, cy1 - 1 - cy0), ckpt_every=1)
+        ta = time.perf_counter() - t0
         out = {"kernel": "adjoint", "workload": prob["name"], "steps": args.steps,
-               "seconds": time.perf_counter() - t0}
+               "forward_us_per_step": tf / args.steps * 1e6, "adjoint_call_seconds": ta,
+               "reverse_us_per_step": (ta - tf) / args.steps * 1e6}
     chip.close()
     print(json.dumps(out), flush=True)
 
