@@ -237,6 +237,9 @@ lbm_status lbm_get_diagnostics(lbm_handle h, double out[4]);
  * copy of the 4 doubles into `out` on the handle's stream and returns.  out
  * (host memory, page-locked for the copy to be asynchronous) is valid after
  * the stream is synchronised (lbm_synchronize, or any synchronising call).
+ * Page-locked memory that the device can address (cudaHostAlloc /
+ * cudaMallocHost with unified addressing) is written by the reduction
+ * kernel itself, without a copy in the stream.
  * A set error word is reported by the next lbm_get_diagnostics or
  * lbm_synchronize.  For a driver loop that reads every step's result while
  * the GPU keeps stepping. */

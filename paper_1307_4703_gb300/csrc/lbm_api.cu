@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lbm.h"
@@ -492,30 +493,59 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     // wall-link table; every fluid node needs a fluid neighbour
     const int pitch = (nx + lbm::kTileNodes - 1) / lbm::kTileNodes * lbm::kTileNodes;
     const int segs = pitch / lbm::kTileNodes;
+    // link masks and the tile table, rows split over host threads on large
+    // lattices (each thread owns whole rows; its tiles are appended in row
+    // order and the first bad node in row order is reported)
     std::vector<uint8_t> links(size_t(pitch) * ny, lbm::kSolid);
-    std::vector<uint2> tiles;
-    for (int y = 0; y < ny; ++y) {
-        for (int x = 0; x < nx; ++x) {
-            if (!is_fluid(mask, nx, ny, x, y)) continue;
-            uint8_t lb = 0;
-            for (int i = 1; i <= 8; ++i)
-                if (!is_fluid(mask, nx, ny, x - kEx[i], y - kEy[i])) lb |= uint8_t(1u << (i - 1));
-            if (lb == lbm::kSolid)
-                return fail(nullptr, LBM_ERR_ARG, "fluid node (%d, %d) has no fluid neighbour", x, y);
-            links[size_t(y) * pitch + x] = lb;
-        }
-        for (int s = 0; s < segs; ++s) {
-            int q0 = -1, q1 = -1;  // first and last quad of the segment holding fluid
-            for (int x = s * lbm::kTileNodes; x < std::min(nx, (s + 1) * lbm::kTileNodes); ++x)
-                if (mask[size_t(y) * nx + x] == 0) {
-                    const int q = (x - s * lbm::kTileNodes) / 4;
-                    if (q0 < 0) q0 = q;
-                    q1 = q;
+    struct RowsOut {
+        std::vector<uint2> tiles;
+        int bad_x = -1, bad_y = -1;
+    };
+    auto build_rows = [&](int y0, int y1, RowsOut& out) {
+        for (int y = y0; y < y1; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                if (!is_fluid(mask, nx, ny, x, y)) continue;
+                uint8_t lb = 0;
+                for (int i = 1; i <= 8; ++i)
+                    if (!is_fluid(mask, nx, ny, x - kEx[i], y - kEy[i])) lb |= uint8_t(1u << (i - 1));
+                if (lb == lbm::kSolid) {
+                    out.bad_x = x;
+                    out.bad_y = y;
+                    return;
                 }
-            if (q0 >= 0)
-                tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s),
-                                           uint32_t(q0) | (uint32_t(q1) << 8)));
+                links[size_t(y) * pitch + x] = lb;
+            }
+            for (int s = 0; s < segs; ++s) {
+                int q0 = -1, q1 = -1;  // first and last quad of the segment holding fluid
+                for (int x = s * lbm::kTileNodes; x < std::min(nx, (s + 1) * lbm::kTileNodes); ++x)
+                    if (mask[size_t(y) * nx + x] == 0) {
+                        const int q = (x - s * lbm::kTileNodes) / 4;
+                        if (q0 < 0) q0 = q;
+                        q1 = q;
+                    }
+                if (q0 >= 0)
+                    out.tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s),
+                                                   uint32_t(q0) | (uint32_t(q1) << 8)));
+            }
         }
+    };
+    const int n_thr = (long long)nx * ny < (1 << 20)
+                          ? 1
+                          : std::max(1, std::min({16, ny, int(std::thread::hardware_concurrency())}));
+    std::vector<RowsOut> parts(n_thr);
+    {
+        std::vector<std::thread> pool;
+        for (int k = 1; k < n_thr; ++k)
+            pool.emplace_back(build_rows, int((long long)ny * k / n_thr), int((long long)ny * (k + 1) / n_thr),
+                              std::ref(parts[k]));
+        build_rows(0, int((long long)ny / n_thr), parts[0]);
+        for (auto& t : pool) t.join();
+    }
+    std::vector<uint2> tiles;
+    for (const RowsOut& r : parts) {
+        if (r.bad_y >= 0)
+            return fail(nullptr, LBM_ERR_ARG, "fluid node (%d, %d) has no fluid neighbour", r.bad_x, r.bad_y);
+        tiles.insert(tiles.end(), r.tiles.begin(), r.tiles.end());
     }
 
     // ---- device set-up ----
@@ -962,9 +992,18 @@ lbm_status lbm_get_diagnostics(lbm_handle h, double out[4])
 lbm_status lbm_get_diagnostics_async(lbm_handle h, double* out)
 {
     if (check_ctx(h) || !out) return fail(h, LBM_ERR_ARG, "out is NULL");
-    cudaError_t e = lbm::launch_diag_finish(h->partials, h->diag_grid, h->diag, h->stream);
+    // page-locked host memory mapped into the device's address space takes
+    // the totals straight from the reduction kernel (no copy in the stream)
+    cudaPointerAttributes pa{};
+    double* direct = nullptr;
+    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess) {
+        if (pa.type == cudaMemoryTypeHost && pa.devicePointer) direct = static_cast<double*>(pa.devicePointer);
+    } else {
+        cudaGetLastError();
+    }
+    cudaError_t e = lbm::launch_diag_finish(h->partials, h->diag_grid, direct ? direct : h->diag, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics reduction launch");
-    LBM_CUDA(h, cudaMemcpyAsync(out, h->diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (!direct) LBM_CUDA(h, cudaMemcpyAsync(out, h->diag, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return pending_numeric(h);
 }
 

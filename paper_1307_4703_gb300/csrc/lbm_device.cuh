@@ -87,8 +87,10 @@ __device__ __forceinline__ uint2 tile_at(const uint2* tiles, int n, int t, int r
 // Storage of the populations.  FP32 keeps them as they are (fluid planes as
 // f_i - w_i, scalar planes as g_i).  FP16 and BF16 hold deviations from a
 // reference: the fluid planes the same f_i - w_i, the scalar planes
-// g_i - w_i C_ref; the codec adds the plane's offset on loading and
-// subtracts it on storing, so all arithmetic stays FP32.
+// g_i - w_i C_ref.  All arithmetic is FP32.  The step kernels move the
+// stored deviations as they are (their collision is written for deviations);
+// the codec's offset argument, added on loading and subtracted on storing,
+// serves the kernels and the port rules that need g_i itself.
 // x + off, skipped when off is zero: the fluid planes have no offset, and
 // x + 0.0f cannot be folded away (it turns -0 into +0), while this test
 // folds when off is a constant after inlining.
@@ -301,7 +303,7 @@ struct LaneDiag {
 // bounce-back).
 template <typename T, bool kWalls = false>
 __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, const T* S, long long P,
-                                            long long oC, float gref1 = 0.f, const T* Wb = nullptr)
+                                            long long oC, const T* Wb = nullptr)
 {
     unsigned wall = 0;  // union of the wall links of the fluid nodes
 #pragma unroll
@@ -316,7 +318,7 @@ __device__ __forceinline__ void bounce_back(float4 (&v)[kPlanes], unsigned lk, c
             const T* src = S + opp(i) * P;  // the node's own opposite population
             if constexpr (kWalls) src = Wb + (i - 1) * P;
             const float4 own = Codec<T>::ld4(src + oC, 0.f);
-            const float4 ownc = i <= 4 ? Codec<T>::ld4(S + (9 + opp(i)) * P + oC, gref1) : own;
+            const float4 ownc = i <= 4 ? Codec<T>::ld4(S + (9 + opp(i)) * P + oC, 0.f) : own;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if ((lk >> (8 * k + i - 1)) & 1u) {
@@ -522,8 +524,7 @@ __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool
 template <bool kReverse, typename T>
 __device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const T* __restrict__ S, long long P,
                                           long long oC, long long oS, long long oN, int halo_w, int halo_e,
-                                          bool act, bool ld_w, bool ld_e, int lane, float gref0 = 0.f,
-                                          float gref1 = 0.f)
+                                          bool act, bool ld_w, bool ld_e, int lane)
 {
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
@@ -531,17 +532,16 @@ __device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const T* __restr
         const int sc = kReverse ? (src_col(p) == 0 ? 0 : 3 - src_col(p)) : src_col(p);
         const long long o = p * P + (sr == 0 ? oC : sr == 1 ? oS : oN);
         const bool ld = sc == 0 ? act : sc == 1 ? ld_w : ld_e;
-        const float off = plane_offset(p, gref0, gref1);
-        float4 r = ld ? Codec<T>::ld4(S + o, off) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 r = ld ? Codec<T>::ld4(S + o, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (sc == 1) {  // from column x - 1
             float h = 0.f;
-            if (act && lane == 0) h = Codec<T>::ld1(S + o + halo_w, off);
+            if (act && lane == 0) h = Codec<T>::ld1(S + o + halo_w, 0.f);
             float w = __shfl_up_sync(kFull, r.w, 1);
             if (lane == 0) w = h;
             r = make_float4(w, r.x, r.y, r.z);
         } else if (sc == 2) {  // from column x + 1
             float h = 0.f;
-            if (act && lane == 31) h = Codec<T>::ld1(S + o + halo_e, off);
+            if (act && lane == 31) h = Codec<T>::ld1(S + o + halo_e, 0.f);
             float e = __shfl_down_sync(kFull, r.x, 1);
             if (lane == 31) e = h;
             r = make_float4(r.y, r.z, r.w, e);
@@ -583,6 +583,11 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     const bool open_w = bw.x >= 0 && valve_open(a, bw.chan_kind);
     const bool open_e = be.x >= 0 && valve_open(a, be.chan_kind);
     const float dfac = a.decay != 0.f ? 1.f - a.decay / omega.y : 1.f;
+    // With 16-bit storage the scalar populations stay in their stored form
+    // g_i - w_i C_ref here (C_ref = kCRef), as the fluid ones stay f_i - w_i:
+    // the collision below is written for deviations, so no offset is added
+    // on loading or subtracted on storing.  FP32 storage holds g_i itself.
+    constexpr bool kDev = !std::is_same<T, float>::value;
 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -596,8 +601,9 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         if (!fluid) {  // solid node: park it at the rest state rho = 1, C = 0
 #pragma unroll
             for (int i = 0; i < 9; ++i) f[i] = 0.f;
+            g[0] = kDev ? -a.gref0 : 0.f;
 #pragma unroll
-            for (int i = 0; i < 5; ++i) g[i] = 0.f;
+            for (int i = 1; i < 5; ++i) g[i] = kDev ? -a.gref1 : 0.f;
         }
 
         // ---- open valve ports (Zou-He; held concentration / do-nothing) ----
@@ -605,7 +611,19 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         const bool pw = open_w && bw.x == xk;
         const bool pe = !pw && open_e && be.x == xk;
         bool pressure_node = false;
-        if (pw || pe) pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k, a.gref1, a.wg1, a.inv_cs2g);
+        if (pw || pe) {  // the port rules work on g_i itself
+            if constexpr (kDev) {
+                g[0] += a.gref0;
+#pragma unroll
+                for (int i = 1; i < 5; ++i) g[i] += a.gref1;
+            }
+            pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k, a.gref1, a.wg1, a.inv_cs2g);
+            if constexpr (kDev) {
+                g[0] -= a.gref0;
+#pragma unroll
+                for (int i = 1; i < 5; ++i) g[i] -= a.gref1;
+            }
+        }
 
         // ---- moments (Eq. moments) and BGK collision of f, in deviations
         //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
@@ -634,13 +652,15 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
             f[8] += wo * (kWd * (rd - t6 + q6) - f[8]);
         }
         // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
-        const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+        float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+        if constexpr (kDev) C += kCRef;  // the weights add up to one
         {
             const float wg = omega.y;
             // the reaction term R = -k C of Eq. cde enters as w_i R, which is
             // omega (w_i R / omega): the equilibrium's isotropic part scaled by
-            // dfac = 1 - k / omega (exactly 1 without decay)
-            const float Cd = C * dfac;
+            // dfac = 1 - k / omega (exactly 1 without decay); for deviations
+            // the isotropic part is w_i (C dfac - C_ref)
+            const float Cd = kDev ? fmaf(C, dfac, -kCRef) : C * dfac;
             const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
             const float c1d = a.wg1 * Cd;
             // rest equilibrium w0 C formed as the remainder, so that the five

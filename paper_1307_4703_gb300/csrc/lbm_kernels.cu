@@ -40,11 +40,13 @@ namespace lbm {
 namespace {
 // Total of the block partials of the last step, in a fixed order (the same
 // bits on every run for a given launch shape).
+// out may be page-locked host memory (written over the interconnect).
 __global__ void diag_finish(const double* partials, int n_blocks, double* out)
 {
     __shared__ double red[8][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double t[4] = {0.0, 0.0, 0.0, 0.0};
+    grid_dependency_sync();  // the step kernel before it has written the partials
     for (int b = threadIdx.x; b < n_blocks; b += blockDim.x)
 #pragma unroll
         for (int q = 0; q < 4; ++q) t[q] += partials[4 * b + q];
@@ -408,7 +410,18 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
 
 cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s)
 {
-    diag_finish<<<1, 256, 0, s>>>(partials, n_blocks, out);
+    // a programmatic dependent of the step before it, like the steps
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, diag_finish, partials, n_blocks, out);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

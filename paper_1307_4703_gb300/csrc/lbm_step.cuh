@@ -56,16 +56,16 @@ __global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
 
         // ---- free flight (pull): v[p] component k = plane p at (x0+k) - e ----
         float4 v[kPlanes];
-        pull_quad<false>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane, a.gref0, a.gref1);
+        pull_quad<false>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
         if (act) {
-            bounce_back<T, kWalls>(v, lk, S, P, oC, a.gref1, static_cast<const T*>(a.wallv));
+            bounce_back<T, kWalls>(v, lk, S, P, oC, static_cast<const T*>(a.wallv));
             const RowBC bw = a.rowbc[y];
             const RowBC be = a.rowbc[a.ny + y];
             QuadAcc q;
             collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p)
-                Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
+                Codec<T>::st4(D + p * P + oC, v[p], 0.f);
             bad |= q.bad;
             diag.add(q);
         }
@@ -225,22 +225,21 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
 #pragma unroll
                 for (int p = 0; p < kPlanes; ++p) {
                     const T* row = sg.pl[p] + 4 * lane;
-                    const float off = plane_offset(p, a.gref0, a.gref1);
-                    const float4 c = Codec<T>::lds4(row + Q, off);
+                    const float4 c = Codec<T>::lds4(row + Q, 0.f);
                     if (src_col(p) == 0) v[p] = c;
-                    else if (src_col(p) == 1) v[p] = make_float4(Codec<T>::lds1(row + Q - 1, off), c.x, c.y, c.z);
-                    else v[p] = make_float4(c.y, c.z, c.w, Codec<T>::lds1(row + Q + 4, off));
+                    else if (src_col(p) == 1) v[p] = make_float4(Codec<T>::lds1(row + Q - 1, 0.f), c.x, c.y, c.z);
+                    else v[p] = make_float4(c.y, c.z, c.w, Codec<T>::lds1(row + Q + 4, 0.f));
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be refilled
             if (act) {
-                bounce_back<T, kWalls>(v, lk, S, P, oC, a.gref1, static_cast<const T*>(a.wallv));
+                bounce_back<T, kWalls>(v, lk, S, P, oC, static_cast<const T*>(a.wallv));
                 QuadAcc q;
                 collide_quad(v, lk, x0, bw, be, a, S, oC, omega, q);
 #pragma unroll
                 for (int p = 0; p < kPlanes; ++p)
-                    Codec<T>::st4(D + p * P + oC, v[p], plane_offset(p, a.gref0, a.gref1));
+                    Codec<T>::st4(D + p * P + oC, v[p], 0.f);
                 bad |= q.bad;
                 diag.add(q);
             }

@@ -158,3 +158,17 @@ def test_batch_creation_checks_run_on_the_host(lib):
     descs[0].tau_c = 0.5
     assert lib.lbm_create_batch(ctypes.byref(h), 1, descs, None) == lbm.LBM_ERR_ARG
     assert b"chip 0" in lib.lbm_last_error(None)
+
+
+def test_create_reports_the_first_isolated_node_of_a_large_mask(lib):
+    """Masks of a million nodes or more are scanned by several host threads,
+    each over its own rows; the error still names the first bad node in row
+    order."""
+    nx, ny = 1024, 1024
+    mask = np.zeros((ny, nx), np.uint8)
+    for x, y in ((300, 1000), (500, 900), (700, 900)):  # three isolated fluid nodes
+        mask[y - 1:y + 2, x - 1:x + 2] = 1
+        mask[y, x] = 0
+    st, msg = _create(lib, nx, ny, mask)
+    assert st == lbm.LBM_ERR_ARG
+    assert "(500, 900)" in msg and "no fluid neighbour" in msg
