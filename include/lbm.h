@@ -117,7 +117,7 @@ typedef struct {
     void* alloc_user;
     int32_t block_threads;  /* register variant: block size, 0 = default (128), else 64..256, a multiple of 32 */
     int32_t max_blocks;     /* step kernel grid cap: 0 = one wave of resident blocks */
-    int32_t variant;        /* step kernel: 0 = default (1 with FP32 storage, 2 with 16-bit storage),
+    int32_t variant;        /* step kernel: 0 = default (1),
                                1 = registers and warp shuffles,
                                2 = bulk-copy pipeline through shared memory with a producer warp,
                                3 = bulk-copy pipeline in which every warp refills its own stages */
@@ -135,6 +135,8 @@ typedef struct {
                                steps with unchanged valve words as one cached CUDA graph (captured
                                on first use, at most 16 per handle), which removes the per-launch
                                host cost on small chips.  Results are identical either way. */
+    int32_t scalar_variant; /* kernel of lbm_scalar_step: 0 = default (1), 1 = registers and warp
+                               shuffles, 2 = bulk-copy pipeline.  Results are identical. */
 } lbm_options;
 
 /* Storage precision.  The paper computes in double precision ("Numerical

@@ -38,6 +38,7 @@ constexpr int kDefaultPipeWarps = 4;
 constexpr int kDefaultRegsBlock = 128;
 constexpr int kScalarConsumers = 3;   // scalar-only step: computing warps per block
 constexpr int kScalarStagesPer = 3;   // and shared-memory stages per computing warp
+constexpr int kScalarRegsBlock = 128; // scalar-only step, register variant: threads per block
 
 struct Alloc {
     void* ptr = nullptr;
@@ -79,6 +80,7 @@ struct lbm_ctx {
     int partials_cap = 0;  // blocks the partials buffer holds (any launch shape fits)
     int diag_grid = 0;     // blocks whose partials the last step wrote
     int scalar_grid = 0;  // one wave of the scalar-only step kernel (set on first use)
+    bool scalar_regs = true;  // scalar-only step: register variant (else the bulk-copy pipeline)
     lbm::StepLaunch launch{lbm::kVariantBulk, 0, 0, 0};
     long long fluid = 0;
     long long device_bytes = 0;
@@ -421,6 +423,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         return fail(nullptr, LBM_ERR_ARG, "wall_scheme = LBM_WALL_EQUILIBRIUM runs variants 1 and 2, not 3");
     if (!(opt.decay >= 0.0 && opt.decay < 1.0))
         return fail(nullptr, LBM_ERR_ARG, "decay = %g outside [0, 1)", opt.decay);
+    if (opt.scalar_variant < 0 || opt.scalar_variant > 2)
+        return fail(nullptr, LBM_ERR_ARG, "scalar_variant = %d outside [0, 2]", opt.scalar_variant);
     if (opt.graph_steps < 0 || opt.graph_steps % 2 != 0 || opt.graph_steps > kMaxGraphSteps)
         return fail(nullptr, LBM_ERR_ARG, "graph_steps = %d: use 0 or an even number up to %d", opt.graph_steps,
                     kMaxGraphSteps);
@@ -574,6 +578,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->precision = opt.precision;
     h->elem = opt.precision == LBM_FP32 ? sizeof(float) : sizeof(uint16_t);
     h->graph_steps = opt.graph_steps;
+    h->scalar_regs = opt.scalar_variant != 2;
     h->decay = float(opt.decay);
     h->wall_scheme = opt.wall_scheme;
     for (int p = 0; p < n_ports; ++p) h->paper_ports |= ports[p].kind >= LBM_PORT_PRESSURE_RESCALE;
@@ -596,9 +601,9 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
     h->sms = sms;
     lbm::StepLaunch& L = h->launch;
-    // default: the register variant for FP32 storage, the bulk-copy pipeline
-    // for 16-bit storage (the faster of the two on each, see profiles)
-    const int variant = opt.variant ? opt.variant : opt.precision == LBM_FP32 ? 1 : 2;
+    // default: the register variant (the fastest with every storage type
+    // since the 16-bit collision runs on the stored deviations)
+    const int variant = opt.variant ? opt.variant : 1;
     L.variant = variant == 1 ? lbm::kVariantRegs : variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
     L.precision = opt.precision;
     L.pdl = true;  // consecutive steps overlap launch and set-up with the previous step's tail
@@ -1492,10 +1497,13 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
     a.fluid_blocks = h->diag_grid;
     a.err = h->err;
     if (h->scalar_grid == 0) {
-        // one wave of resident blocks of the bulk-copy kernel
+        // one wave of resident blocks of the scalar kernel
         int per_sm = 0;
-        LBM_CUDA(h, lbm::scalar_bulk_occupancy(kScalarConsumers, kScalarStagesPer, &per_sm));
-        h->scalar_grid = std::max(1, std::min(h->n_tiles, std::max(1, per_sm) * h->sms));
+        if (h->scalar_regs) LBM_CUDA(h, lbm::scalar_regs_occupancy(kScalarRegsBlock, &per_sm));
+        else LBM_CUDA(h, lbm::scalar_bulk_occupancy(kScalarConsumers, kScalarStagesPer, &per_sm));
+        const int tiles_per_block = h->scalar_regs ? kScalarRegsBlock / 32 : 1;
+        h->scalar_grid = std::max(1, std::min((h->n_tiles + tiles_per_block - 1) / tiles_per_block,
+                                              std::max(1, per_sm) * h->sms));
     }
     const int scalar_grid = std::min(h->scalar_grid, h->partials_cap);
     a.n_partials = std::max(h->diag_grid, scalar_grid);
@@ -1513,7 +1521,9 @@ lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
         a.ux = u;
         a.uy = u + h->plane;
         a.open_mask = w;
-        cudaError_t e = lbm::launch_scalar_step_bulk(a, scalar_grid, kScalarConsumers, kScalarStagesPer, h->stream);
+        cudaError_t e = h->scalar_regs
+                            ? lbm::launch_scalar_step_regs(a, scalar_grid, kScalarRegsBlock, h->stream)
+                            : lbm::launch_scalar_step_bulk(a, scalar_grid, kScalarConsumers, kScalarStagesPer, h->stream);
         if (e != cudaSuccess) {
             h->gbuf = g;
             return cuda_fail(h, e, "scalar step launch");

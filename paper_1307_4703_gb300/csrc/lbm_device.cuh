@@ -521,16 +521,19 @@ __device__ __forceinline__ bool complete_port(float (&f)[9], float (&g)[5], bool
 // from the neighbouring segment.  act: this lane holds fluid; ld_w / ld_e:
 // this lane's edge value feeds a fluid neighbour lane.  reverse: pull from
 // (x0 + k) + e_i instead (the transposed free flight of the adjoint).
-template <bool kReverse, typename T>
-__device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const T* __restrict__ S, long long P,
+// kP0, kN: the planes kP0 .. kP0 + kN - 1 only (S then points at plane kP0,
+// v[j] holds plane kP0 + j).
+template <bool kReverse, typename T, int kP0 = 0, int kN = kPlanes>
+__device__ __forceinline__ void pull_quad(float4 (&v)[kN], const T* __restrict__ S, long long P,
                                           long long oC, long long oS, long long oN, int halo_w, int halo_e,
                                           bool act, bool ld_w, bool ld_e, int lane)
 {
 #pragma unroll
-    for (int p = 0; p < kPlanes; ++p) {
+    for (int j = 0; j < kN; ++j) {
+        const int p = kP0 + j;
         const int sr = kReverse ? (src_row(p) == 0 ? 0 : 3 - src_row(p)) : src_row(p);
         const int sc = kReverse ? (src_col(p) == 0 ? 0 : 3 - src_col(p)) : src_col(p);
-        const long long o = p * P + (sr == 0 ? oC : sr == 1 ? oS : oN);
+        const long long o = j * P + (sr == 0 ? oC : sr == 1 ? oS : oN);
         const bool ld = sc == 0 ? act : sc == 1 ? ld_w : ld_e;
         float4 r = ld ? Codec<T>::ld4(S + o, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (sc == 1) {  // from column x - 1
@@ -546,7 +549,7 @@ __device__ __forceinline__ void pull_quad(float4 (&v)[kPlanes], const T* __restr
             if (lane == 31) e = h;
             r = make_float4(r.y, r.z, r.w, e);
         }
-        v[p] = r;
+        v[j] = r;
     }
 }
 

@@ -152,6 +152,9 @@ struct ScalarArgs {
 // warps and a producer warp, `per` shared-memory stages per computing warp.
 cudaError_t launch_scalar_step_bulk(const ScalarArgs& a, int grid, int consumers, int per, cudaStream_t s);
 cudaError_t scalar_bulk_occupancy(int consumers, int per, int* blocks_per_sm);
+// The register variant of the same step (blocks of `block` threads).
+cudaError_t launch_scalar_step_regs(const ScalarArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t scalar_regs_occupancy(int block, int* blocks_per_sm);
 cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, long long plane, float* ux, float* uy,
                                      cudaStream_t s);
 

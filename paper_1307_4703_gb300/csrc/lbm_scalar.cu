@@ -110,6 +110,29 @@ __device__ __forceinline__ void scalar_quad(float4 (&v)[5], unsigned lk, int x0,
     for (int i = 0; i < 5; ++i) stg4(a.dst + i * P + oC, v[i]);
 }
 
+// The block's scalar and outlet-flux sums into slots 1 and 3 of its
+// partials (and the bookkeeping of the slots of the coupled step's grid).
+__device__ __forceinline__ void scalar_partials(const ScalarArgs& a, const KahanF& sc, const KahanF& sq)
+{
+    __shared__ double red[32][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s1 = warp_sum(sc.value()), s3 = warp_sum(sq.value());
+    if (lane == 0) {
+        red[warp][0] = s1;
+        red[warp][1] = s3;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double sum = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
+        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = sum;
+        for (int b = blockIdx.x + gridDim.x; b < a.n_partials; b += gridDim.x)
+            a.partials[b * 4 + 1 + 2 * threadIdx.x] = 0.0;
+        // blocks beyond the last coupled step's grid hold no fluid partial
+        if (int(blockIdx.x) >= a.fluid_blocks) a.partials[blockIdx.x * 4 + 2 * threadIdx.x] = 0.0;
+    }
+}
+
 // The kernel: a producer warp streams each tile's 5 scalar plane rows
 // (with the halos of the shifted directions), its 2 stored velocity rows,
 // its wall-link bytes and port entries into a ring of shared-memory stages
@@ -241,22 +264,48 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) scalar_frozen_bulk(const S
         }
         if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
     }
-    __shared__ double red[32][2];
-    double s1 = warp_sum(sc.value()), s3 = warp_sum(sq.value());
-    if (lane == 0) {
-        red[warp][0] = s1;
-        red[warp][1] = s3;
+    scalar_partials(a, sc, sq);
+}
+
+// The register variant: each warp pulls its tile's five scalar planes with
+// 128-bit loads and warp shuffles (as coupled_step_regs does for all
+// fourteen) and the stored field of its nodes; 20 live floats per lane
+// instead of 56 leave room for many warps per SM, which keep the loads in
+// flight without a shared-memory pipeline.
+__global__ void __launch_bounds__(128) scalar_frozen_regs(const ScalarArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const long long P = a.plane;
+    const float* __restrict__ S = a.src;
+    KahanF sc, sq;
+    bool bad = false;
+    grid_dependency_sync();
+    for (int t = blockIdx.x * wpb + warp; t < a.n_tiles; t += gridDim.x * wpb) {
+        const uint2 tile = tile_at(a.tiles, a.n_tiles, t, a.reverse);
+        const int y = int(tile.x >> kSegBits);
+        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+        const long long oC = (long long)y * a.pitch + x0;
+        const long long oS = (long long)(y > 0 ? y - 1 : y) * a.pitch + x0;
+        const long long oN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + x0;
+        const int halo_w = x0 > 0 ? -1 : 0;
+        const int halo_e = x0 + 4 < a.pitch ? 4 : 3;
+        const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
+        const bool act = lk != 0xFFFFFFFFu;
+        const unsigned ball = __ballot_sync(kFull, act);
+        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;
+        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;
+        float4 v[5];
+        pull_quad<false, float, 9, 5>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
+        if (!act) continue;
+        const float4 ux4 = ldg4(a.ux + oC), uy4 = ldg4(a.uy + oC);
+        const RowBC bw = a.rowbc[y];
+        const RowBC be = a.rowbc[a.ny + y];
+        scalar_quad(v, lk, x0, bw, be, ux4, uy4, a, S, P, oC, sc, sq, bad);
     }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double sum = 0.0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
-        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = sum;
-        for (int b = blockIdx.x + gridDim.x; b < a.n_partials; b += gridDim.x)
-            a.partials[b * 4 + 1 + 2 * threadIdx.x] = 0.0;
-        // blocks beyond the last coupled step's grid hold no fluid partial
-        if (int(blockIdx.x) >= a.fluid_blocks) a.partials[blockIdx.x * 4 + 2 * threadIdx.x] = 0.0;
-    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
+    scalar_partials(a, sc, sq);
 }
 
 // Velocity of the stored populations (f as deviations) into two planes.
@@ -315,6 +364,27 @@ cudaError_t scalar_bulk_occupancy(int consumers, int per, int* blocks_per_sm)
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, scalar_frozen_bulk, 32 * (consumers + 1),
                                                          scalar_bulk_smem_bytes(consumers * per));
+}
+
+cudaError_t launch_scalar_step_regs(const ScalarArgs& a, int grid, int block, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, scalar_frozen_regs, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t scalar_regs_occupancy(int block, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, scalar_frozen_regs, block, 0);
 }
 
 cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, long long plane, float* ux, float* uy,

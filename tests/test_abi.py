@@ -85,6 +85,7 @@ def _create(lib, nx, ny, mask, tau=0.8, tau_c=0.6, ports=(), edge_u=None, edge_C
     (dict(opt="fp16pipe"), "variants 1 and 2"),
     (dict(opt="wallpipe"), "runs variants 1 and 2"),
     (dict(opt="badwall"), "wall_scheme = 2"),
+    (dict(opt="badscalar"), "scalar_variant = 3"),
 ])
 def test_create_rejects_invalid_arguments(lib, case, needle):
     nx, ny = case.get("nx", 8), 6
@@ -111,6 +112,8 @@ def test_create_rejects_invalid_arguments(lib, case, needle):
             opt.wall_scheme, opt.variant = lbm.LBM_WALL_EQUILIBRIUM, 3
         elif case["opt"] == "badwall":
             opt.wall_scheme = 2
+        elif case["opt"] == "badscalar":
+            opt.scalar_variant = 3
         else:
             opt.block_threads = 100
     st, msg = _create(lib, nx, ny, mask, tau=case.get("tau", 0.8), tau_c=case.get("tau_c", 0.6),
