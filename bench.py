@@ -354,34 +354,42 @@ def _batch(steps, stream, device, peak, n_chips=64):
                          "frac": achieved / peak, "bytes_per_launch": info["algorithmic_bytes_per_step"]}}
 
 
-def _graphs(steps, stream, device, peak):
-    """The 1024 x 768 chip (the paper's 1 um lattice, 313,600 fluid nodes:
-    a few microseconds per step, so launch costs show): single-step launches
-    against replayed CUDA graphs of 100 steps, after lbm_autotune."""
+def _small_chips(steps, stream, device, peak):
+    """Chips of a few microseconds per step, where launch costs show: the
+    1024 x 768 chip (the paper's 1 um lattice, 313,600 fluid nodes) with
+    single-step launches, replayed CUDA graphs of 100 steps (both after
+    lbm_autotune) and runs of up to 1000 steps in one cooperative launch
+    (multi_step); the 1024 x 512 chip (two buffers in L2) with single-step
+    launches and multi_step runs."""
     import torch
     from paper_1307_4703_gb300 import lbm, workloads as W
-    prob = W.config_full_chip()
-    fluid = W.fluid_count(prob)
-    out = {"workload": "chip-1024x768, %d fluid nodes" % fluid}
-    for key, gs in (("launches", 0), ("graphs_100", 100)):
-        chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=device, graph_steps=gs)
-        chip.set_valve_schedule(prob["period"], prob["states"])
-        info = chip.autotune()
-        chip.step(200)
-        chip.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        chip.step(steps)
-        e1.record(stream)
-        stream.synchronize()
-        s = e0.elapsed_time(e1) / 1e3
-        chip.diagnostics()
-        chip.close()
-        achieved = info["algorithmic_bytes_per_step"] * steps / s / 1e9
-        out[key] = {"value": fluid * steps / s / 1e9, "unit": UNIT, "steps": steps,
-                    "launch": {k: info[k] for k in ("variant", "grid", "block", "stages")},
-                    "roofline_frac": achieved / peak}
+    out = {}
+    for prob, modes in ((W.config_full_chip(), (("launches", {}), ("graphs_100", {"graph_steps": 100}),
+                                                ("multi_step_1000", {"multi_step": 1000}))),
+                        (W.config_adjoint_chip(), (("launches", {}), ("multi_step_1000", {"multi_step": 1000})))):
+        fluid = W.fluid_count(prob)
+        res = {"workload": "chip-%dx%d, %d fluid nodes" % (prob["nx"], prob["ny"], fluid)}
+        for key, kw in modes:
+            chip = lbm.Chip.from_problem(prob, stream=stream, torch_alloc=True, device=device, **kw)
+            chip.set_valve_schedule(prob["period"], prob["states"])
+            info = chip.autotune() if "multi_step" not in kw else chip.info()
+            chip.step(200)
+            chip.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            chip.step(steps)
+            e1.record(stream)
+            stream.synchronize()
+            s = e0.elapsed_time(e1) / 1e3
+            chip.diagnostics()
+            chip.close()
+            achieved = info["algorithmic_bytes_per_step"] * steps / s / 1e9
+            res[key] = {"value": fluid * steps / s / 1e9, "unit": UNIT, "steps": steps,
+                        "us_per_step": s / steps * 1e6, "roofline_frac": achieved / peak}
+            if "multi_step" not in kw:
+                res[key]["launch"] = {k: info[k] for k in ("variant", "grid", "block", "stages")}
+        out["chip-%dx%d" % (prob["nx"], prob["ny"])] = res
     return out
 
 
@@ -549,7 +557,7 @@ def main():
         extras["frozen_scalar_step"] = _frozen_scalar(chip, prob, min(args.steps, 2000), stream, peak)
         extras["reduced_precision_storage"] = _reduced_precision(prob, min(args.steps, 5000), stream, local, peak)
         extras["batch_64_chips"] = _batch(min(args.steps, 2000), stream, local, peak)
-        extras["small_chip_graphs"] = _graphs(min(args.steps, 20000), stream, local, peak)
+        extras["small_chips"] = _small_chips(min(args.steps, 20000), stream, local, peak)
         e2e_steps = min(args.steps, 5000)
         e = _e2e(prob, e2e_steps, local)
         e["value"] = aggregate_glups(fluid * e2e_steps, e["seconds"], ws)

@@ -137,6 +137,12 @@ typedef struct {
                                host cost on small chips.  Results are identical either way. */
     int32_t scalar_variant; /* kernel of lbm_scalar_step: 0 = default (1), 1 = registers and warp
                                shuffles, 2 = bulk-copy pipeline.  Results are identical. */
+    int32_t multi_step;     /* 0 = off; else <= 65536: lbm_step runs up to this many consecutive
+                               steps with unchanged valve words in ONE cooperative launch of the
+                               register kernel, a grid-wide barrier in place of the launch between
+                               steps (for small chips, whose steps are short next to a launch).
+                               FP32 storage and halfway bounce-back walls only.  Results are
+                               identical; a barrier that waits too long gives LBM_ERR_TIMEOUT. */
 } lbm_options;
 
 /* Storage precision.  The paper computes in double precision ("Numerical

@@ -39,6 +39,7 @@ constexpr int kDefaultRegsBlock = 128;
 constexpr int kScalarConsumers = 3;   // scalar-only step: computing warps per block
 constexpr int kScalarStagesPer = 3;   // and shared-memory stages per computing warp
 constexpr int kScalarRegsBlock = 128; // scalar-only step, register variant: threads per block
+constexpr int kMaxMultiStep = 65536;  // steps per cooperative launch
 
 struct Alloc {
     void* ptr = nullptr;
@@ -81,6 +82,9 @@ struct lbm_ctx {
     int diag_grid = 0;     // blocks whose partials the last step wrote
     int scalar_grid = 0;  // one wave of the scalar-only step kernel (set on first use)
     bool scalar_regs = true;  // scalar-only step: register variant (else the bulk-copy pipeline)
+    int multi_step = 0;           // lbm_step: steps per cooperative launch (0 = one launch per step)
+    int coop_grid = 0;            // blocks of that launch (all resident)
+    unsigned* bar = nullptr;      // its grid-barrier count
     lbm::StepLaunch launch{lbm::kVariantBulk, 0, 0, 0};
     long long fluid = 0;
     long long device_bytes = 0;
@@ -146,6 +150,19 @@ struct lbm_ctx {
         float* u;                    // 2 planes (u_x, u_y) of ny x pitch floats
     };
     std::vector<Field> fields;       // stored velocity fields, one per valve word
+
+    // The longest run of steps from t0, at most max_len, over which no valve
+    // word changes (mask_constant holds for it).
+    int64_t mask_run(int64_t t0, int64_t max_len) const
+    {
+        int64_t len = max_len;
+        auto lim = [&](int64_t per, size_t n) {
+            if (n > 1) len = std::min(len, per - t0 % per);
+        };
+        if (inst.empty()) lim(period, schedule.size());
+        for (const Inst& k : inst) lim(k.period, k.schedule.size());
+        return len;
+    }
 
     uint32_t mask_at(int64_t t) const
     {
@@ -423,6 +440,10 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         return fail(nullptr, LBM_ERR_ARG, "wall_scheme = LBM_WALL_EQUILIBRIUM runs variants 1 and 2, not 3");
     if (!(opt.decay >= 0.0 && opt.decay < 1.0))
         return fail(nullptr, LBM_ERR_ARG, "decay = %g outside [0, 1)", opt.decay);
+    if (opt.multi_step < 0 || opt.multi_step > kMaxMultiStep)
+        return fail(nullptr, LBM_ERR_ARG, "multi_step = %d outside [0, %d]", opt.multi_step, kMaxMultiStep);
+    if (opt.multi_step > 0 && (opt.precision != LBM_FP32 || opt.wall_scheme != LBM_WALL_BOUNCE_BACK))
+        return fail(nullptr, LBM_ERR_ARG, "multi_step needs FP32 storage and bounce-back walls");
     if (opt.scalar_variant < 0 || opt.scalar_variant > 2)
         return fail(nullptr, LBM_ERR_ARG, "scalar_variant = %d outside [0, 2]", opt.scalar_variant);
     if (opt.graph_steps < 0 || opt.graph_steps % 2 != 0 || opt.graph_steps > kMaxGraphSteps)
@@ -579,6 +600,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->elem = opt.precision == LBM_FP32 ? sizeof(float) : sizeof(uint16_t);
     h->graph_steps = opt.graph_steps;
     h->scalar_regs = opt.scalar_variant != 2;
+    h->multi_step = opt.multi_step;
     h->decay = float(opt.decay);
     h->wall_scheme = opt.wall_scheme;
     for (int p = 0; p < n_ports; ++p) h->paper_ports |= ports[p].kind >= LBM_PORT_PRESSURE_RESCALE;
@@ -642,6 +664,15 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->diag_grid = h->launch.grid;
     h->partials = static_cast<double*>(dev_alloc(h, size_t(h->partials_cap) * 4 * sizeof(double)));
     h->err = static_cast<unsigned*>(dev_alloc(h, sizeof(unsigned)));
+    if (h->multi_step > 0) {
+        int coop_per_sm = 0;
+        e = lbm::steps_coop_occupancy(kDefaultRegsBlock, &coop_per_sm);
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
+        const int wpb = kDefaultRegsBlock / 32;
+        h->coop_grid = std::max(1, std::min((h->n_tiles + wpb - 1) / wpb, std::max(1, coop_per_sm) * sms));
+        h->bar = static_cast<unsigned*>(dev_alloc(h, sizeof(unsigned)));
+        if (!h->bar) return bail(fail(h, LBM_ERR_OOM, "device allocation of the barrier word failed"));
+    }
     h->diag = static_cast<double*>(dev_alloc(h, 4 * sizeof(double)));
     h->fields_tmp = static_cast<float*>(dev_alloc(h, size_t(4) * nx * ny * sizeof(float)));
     if (batch) h->rates = static_cast<float4*>(dev_alloc(h, size_t(ny) * sizeof(float4)));
@@ -898,6 +929,24 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
     const int G = h->graph_steps;
     for (int64_t k = 0; k < n;) {
         h->mask_words(h->step, a.open_mask);
+        if (h->multi_step > 0 && n - k >= 2) {
+            const int64_t m = h->mask_run(h->step, std::min<int64_t>(n - k, h->multi_step));
+            if (m >= 2) {
+                // m steps in one cooperative launch; the state ends in the
+                // other buffer when m is odd
+                a.src = h->pop[h->cur];
+                a.dst = h->pop[1 - h->cur];
+                a.reverse = h->cur;
+                cudaError_t e = lbm::launch_steps_coop(a, int(m), h->bar, h->coop_grid, kDefaultRegsBlock, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "multi-step launch");
+                if (m & 1) h->cur = 1 - h->cur;
+                h->gbuf = h->cur;
+                h->diag_grid = h->coop_grid;
+                h->step += m;
+                k += m;
+                continue;
+            }
+        }
         if (G > 0 && n - k >= G && h->mask_constant(h->step, G)) {
             // G steps (an even number: the state ends in the buffer it
             // started from) as one graph launch

@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstddef>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -112,6 +113,31 @@ struct Codec<float> {
     static __device__ __forceinline__ float4 lds4(const float* p, float) { return *reinterpret_cast<const float4*>(p); }
     static __device__ __forceinline__ float lds1(const float* p, float) { return *p; }
 };
+
+// FP32 storage read coherently at L2 (ld.global.cg), for a kernel that
+// reads in one time step what other blocks of the same launch wrote in the
+// step before (the multi-step kernel): the read-only path of __ldg may not
+// be used for such data.
+struct F32Coherent {
+    float v;
+};
+
+template <>
+struct Codec<F32Coherent> {
+    static __device__ __forceinline__ const float* f(const F32Coherent* p) { return reinterpret_cast<const float*>(p); }
+    static __device__ __forceinline__ float* f(F32Coherent* p) { return reinterpret_cast<float*>(p); }
+    static __device__ __forceinline__ float4 ld4(const F32Coherent* p, float)
+    {
+        return __ldcg(reinterpret_cast<const float4*>(p));
+    }
+    static __device__ __forceinline__ float ld1(const F32Coherent* p, float) { return __ldcg(f(p)); }
+    static __device__ __forceinline__ void st4(F32Coherent* p, const float4& v, float) { stg4(f(p), v); }
+    static __device__ __forceinline__ void st1(F32Coherent* p, float v, float) { *f(p) = v; }
+};
+
+// Storage types that hold FP32 values as they are (no deviation offsets).
+template <typename T>
+constexpr bool kStoresF32 = std::is_same<T, float>::value || std::is_same<T, F32Coherent>::value;
 
 template <>
 struct Codec<__half> {
@@ -250,6 +276,41 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident): thread 0
+// of each block adds one to *count and waits until it reaches target.  The
+// wait is bounded (kBarrierPolls polls, 100 ns apart or more, some seconds
+// in all); a block that gives up, or sees that another one did (bit 1 of
+// the error word), sets that bit and returns false, and the kernel stops.
+// The fences around the count make each block's writes before the barrier
+// visible to every block after it.
+constexpr unsigned kBarrierPolls = 1u << 25;
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, unsigned* err)
+{
+    __shared__ int go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(count, 1u);
+        for (unsigned n = 0;; ++n) {
+            unsigned c, e;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(count) : "memory");
+            if (c >= target) break;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
+            if ((e & 2u) || n >= kBarrierPolls) {
+                atomicOr(err, 2u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        go = ok;
+    }
+    __syncthreads();
+    return go != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -590,7 +651,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     // g_i - w_i C_ref here (C_ref = kCRef), as the fluid ones stay f_i - w_i:
     // the collision below is written for deviations, so no offset is added
     // on loading or subtracted on storing.  FP32 storage holds g_i itself.
-    constexpr bool kDev = !std::is_same<T, float>::value;
+    constexpr bool kDev = !kStoresF32<T>;
 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

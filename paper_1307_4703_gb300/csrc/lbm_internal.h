@@ -179,6 +179,13 @@ cudaError_t step_walls_occupancy(const StepLaunch& l, int* blocks_per_sm);
 cudaError_t prepare_walls_kernels();
 
 cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s);
+// n coupled steps (FP32 storage, halfway bounce-back) in one cooperative
+// launch of `grid` blocks of `block` threads, all resident (grid <= the
+// occupancy times the SMs): src holds time t, the result of t + n ends in
+// src if n is even, else in dst.  count: a device word for the grid barrier
+// (zeroed here).  The valve words of a.open_mask hold for all n steps.
+cudaError_t launch_steps_coop(const StepArgs& a, int n, unsigned* count, int grid, int block, cudaStream_t s);
+cudaError_t steps_coop_occupancy(int block, int* blocks_per_sm);
 cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm);
 
 // Every node (fluid and solid, padding included) to the rest equilibrium

@@ -63,6 +63,35 @@ __global__ void diag_finish(const double* partials, int n_blocks, double* out)
     }
 }
 
+// Many steps in one cooperative launch (every block resident): the register
+// variant's tile loop once per step, the two buffers swapping roles, and a
+// grid-wide barrier between steps in place of the launch boundary.  Loads go
+// through L2 (F32Coherent): each step reads what other blocks wrote in the
+// step before.  The valve words are those of a.open_mask for all n steps;
+// the diagnostics partials are those of the last step.  A barrier that
+// times out stops the kernel with bit 1 of the error word set.
+__global__ void __launch_bounds__(256, 2) coupled_steps_coop(const StepArgs a, int n, unsigned* count)
+{
+    using T = F32Coherent;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int stride = gridDim.x * wpb;
+    LaneDiag diag;
+    bool bad = false;
+    for (int s = 0; s < n; ++s) {
+        const T* __restrict__ S = reinterpret_cast<const T*>((s & 1) ? a.dst : a.src);
+        T* __restrict__ D = reinterpret_cast<T*>((s & 1) ? const_cast<float*>(a.src) : a.dst);  // both buffers are written
+        const int rev = a.reverse ^ (s & 1);
+        diag = LaneDiag();
+        for (int t = blockIdx.x * wpb + warp; t < a.n_tiles; t += stride)
+            regs_tile<T, false>(a, S, D, a.plane, tile_at(a.tiles, a.n_tiles, t, rev), lane, diag, bad);
+        if (s + 1 < n && !grid_barrier(count, unsigned(s + 1) * gridDim.x, a.err)) break;
+    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
+    block_partials(a, diag);
+}
+
 // ---------------------------------------------------------------------------
 // Variant 3: every warp streams its own tiles
 // ---------------------------------------------------------------------------
@@ -406,6 +435,29 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+cudaError_t launch_steps_coop(const StepArgs& a, int n, unsigned* count, int grid, int block, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident, or the launch fails
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, coupled_steps_coop, a, n, count);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t steps_coop_occupancy(int block, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_steps_coop, block, 0);
 }
 
 cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s)

@@ -75,6 +75,43 @@ __global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
     block_partials(a, diag);
 }
 
+// One warp tile of the register variant as a function (the multi-step
+// kernel's body; coupled_step_regs keeps the same code written out, which
+// the register allocator handles without spills): pull, walls, ports,
+// collisions and stores of the lane's four nodes (S holds time t, D
+// receives t + 1).
+template <typename T, bool kWalls>
+__device__ __forceinline__ void regs_tile(const StepArgs& a, const T* __restrict__ S, T* __restrict__ D,
+                                          long long P, uint2 tile, int lane, LaneDiag& diag, bool& bad)
+{
+    const int y = int(tile.x >> kSegBits);
+    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+    const long long oC = (long long)y * a.pitch + x0;
+    const long long oS = (long long)(y > 0 ? y - 1 : y) * a.pitch + x0;
+    const long long oN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + x0;
+    const int halo_w = x0 > 0 ? -1 : 0;
+    const int halo_e = x0 + 4 < a.pitch ? 4 : 3;
+    const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
+    const bool act = lk != 0xFFFFFFFFu;
+    const unsigned ball = __ballot_sync(kFull, act);
+    const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;
+    const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;
+    float4 v[kPlanes];
+    pull_quad<false>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
+    if (act) {
+        bounce_back<T, kWalls>(v, lk, S, P, oC, static_cast<const T*>(a.wallv));
+        const RowBC bw = a.rowbc[y];
+        const RowBC be = a.rowbc[a.ny + y];
+        QuadAcc q;
+        collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p)
+            Codec<T>::st4(D + p * P + oC, v[p], 0.f);
+        bad |= q.bad;
+        diag.add(q);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Variant 2: bulk-copy pipeline through shared memory
 // ---------------------------------------------------------------------------

@@ -52,7 +52,8 @@ class lbm_options(ctypes.Structure):
                 ("max_blocks", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("consumer_warps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("decay", ctypes.c_double), ("wall_scheme", ctypes.c_int32),
-                ("graph_steps", ctypes.c_int32), ("scalar_variant", ctypes.c_int32)]
+                ("graph_steps", ctypes.c_int32), ("scalar_variant", ctypes.c_int32),
+                ("multi_step", ctypes.c_int32)]
 
 
 class lbm_info(ctypes.Structure):
@@ -216,7 +217,7 @@ class Chip:
     def __init__(self, solid, tau, tau_c, ports=(), edge_u=None, edge_C=None, w0=1.0 / 3.0,
                  rho0=1.0, C0=0.0, stream=None, torch_alloc=False, device=-1, block_threads=0,
                  max_blocks=0, variant=0, pipeline_stages=0, consumer_warps=0, precision="fp32",
-                 graph_steps=0, decay=0.0, wall_scheme=0, scalar_variant=0, _batch=None):
+                 graph_steps=0, decay=0.0, wall_scheme=0, scalar_variant=0, multi_step=0, _batch=None):
         self._lib = load()
         if _batch is None:
             solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
@@ -238,6 +239,7 @@ class Chip:
         opt.decay = float(decay)
         opt.wall_scheme = int(wall_scheme)
         opt.scalar_variant = int(scalar_variant)
+        opt.multi_step = int(multi_step)
         self.stream = stream
         if stream is not None:
             opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))

@@ -86,6 +86,8 @@ def _create(lib, nx, ny, mask, tau=0.8, tau_c=0.6, ports=(), edge_u=None, edge_C
     (dict(opt="wallpipe"), "runs variants 1 and 2"),
     (dict(opt="badwall"), "wall_scheme = 2"),
     (dict(opt="badscalar"), "scalar_variant = 3"),
+    (dict(opt="multifp16"), "multi_step needs FP32"),
+    (dict(opt="badmulti"), "multi_step = 70000"),
 ])
 def test_create_rejects_invalid_arguments(lib, case, needle):
     nx, ny = case.get("nx", 8), 6
@@ -114,6 +116,10 @@ def test_create_rejects_invalid_arguments(lib, case, needle):
             opt.wall_scheme = 2
         elif case["opt"] == "badscalar":
             opt.scalar_variant = 3
+        elif case["opt"] == "multifp16":
+            opt.precision, opt.multi_step = lbm.LBM_FP16, 8
+        elif case["opt"] == "badmulti":
+            opt.multi_step = 70000
         else:
             opt.block_threads = 100
     st, msg = _create(lib, nx, ny, mask, tau=case.get("tau", 0.8), tau_c=case.get("tau_c", 0.6),

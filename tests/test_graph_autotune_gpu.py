@@ -86,3 +86,50 @@ def test_graph_steps_must_be_even():
     with pytest.raises(lbm.LbmError) as e:
         lbm.Chip.from_problem(prob, graph_steps=3)
     assert e.value.status == lbm.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("multi_step", [16, 7, 1000])
+def test_multi_step_launch_is_bit_identical(multi_step):
+    """Runs of steps in one cooperative launch (a grid-wide barrier between
+    steps): valve switches every 25 steps split the runs, odd run lengths
+    leave the state in the other buffer.  Populations are bit-identical; the
+    diagnostics are sums over another grouping of blocks, equal to round-off."""
+    prob, init = W.random_case(12, 300, 20)
+    a = lbm.Chip.from_problem(prob)
+    b = lbm.Chip.from_problem(prob, multi_step=multi_step)
+    for c in (a, b):
+        c.init_equilibrium(**init)
+        c.set_valve_schedule(25, prob["states"])
+    for n in (137, 1, 64, 3):
+        a.step(n)
+        b.step(n)
+    assert a.step_count() == b.step_count() == 205
+    assert _same(a, b)
+    assert np.allclose(a.diagnostics(), b.diagnostics(), rtol=1e-6, atol=1e-9)
+    a.close()
+    b.close()
+
+
+def test_multi_step_launch_on_larger_chips_and_batches():
+    """A chip of several tiles per row with a ragged last segment, and a
+    batch of chips with their own valve programs."""
+    prob = W.two_channel_chip(600, 300, 40, 580, 120, 0.6, 0.52, 0.04, 30, 200)
+    a = lbm.Chip.from_problem(prob)
+    b = lbm.Chip.from_problem(prob, multi_step=64)
+    for c in (a, b):
+        c.set_valve_schedule(prob["period"], prob["states"])
+        c.step(173)
+    assert _same(a, b)
+    assert np.allclose(a.diagnostics(), b.diagnostics(), rtol=1e-6, atol=1e-9)
+    a.close()
+    b.close()
+    chips = W.config_batch(3, seed=6)
+    a = lbm.Chip.batch(chips)
+    b = lbm.Chip.batch(chips, multi_step=50)
+    for c in (a, b):
+        for k, p in enumerate(chips):
+            c.set_instance_schedule(k, 30 + 17 * k, p["states"])
+        c.step(250)
+    assert _same(a, b)
+    a.close()
+    b.close()
