@@ -346,6 +346,14 @@ lbm_status lbm_synchronize(lbm_handle h);
 /* Reset a sticky LBM_ERR_NUMERIC or LBM_ERR_TIMEOUT flag. */
 lbm_status lbm_clear_error(lbm_handle h);
 
+/* Test hook of the failure path of multi_step runs: with extra > 0 every
+ * grid-wide barrier of the multi-step kernel waits for `extra` arrivals that
+ * never come, so its bounded wait (about a second) runs out, the kernel
+ * stops and the next synchronising call returns LBM_ERR_TIMEOUT; the
+ * context stays usable.  0 (the default) restores normal operation.
+ * LBM_ERR_ARG for extra < 0 or > 1024. */
+lbm_status lbm_debug_barrier_extra(lbm_handle h, int32_t extra);
+
 typedef struct {
     int32_t nx, ny;
     int32_t pitch;          /* elements per stored row (multiple of 128) */

@@ -85,6 +85,7 @@ struct lbm_ctx {
     int multi_step = 0;           // lbm_step: steps per cooperative launch (0 = one launch per step)
     int coop_grid = 0;            // blocks of that launch (all resident)
     unsigned* bar = nullptr;      // its grid-barrier count
+    unsigned barrier_extra = 0;   // test hook (lbm_debug_barrier_extra)
     lbm::StepLaunch launch{lbm::kVariantBulk, 0, 0, 0};
     long long fluid = 0;
     long long device_bytes = 0;
@@ -937,6 +938,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
                 a.src = h->pop[h->cur];
                 a.dst = h->pop[1 - h->cur];
                 a.reverse = h->cur;
+                a.barrier_extra = h->barrier_extra;
                 cudaError_t e = lbm::launch_steps_coop(a, int(m), h->bar, h->coop_grid, kDefaultRegsBlock, h->stream);
                 if (e != cudaSuccess) return cuda_fail(h, e, "multi-step launch");
                 if (m & 1) h->cur = 1 - h->cur;
@@ -995,6 +997,14 @@ static lbm_status read_err_word(lbm_handle h)
     if (err & 1u)
         return fail(h, LBM_ERR_NUMERIC, "numeric: a fluid node reached a non-finite or non-positive density or a non-finite concentration");
     return pending_numeric(h);
+}
+
+lbm_status lbm_debug_barrier_extra(lbm_handle h, int32_t extra)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (extra < 0 || extra > 1024) return fail(h, LBM_ERR_ARG, "extra = %d outside [0, 1024]", extra);
+    h->barrier_extra = unsigned(extra);
+    return LBM_OK;
 }
 
 lbm_status lbm_clear_error(lbm_handle h)

@@ -280,12 +280,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 // Grid-wide barrier of a cooperative launch (every block resident): thread 0
 // of each block adds one to *count and waits until it reaches target.  The
-// wait is bounded (kBarrierPolls polls, 100 ns apart or more, some seconds
-// in all); a block that gives up, or sees that another one did (bit 1 of
-// the error word), sets that bit and returns false, and the kernel stops.
-// The fences around the count make each block's writes before the barrier
-// visible to every block after it.
-constexpr unsigned kBarrierPolls = 1u << 25;
+// wait is bounded like the mbarrier waits (kWaitCycles, about a second); a
+// block that gives up, or sees that another one did (bit 1 of the error
+// word), sets that bit and returns false, and the kernel stops.  The fences
+// around the count make each block's writes before the barrier visible to
+// every block after it.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, unsigned* err)
 {
     __shared__ int go;
@@ -294,12 +293,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, u
         int ok = 1;
         __threadfence();
         atomicAdd(count, 1u);
-        for (unsigned n = 0;; ++n) {
+        const long long t0 = clock64();
+        for (;;) {
             unsigned c, e;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(count) : "memory");
             if (c >= target) break;
             asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
-            if ((e & 2u) || n >= kBarrierPolls) {
+            if ((e & 2u) || clock64() - t0 > kWaitCycles) {
                 atomicOr(err, 2u);
                 ok = 0;
                 break;

@@ -84,6 +84,8 @@ struct StepArgs {
     double* partials;       // 4 diagnostics partial sums per block (scratch)
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
     float gref0, gref1;     // 16-bit storage: offsets w_0 C_ref and w_1 C_ref of the scalar planes
+    unsigned barrier_extra; // multi-step kernel: arrivals its barriers wait for beyond the grid's
+                            // (0; a test hook sets 1 so that the bounded wait runs out)
 };
 
 // One adjoint step (lbm_adjoint.cu): A(t) from A(t+1) and the state P(t).

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256, 2) coupled_steps_coop(const StepArgs a, i
         diag = LaneDiag();
         for (int t = blockIdx.x * wpb + warp; t < a.n_tiles; t += stride)
             regs_tile<T, false>(a, S, D, a.plane, tile_at(a.tiles, a.n_tiles, t, rev), lane, diag, bad);
-        if (s + 1 < n && !grid_barrier(count, unsigned(s + 1) * gridDim.x, a.err)) break;
+        if (s + 1 < n && !grid_barrier(count, unsigned(s + 1) * gridDim.x + a.barrier_extra, a.err)) break;
     }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
     block_partials(a, diag);

@@ -129,6 +129,7 @@ SIGNATURES = {
     "lbm_get_step": (ctypes.c_int, [ctypes.c_void_p, _P(ctypes.c_int64)]),
     "lbm_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
     "lbm_clear_error": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbm_debug_barrier_extra": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lbm_get_info": (ctypes.c_int, [ctypes.c_void_p, _P(lbm_info)]),
     "lbm_step_noalloc": (ctypes.c_int, [_P(lbm_noalloc_step)]),
     "lbm_adjoint": (ctypes.c_int, [ctypes.c_void_p, _P(lbm_objective), ctypes.c_int64, ctypes.c_int32,
@@ -409,6 +410,11 @@ class Chip:
 
     def clear_error(self):
         self._check(self._lib.lbm_clear_error(self._h))
+
+    def debug_barrier_extra(self, extra):
+        """Test hook: make the multi-step kernel's barriers wait for arrivals
+        that never come (extra > 0), so that their bounded wait runs out."""
+        self._check(self._lib.lbm_debug_barrier_extra(self._h, int(extra)))
 
     def adjoint(self, n_steps, obj_x, obj_y, target, weight=None, ckpt_every=250):
         """Gradient of J = sum weight (C(x, y) - target)^2 after n_steps

@@ -133,3 +133,29 @@ def test_multi_step_launch_on_larger_chips_and_batches():
     assert _same(a, b)
     a.close()
     b.close()
+
+
+def test_multi_step_barrier_timeout_is_reported_and_recoverable():
+    """The grid barrier's bounded wait runs out (the test hook makes it wait
+    for an arrival that never comes): the kernel stops with the timeout bit,
+    the host reports LBM_ERR_TIMEOUT, and after clearing it the context and
+    the handle work again.  No fault, trap or endless wait."""
+    prob, init = W.random_case(12, 300, 20)
+    chip = lbm.Chip.from_problem(prob, multi_step=8)
+    chip.init_equilibrium(**init)
+    chip.debug_barrier_extra(1)
+    chip.step(4)
+    with pytest.raises(lbm.LbmError) as e:
+        chip.synchronize()
+    assert e.value.status == lbm.LBM_ERR_TIMEOUT
+    chip.clear_error()
+    chip.debug_barrier_extra(0)
+    chip.init_equilibrium(**init)
+    ref = lbm.Chip.from_problem(prob)
+    ref.init_equilibrium(**init)
+    for c in (chip, ref):
+        c.step(10)
+    chip.synchronize()
+    assert _same(chip, ref)
+    chip.close()
+    ref.close()
