@@ -260,6 +260,16 @@ __device__ __forceinline__ void complete_quad(float4 (&x)[kPlanes], const QuadPo
 // not fluid) returns the node's own opposite entry; at an open pressure-port
 // node the scalar population with e_x = s gets the do-nothing term of step
 // t+1; solid nodes are zero.
+// kCoherent: M(t+1) and dn were written by other blocks of the same launch
+// (the multi-step kernel), so they are read through L2.
+template <bool kCoherent>
+__device__ __forceinline__ float4 ld4_mid(const float* p)
+{
+    if constexpr (kCoherent) return __ldcg(reinterpret_cast<const float4*>(p));
+    else return ldg4(p);
+}
+
+template <bool kCoherent>
 __device__ __forceinline__ void transposed_flight(float4 (&v)[kPlanes], const QuadPos& q, const RowBC& bw,
                                                   const RowBC& be, const AdjointArgs& A)
 {
@@ -276,8 +286,8 @@ __device__ __forceinline__ void transposed_flight(float4 (&v)[kPlanes], const Qu
         for (int i = 1; i <= 8; ++i) {
             const int o = opp(i);
             if (wall & (1u << (o - 1))) {
-                const float4 own = ldg4(M + o * P + q.oC);
-                const float4 ownc = i <= 4 ? ldg4(M + (9 + o) * P + q.oC) : own;
+                const float4 own = ld4_mid<kCoherent>(M + o * P + q.oC);
+                const float4 ownc = i <= 4 ? ld4_mid<kCoherent>(M + (9 + o) * P + q.oC) : own;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     if ((q.lk >> (8 * k + o - 1)) & 1u) {
@@ -299,8 +309,8 @@ __device__ __forceinline__ void transposed_flight(float4 (&v)[kPlanes], const Qu
             for (int p = 0; p < kPlanes; ++p) at(v[p], k) = 0.f;
             continue;
         }
-        if (dn_w && bw.x == q.x0 + k) at(v[10], k) += A.dn[q.y];
-        else if (dn_e && be.x == q.x0 + k) at(v[12], k) += A.dn[A.ny + q.y];
+        if (dn_w && bw.x == q.x0 + k) at(v[10], k) += kCoherent ? __ldcg(A.dn + q.y) : A.dn[q.y];
+        else if (dn_e && be.x == q.x0 + k) at(v[12], k) += kCoherent ? __ldcg(A.dn + A.ny + q.y) : A.dn[A.ny + q.y];
     }
 }
 
@@ -331,38 +341,81 @@ __global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_collide(const Adjoin
 // K'^T and B^T as in adjoint_collide.  dn carries the do-nothing terms from
 // one step to the next: the node that reads the entry of step t+1 is the
 // node that then writes the one of step t.
+// One tile of a fused reverse step (the body of adjoint_fused and of the
+// multi-step kernel).
+template <bool kCoherent>
+__device__ __forceinline__ void fused_tile(const AdjointArgs& A, uint2 tile, int lane, const NextShared& next,
+                                           KahanF& dwg)
+{
+    const long long P = A.plane;
+    const QuadPos q = quad_pos(A, tile, lane);
+    const RowBC bw = A.rowbc[q.y];
+    const RowBC be = A.rowbc[A.ny + q.y];
+    {
+        float4 v[kPlanes];
+        if constexpr (kCoherent)
+            pull_quad<true>(v, reinterpret_cast<const F32Coherent*>(A.mid_next), P, q.oC, q.oS, q.oN, q.halo_w,
+                            q.halo_e, q.act, q.ld_w, q.ld_e, lane);
+        else
+            pull_quad<true>(v, A.mid_next, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
+        if (q.act) {
+            transposed_flight<kCoherent>(v, q, bw, be, A);
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) next(p, k) = at(v[p], k);
+        }
+    }
+    float4 x[kPlanes];
+    pull_quad<false>(x, A.state, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
+    if (!q.act) return;
+    complete_quad(x, q, bw, be, A);
+    collide_adjoint_quad(x, q.lk, q.x0, q.y, q.oC, bw, be, A, next, dwg);
+}
+
 __global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_fused(const AdjointArgs A)
 {
     extern __shared__ float next_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const long long P = A.plane;
     const NextShared next{next_smem + threadIdx.x, int(blockDim.x)};
     KahanF dwg;
     grid_dependency_sync();
-    for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb) {
-        const QuadPos q = quad_pos(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane);
-        const RowBC bw = A.rowbc[q.y];
-        const RowBC be = A.rowbc[A.ny + q.y];
-        {
-            float4 v[kPlanes];
-            pull_quad<true>(v, A.mid_next, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
-            if (q.act) {
-                transposed_flight(v, q, bw, be, A);
-#pragma unroll
-                for (int p = 0; p < kPlanes; ++p)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) next(p, k) = at(v[p], k);
-            }
-        }
-        float4 x[kPlanes];
-        pull_quad<false>(x, A.state, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
-        if (!q.act) continue;
-        complete_quad(x, q, bw, be, A);
-        collide_adjoint_quad(x, q.lk, q.x0, q.y, q.oC, bw, be, A, next, dwg);
-    }
+    for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb)
+        fused_tile<false>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, next, dwg);
     block_add(A.grad_w, dwg.value());
+}
+
+// Reverse steps j = j_hi down to j_lo in one cooperative launch (every block
+// resident), a grid-wide barrier between them: step j reads the state
+// state_lo + (j - j_lo) stride and the valve words masks[j - j_lo],
+// masks[j - j_lo + 1]; M alternates between mid_a (M(j_hi + 1) on entry)
+// and mid_b.  The step's own reads of M and dn go through L2.  A barrier
+// that times out stops the kernel with bit 1 of the error word set.
+__global__ void __launch_bounds__(kAdjointBlock, 4)
+    adjoint_steps_coop(const AdjointArgs A0, int j_hi, int j_lo, const float* state_lo, long long stride,
+                       const uint32_t* masks, float* mid_a, float* mid_b, unsigned* count)
+{
+    extern __shared__ float next_smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const NextShared next{next_smem + threadIdx.x, int(blockDim.x)};
+    KahanF dwg;
+    for (int j = j_hi, s = 0; j >= j_lo; --j, ++s) {
+        AdjointArgs A = A0;
+        A.state = state_lo + (j - j_lo) * stride;
+        A.open_mask = __ldg(masks + (j - j_lo));
+        A.open_mask_next = __ldg(masks + (j - j_lo) + 1);
+        A.mid_next = (s & 1) ? mid_b : mid_a;
+        A.adj_mid = (s & 1) ? mid_a : mid_b;
+        A.reverse = A0.reverse ^ (s & 1);
+        for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb)
+            fused_tile<true>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, next, dwg);
+        if (j > j_lo && !grid_barrier(count, unsigned(s + 1) * gridDim.x + A0.barrier_extra, A0.err)) break;
+    }
+    block_add(A0.grad_w, dwg.value());
 }
 
 // J = sum w (C - target)^2 at the final state, and its derivative with
@@ -420,6 +473,36 @@ cudaError_t adjoint_occupancy(int* blocks_per_sm)
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, adjoint_fused, kAdjointBlock, smem);
     *blocks_per_sm = a < b ? a : b;
     return e;
+}
+
+cudaError_t adjoint_coop_occupancy(int* blocks_per_sm)
+{
+    const size_t smem = adjoint_fused_smem(kAdjointBlock);
+    cudaError_t e = cudaFuncSetAttribute(adjoint_steps_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, adjoint_steps_coop,
+                                                                           kAdjointBlock, smem);
+    return e;
+}
+
+cudaError_t launch_adjoint_steps_coop(const AdjointArgs& a, int j_hi, int j_lo, const float* state_lo,
+                                      long long stride, const uint32_t* masks, float* mid_a, float* mid_b,
+                                      unsigned* count, int grid, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kAdjointBlock);
+    cfg.dynamicSmemBytes = adjoint_fused_smem(kAdjointBlock);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident, or the launch fails
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, adjoint_steps_coop, a, j_hi, j_lo, state_lo, stride, masks, mid_a, mid_b, count);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_step(const AdjointArgs& a, bool first, int grid, cudaStream_t s)

@@ -939,7 +939,8 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
                 a.dst = h->pop[1 - h->cur];
                 a.reverse = h->cur;
                 a.barrier_extra = h->barrier_extra;
-                cudaError_t e = lbm::launch_steps_coop(a, int(m), h->bar, h->coop_grid, kDefaultRegsBlock, h->stream);
+                cudaError_t e =
+                    lbm::launch_steps_coop(a, int(m), 0, h->bar, h->coop_grid, kDefaultRegsBlock, h->stream);
                 if (e != cudaSuccess) return cuda_fail(h, e, "multi-step launch");
                 if (m & 1) h->cur = 1 - h->cur;
                 h->gbuf = h->cur;
@@ -1340,8 +1341,17 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     int* oy = static_cast<int*>(tmp.get(size_t(obj->n) * sizeof(int)));
     float* ot = static_cast<float*>(tmp.get(size_t(obj->n) * sizeof(float)));
     float* ow = static_cast<float*>(tmp.get(size_t(obj->n) * sizeof(float)));
+    // multi_step: the valve word of every step t0 .. t0 + n for the reverse kernel
+    const bool coop = h->multi_step > 0;
+    uint32_t* masks_d = coop ? static_cast<uint32_t*>(tmp.get(size_t(n + 1) * sizeof(uint32_t))) : nullptr;
+    int coop_grid = 0;
+    if (coop) {
+        int cps = 0;
+        LBM_CUDA(h, lbm::adjoint_coop_occupancy(&cps));
+        coop_grid = std::max(1, std::min(agrid, std::max(1, cps) * sms));
+    }
     if (!ckpt || (seg_slots > 0 && !seg) || !adj[0] || !adj[1] || !adj[2] || !dn || !gw || !gu || !gc || !dJ ||
-        !rp || !ox || !oy || !ot || !ow)
+        !rp || !ox || !oy || !ot || !ow || (coop && !masks_d))
         return fail(h, LBM_ERR_OOM, "adjoint: device memory for %lld checkpoints and %d recomputed states not available",
                     n_ck, seg_slots);
 
@@ -1363,7 +1373,46 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     a.err = h->err;
     const int64_t t0 = h->step;
     if (lbm_status js = join_scalar(h)) return js;
-    if (K == 1) {
+    a.barrier_extra = h->barrier_extra;
+    // Forward steps t = tstart .. tstart + m - 1 of the run, step t reading
+    // slot (t - tstart) of `from` and writing the next slot (every state
+    // kept); with multi_step, runs of unchanged valve words go to the
+    // cooperative kernel.
+    auto forward_slots = [&](lbm::StepArgs& x, float* from, int64_t tstart, int64_t m) -> lbm_status {
+        const long long stride = (long long)(S / sizeof(float));
+        for (int64_t s = 0; s < m;) {
+            const int64_t run = coop ? h->mask_run(t0 + tstart + s, std::min<int64_t>(m - s, h->multi_step)) : 1;
+            x.open_mask[0] = h->mask_at(t0 + tstart + s);
+            x.reverse = int((tstart + s) & 1);
+            x.src = from + s * stride;
+            cudaError_t e;
+            if (run >= 2) {
+                e = lbm::launch_steps_coop(x, int(run), stride, h->bar, h->coop_grid, kDefaultRegsBlock, st);
+            } else {
+                x.dst = from + (s + 1) * stride;
+                e = lbm::launch_step(x, h->launch, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(h, e, "forward step launch");
+            s += std::max<int64_t>(run, 1);
+        }
+        return LBM_OK;
+    };
+    if (K == 1 && coop) {
+        // every state kept, runs of steps in cooperative launches; the last
+        // step writes into the other buffer
+        LBM_CUDA(h, cudaMemcpyAsync(ckpt, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
+        if (lbm_status fs = forward_slots(a, reinterpret_cast<float*>(ckpt), 0, n - 1)) return fs;
+        a.src = reinterpret_cast<float*>(ckpt + size_t(n - 1) * S);
+        a.dst = h->pop[1 - h->cur];
+        a.reverse = int((n - 1) & 1);
+        a.open_mask[0] = h->mask_at(t0 + n - 1);
+        cudaError_t e = lbm::launch_step(a, h->launch, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+        h->cur = 1 - h->cur;
+        h->gbuf = h->cur;
+        h->diag_grid = h->launch.grid;
+        h->step += n;
+    } else if (K == 1) {
         // every state kept: the steps write straight into the state array
         // (no copies, no recomputation), the last one into the other buffer
         LBM_CUDA(h, cudaMemcpyAsync(ckpt, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
@@ -1407,6 +1456,13 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     LBM_CUDA(h, cudaMemsetAsync(gu, 0, size_t(2) * h->ny * sizeof(double), st));
     LBM_CUDA(h, cudaMemsetAsync(gc, 0, size_t(2) * h->ny * sizeof(double), st));
     LBM_CUDA(h, cudaMemsetAsync(dn, 0, size_t(2) * h->ny * sizeof(float), st));
+    std::vector<uint32_t> masks_h;
+    if (coop) {
+        masks_h.resize(size_t(n + 1));
+        for (int64_t t = 0; t <= n; ++t) masks_h[size_t(t)] = h->mask_at(t0 + t);
+        LBM_CUDA(h, cudaMemcpyAsync(masks_d, masks_h.data(), masks_h.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                    st));
+    }
     {
         cudaError_t e = lbm::launch_adjoint_seed(h->pop[h->cur], h->plane, h->pitch, ox, oy, ot, ow, obj->n, adj[0],
                                                  dJ, st);
@@ -1431,37 +1487,78 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     A.grad_w = gw;
     A.grad_u = gu;
     A.grad_c = gc;
+    A.err = h->err;
+    A.barrier_extra = h->barrier_extra;
     lbm::StepArgs r = a;
     r.partials = rp;  // keep the diagnostics of the last forward step
     // adj[0] holds A(n); M(t) alternates between adj[1] and adj[2]
     int mid = 0;  // 0 before the first reverse step, else adj[mid] holds M(t+1)
-    for (long long sg = n_ck - 1; sg >= 0; --sg) {
+    // One reverse step t (state `state`): the first one reads A(n), the
+    // others gather M(t + 1).
+    auto reverse_one = [&](int64_t t, const float* state) -> lbm_status {
+        A.state = state;
+        A.adj_next = adj[0];
+        A.mid_next = mid ? adj[mid] : nullptr;
+        A.adj_mid = adj[mid == 1 ? 2 : 1];
+        A.open_mask = h->mask_at(t0 + t);
+        A.open_mask_next = h->mask_at(t0 + t + 1);
+        A.reverse = int((n - 1 - t) & 1);
+        cudaError_t e = lbm::launch_adjoint_step(A, mid == 0, agrid, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
+        mid = mid == 1 ? 2 : 1;
+        return LBM_OK;
+    };
+    // Reverse steps t_hi down to t_lo (all after the first), the state of
+    // step t at state_lo + (t - t_lo) slots, in cooperative launches of at
+    // most multi_step steps.
+    auto reverse_coop = [&](int64_t t_hi, int64_t t_lo, const float* state_lo) -> lbm_status {
+        const long long stride = (long long)(S / sizeof(float));
+        for (int64_t hi = t_hi; hi >= t_lo;) {
+            const int64_t lo = std::max<int64_t>(t_lo, hi - h->multi_step + 1);
+            A.reverse = int((n - 1 - hi) & 1);
+            cudaError_t e = lbm::launch_adjoint_steps_coop(A, int(hi - lo), 0, state_lo + (lo - t_lo) * stride, stride,
+                                                           masks_d + lo, adj[mid], adj[3 - mid], h->bar, coop_grid,
+                                                           st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "multi-step adjoint launch");
+            if ((hi - lo + 1) & 1) mid = 3 - mid;
+            hi = lo - 1;
+        }
+        return LBM_OK;
+    };
+    if (coop && K == 1) {
+        // every state kept: the first reverse step, then all others in
+        // cooperative launches
+        if (lbm_status rs = reverse_one(n - 1, reinterpret_cast<float*>(ckpt + size_t(n - 1) * S))) return rs;
+        if (n >= 2)
+            if (lbm_status rs = reverse_coop(n - 2, 0, reinterpret_cast<float*>(ckpt))) return rs;
+    }
+    for (long long sg = n_ck - 1; sg >= 0 && !(coop && K == 1); --sg) {
         const int64_t s0 = sg * K;
         const int len = int(std::min<int64_t>(K, n - s0));
         auto state = [&](int j) -> float* {
             return reinterpret_cast<float*>(j == 0 ? ckpt + size_t(sg) * S : seg + size_t(j - 1) * S);
         };
-        for (int j = 1; j < len; ++j) {
-            r.src = state(j - 1);
-            r.dst = state(j);
-            r.reverse = j & 1;
-            r.open_mask[0] = h->mask_at(t0 + s0 + j - 1);
+        // recompute the segment's states 1 .. len - 1 from its checkpoint
+        if (len >= 2) {
+            r.src = state(0);
+            r.dst = state(1);
+            r.reverse = 1;
+            r.open_mask[0] = h->mask_at(t0 + s0);
             cudaError_t e = lbm::launch_step(r, h->launch, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "recompute step launch");
+            if (lbm_status fs = forward_slots(r, state(1), s0 + 1, len - 2)) return fs;
         }
-        for (int j = len - 1; j >= 0; --j) {
-            const int64_t t = s0 + j;
-            A.state = state(j);
-            A.adj_next = adj[0];
-            A.mid_next = mid ? adj[mid] : nullptr;
-            A.adj_mid = adj[mid == 1 ? 2 : 1];
-            A.open_mask = h->mask_at(t0 + t);
-            A.open_mask_next = h->mask_at(t0 + t + 1);
-            A.reverse = int((n - 1 - t) & 1);
-            cudaError_t e = lbm::launch_adjoint_step(A, mid == 0, agrid, st);
-            if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step launch");
-            mid = mid == 1 ? 2 : 1;
+        int j_hi = len - 1;
+        if (mid == 0) {  // the first reverse step of the sweep
+            if (lbm_status rs = reverse_one(s0 + j_hi, state(j_hi))) return rs;
+            --j_hi;
         }
+        if (coop && j_hi >= 1) {
+            if (lbm_status rs = reverse_coop(s0 + j_hi, s0 + 1, state(1))) return rs;
+            j_hi = 0;
+        }
+        for (int j = j_hi; j >= 0; --j)
+            if (lbm_status rs = reverse_one(s0 + j, state(j))) return rs;
     }
     {
         cudaError_t e = lbm::launch_sum_doubles(gw, agrid, dJ + 1, st);

@@ -109,6 +109,8 @@ struct AdjointArgs {
     double* grad_w;         // one running sum of dJ/d(1/tau_g) per block
     double* grad_u;         // 2*ny running sums of dJ/du_in
     double* grad_c;         // 2*ny running sums of dJ/dC_in
+    unsigned* err;          // error word: bit 1 set when a grid barrier of the multi-step kernel timed out
+    unsigned barrier_extra; // test hook (see StepArgs)
 };
 
 // Threads per block of the reverse-step kernels; the fused one keeps A(t+1)
@@ -120,6 +122,15 @@ cudaError_t adjoint_occupancy(int* blocks_per_sm);
 // first: the first reverse step (A(n) from adj_next); else the fused step
 // (A(t+1) gathered from mid_next)
 cudaError_t launch_adjoint_step(const AdjointArgs& a, bool first, int grid, cudaStream_t s);
+// Reverse steps j_hi .. j_lo (descending, all fused) in one cooperative
+// launch of `grid` blocks (<= the occupancy times the SMs): state of step j
+// at state_lo + (j - j_lo) stride, valve words masks[0 .. j_hi - j_lo + 1],
+// M(j_hi + 1) in mid_a on entry; M(j_lo) ends in mid_a if the step count is
+// even, else in mid_b.  count: a device word for the barrier (zeroed here).
+cudaError_t launch_adjoint_steps_coop(const AdjointArgs& a, int j_hi, int j_lo, const float* state_lo,
+                                      long long stride, const uint32_t* masks, float* mid_a, float* mid_b,
+                                      unsigned* count, int grid, cudaStream_t s);
+cudaError_t adjoint_coop_occupancy(int* blocks_per_sm);
 cudaError_t launch_adjoint_seed(const float* state, long long plane, int pitch, const int* ox, const int* oy,
                                 const float* target, const float* weight, int n, float* adj, double* J,
                                 cudaStream_t s);
@@ -183,10 +194,13 @@ cudaError_t prepare_walls_kernels();
 cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s);
 // n coupled steps (FP32 storage, halfway bounce-back) in one cooperative
 // launch of `grid` blocks of `block` threads, all resident (grid <= the
-// occupancy times the SMs): src holds time t, the result of t + n ends in
-// src if n is even, else in dst.  count: a device word for the grid barrier
-// (zeroed here).  The valve words of a.open_mask hold for all n steps.
-cudaError_t launch_steps_coop(const StepArgs& a, int n, unsigned* count, int grid, int block, cudaStream_t s);
+// occupancy times the SMs): src holds time t; with seq_stride = 0 the result
+// of t + n ends in src if n is even, else in dst; with seq_stride > 0 (in
+// floats) step s writes src + (s + 1) seq_stride (every state kept, dst
+// unused).  count: a device word for the grid barrier (zeroed here).  The
+// valve words of a.open_mask hold for all n steps.
+cudaError_t launch_steps_coop(const StepArgs& a, int n, long long seq_stride, unsigned* count, int grid, int block,
+                              cudaStream_t s);
 cudaError_t steps_coop_occupancy(int block, int* blocks_per_sm);
 cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm);
 

@@ -64,13 +64,16 @@ __global__ void diag_finish(const double* partials, int n_blocks, double* out)
 }
 
 // Many steps in one cooperative launch (every block resident): the register
-// variant's tile loop once per step, the two buffers swapping roles, and a
-// grid-wide barrier between steps in place of the launch boundary.  Loads go
+// variant's tile loop once per step, the two buffers swapping roles (or,
+// with seq_stride > 0, step s reading src + s seq_stride and writing the
+// next slot), and a grid-wide barrier between steps in place of the launch
+// boundary.  Loads go
 // through L2 (F32Coherent): each step reads what other blocks wrote in the
 // step before.  The valve words are those of a.open_mask for all n steps;
 // the diagnostics partials are those of the last step.  A barrier that
 // times out stops the kernel with bit 1 of the error word set.
-__global__ void __launch_bounds__(256, 2) coupled_steps_coop(const StepArgs a, int n, unsigned* count)
+__global__ void __launch_bounds__(256, 2) coupled_steps_coop(const StepArgs a, int n, long long seq_stride,
+                                                             unsigned* count)
 {
     using T = F32Coherent;
     const int lane = threadIdx.x & 31;
@@ -80,8 +83,9 @@ __global__ void __launch_bounds__(256, 2) coupled_steps_coop(const StepArgs a, i
     LaneDiag diag;
     bool bad = false;
     for (int s = 0; s < n; ++s) {
-        const T* __restrict__ S = reinterpret_cast<const T*>((s & 1) ? a.dst : a.src);
-        T* __restrict__ D = reinterpret_cast<T*>((s & 1) ? const_cast<float*>(a.src) : a.dst);  // both buffers are written
+        float* const src = const_cast<float*>(a.src);  // both buffers are written
+        const T* __restrict__ S = reinterpret_cast<const T*>(seq_stride ? src + s * seq_stride : (s & 1) ? a.dst : src);
+        T* __restrict__ D = reinterpret_cast<T*>(seq_stride ? src + (s + 1) * seq_stride : (s & 1) ? src : a.dst);
         const int rev = a.reverse ^ (s & 1);
         diag = LaneDiag();
         for (int t = blockIdx.x * wpb + warp; t < a.n_tiles; t += stride)
@@ -437,7 +441,8 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_steps_coop(const StepArgs& a, int n, unsigned* count, int grid, int block, cudaStream_t s)
+cudaError_t launch_steps_coop(const StepArgs& a, int n, long long seq_stride, unsigned* count, int grid, int block,
+                              cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -450,7 +455,7 @@ cudaError_t launch_steps_coop(const StepArgs& a, int n, unsigned* count, int gri
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, coupled_steps_coop, a, n, count);
+    e = cudaLaunchKernelEx(&cfg, coupled_steps_coop, a, n, seq_stride, count);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -142,6 +142,32 @@ def test_adjoint_keeping_every_state_equals_checkpointed():
     assert np.allclose(u1, u2, rtol=1e-9, atol=0) and np.allclose(c1, c2, rtol=1e-9, atol=0)
 
 
+@pytest.mark.parametrize("K,multi_step", [(1, 16), (1, 1000), (13, 5), (250, 64)])
+def test_adjoint_with_multi_step_launches_equals_single_launches(K, multi_step):
+    """Forward sweep, recomputation and reverse sweep in cooperative
+    multi-step launches (runs split by valve switches every 30 steps and by
+    the run cap) against one launch per step: the same populations, J
+    identical and the gradients equal up to the order of their FP64 sums;
+    both against the FP64 oracle adjoint."""
+    prob = W.config_large_chip(256, 128)
+    prob["period"] = 30
+    obj = _objective(prob)
+    res = []
+    for ms in (0, multi_step):
+        c = lbm.Chip.from_problem(prob, multi_step=ms)
+        c.set_valve_schedule(prob["period"], prob["states"])
+        res.append(c.adjoint(97, obj[0], obj[1], obj[2], obj[3], ckpt_every=K))
+        res.append(c.populations())
+        c.close()
+    (J1, t1, u1, c1), (f1, g1), (J2, t2, u2, c2), (f2, g2) = res
+    assert np.array_equal(f1, f2) and np.array_equal(g1, g2)
+    assert J1 == J2
+    assert abs(t1 - t2) <= 1e-6 * abs(t1)
+    assert _rel(u2, u1) < 1e-6 and _rel(c2, c1) < 1e-6
+    masks = [W.valve_word(prob, t) for t in range(97)]
+    _check((J2, t2, u2, c2), oracle.from_problem(prob).adjoint(97, masks, *obj))
+
+
 def test_adjoint_rejects_bad_objectives():
     prob = W.config_large_chip(96, 48)
     chip = lbm.Chip.from_problem(prob)
