@@ -586,7 +586,8 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB of populations per copy)"
                              % (info["pitch"] * prob["ny"] * 14 * (4 if args.precision == "fp32" else 2) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "launch": {"variant": {1: "registers", 2: "bulk-copy pipeline", 3: "self-refilling pipeline"}[
+                       "launch": {"variant": {1: "registers", 2: "bulk-copy pipeline", 3: "self-refilling pipeline",
+                                              4: "registers + async-copy prefetch"}[
                                       info["variant"]],
                                   "grid": info["grid"], "block": info["block"],
                                   "stages": info["stages"], "tiles": info["n_tiles"]}},

@@ -115,12 +115,15 @@ typedef struct {
     lbm_alloc_fn alloc;     /* NULL = cudaMalloc */
     lbm_free_fn free;       /* NULL = cudaFree */
     void* alloc_user;
-    int32_t block_threads;  /* register variant: block size, 0 = default (128), else 64..256, a multiple of 32 */
+    int32_t block_threads;  /* register variants (1, 4): block size, 0 = default (128), else 64..256, a multiple of 32 */
     int32_t max_blocks;     /* step kernel grid cap: 0 = one wave of resident blocks */
-    int32_t variant;        /* step kernel: 0 = default (1),
+    int32_t variant;        /* step kernel: 0 = default (1 with FP32 storage or the paper's walls,
+                               4 with 16-bit storage),
                                1 = registers and warp shuffles,
                                2 = bulk-copy pipeline through shared memory with a producer warp,
-                               3 = bulk-copy pipeline in which every warp refills its own stages */
+                               3 = bulk-copy pipeline in which every warp refills its own stages,
+                               4 = registers, each warp's next tile prefetched into shared memory
+                                   by per-lane asynchronous copies (halfway bounce-back only) */
     int32_t pipeline_stages;/* variants 2, 3: shared-memory stages per computing warp, 0 = default
                                (1, or 2 with 16-bit storage);
                                computing warps x stages <= 24 */

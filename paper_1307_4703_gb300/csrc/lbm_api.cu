@@ -411,8 +411,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         return fail(nullptr, LBM_ERR_ARG, "block_threads = %d: use 0 or a multiple of 32 in [64, 256]",
                     opt.block_threads);
     if (opt.max_blocks < 0) return fail(nullptr, LBM_ERR_ARG, "max_blocks = %d < 0", opt.max_blocks);
-    if (opt.variant < 0 || opt.variant > 3)
-        return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1, 2 or 3", opt.variant);
+    if (opt.variant < 0 || opt.variant > 4)
+        return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1, 2, 3 or 4", opt.variant);
     if (opt.precision != LBM_FP32 && opt.precision != LBM_FP16 && opt.precision != LBM_BF16)
         return fail(nullptr, LBM_ERR_ARG, "precision = %d: use LBM_FP32, LBM_FP16 or LBM_BF16", opt.precision);
     if (opt.precision != LBM_FP32 && opt.variant == 3)
@@ -437,6 +437,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (opt.wall_scheme != LBM_WALL_BOUNCE_BACK && opt.wall_scheme != LBM_WALL_EQUILIBRIUM)
         return fail(nullptr, LBM_ERR_ARG, "wall_scheme = %d: use LBM_WALL_BOUNCE_BACK or LBM_WALL_EQUILIBRIUM",
                     opt.wall_scheme);
+    if (opt.wall_scheme == LBM_WALL_EQUILIBRIUM && opt.variant == 4)
+        return fail(nullptr, LBM_ERR_ARG, "wall_scheme = LBM_WALL_EQUILIBRIUM runs variants 1 and 2, not 4");
     if (opt.wall_scheme == LBM_WALL_EQUILIBRIUM && opt.variant == 3)
         return fail(nullptr, LBM_ERR_ARG, "wall_scheme = LBM_WALL_EQUILIBRIUM runs variants 1 and 2, not 3");
     if (!(opt.decay >= 0.0 && opt.decay < 1.0))
@@ -624,10 +626,16 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaDeviceGetAttribute"));
     h->sms = sms;
     lbm::StepLaunch& L = h->launch;
-    // default: the register variant (the fastest with every storage type
-    // since the 16-bit collision runs on the stored deviations)
-    const int variant = opt.variant ? opt.variant : 1;
-    L.variant = variant == 1 ? lbm::kVariantRegs : variant == 3 ? lbm::kVariantPipe : lbm::kVariantBulk;
+    // default: the register variant; with 16-bit storage (issue-bound) its
+    // form with the next tile prefetched by asynchronous copies (the fastest
+    // on each, see profiles)
+    const int variant = opt.variant                                                              ? opt.variant
+                        : opt.precision != LBM_FP32 && opt.wall_scheme == LBM_WALL_BOUNCE_BACK ? 4
+                                                                                                : 1;
+    L.variant = variant == 1   ? lbm::kVariantRegs
+                : variant == 3 ? lbm::kVariantPipe
+                : variant == 4 ? lbm::kVariantAsync
+                               : lbm::kVariantBulk;
     L.precision = opt.precision;
     L.pdl = true;  // consecutive steps overlap launch and set-up with the previous step's tail
     L.walls = opt.wall_scheme == LBM_WALL_EQUILIBRIUM;
@@ -648,6 +656,10 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     } else {
         L.stages = 0;
         L.block = opt.block_threads ? opt.block_threads : kDefaultRegsBlock;
+        if (L.variant == lbm::kVariantAsync) {
+            e = lbm::prepare_step_kernels();
+            if (e != cudaSuccess) return bail(cuda_fail(h, e, "shared-memory attribute"));
+        }
     }
     e = lbm::step_kernel_occupancy(L, &per_sm);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "occupancy query"));
@@ -1707,7 +1719,8 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     if (lbm_status js = join_scalar(h)) return js;
     // candidate shapes: {variant, block (variant 1) or computing warps, stages per computing warp}
     struct Cand { int variant, warps, per; };
-    std::vector<Cand> cands = {{1, 4, 0}, {1, 8, 0}, {2, 2, 1}, {2, 3, 1}, {2, 4, 1}, {2, 2, 2}, {2, 3, 2}, {2, 4, 2}};
+    std::vector<Cand> cands = {{1, 4, 0}, {1, 8, 0}, {4, 2, 0}, {4, 4, 0}, {2, 2, 1}, {2, 3, 1},
+                               {2, 4, 1}, {2, 2, 2}, {2, 3, 2}, {2, 4, 2}};
     if (h->precision == LBM_FP32) cands.push_back({3, 4, 1});
     else cands.push_back({2, 3, 3});
     // trials write to scratch buffers: the state, step count and diagnostics stay as they are
@@ -1756,9 +1769,9 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         L.precision = h->precision;
         L.pdl = true;
         L.walls = h->wallv != nullptr;
-        if (L.walls && c.variant == 3) continue;
-        if (c.variant == 1) {
-            L.variant = lbm::kVariantRegs;
+        if (L.walls && (c.variant == 3 || c.variant == 4)) continue;
+        if (c.variant == 1 || c.variant == 4) {
+            L.variant = c.variant == 1 ? lbm::kVariantRegs : lbm::kVariantAsync;
             L.block = 32 * c.warps;
             L.stages = 0;
         } else if (c.variant == 2) {

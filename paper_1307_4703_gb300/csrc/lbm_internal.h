@@ -36,12 +36,12 @@ constexpr int kBulkMaxThreads = 256;        // bulk variant: at most 7 consumer 
 constexpr int kMaxStages = 24;             // bulk variant: largest shared-memory ring
 constexpr int kMaskWords = 8;              // valve channels per lattice: 32 * kMaskWords
 
-enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3 };
+enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3, kVariantAsync = 4 };
 enum Precision { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 constexpr float kCRef = 0.5f;  // reference concentration of 16-bit scalar storage
 
 struct StepLaunch {
-    int variant;  // kVariantRegs, kVariantBulk or kVariantPipe
+    int variant;  // kVariantRegs, kVariantBulk, kVariantPipe or kVariantAsync
     int grid;
     int block;
     int stages;   // shared-memory stages per block (computing warps x stages per warp)
@@ -173,6 +173,8 @@ cudaError_t launch_velocity_of_state(const float* pop, const uint8_t* links, lon
 
 // Dynamic shared memory of the bulk variant, and the attribute it needs.
 size_t bulk_smem_bytes(int stages, int precision = 0);
+// Dynamic shared memory of the cp.async variant (one stage per warp).
+size_t async_smem_bytes(int block, int precision);
 int bulk_stage_bytes(int precision = 0);
 cudaError_t prepare_step_kernels();
 cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s);

@@ -403,6 +403,16 @@ cudaError_t prepare_step_kernels()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(coupled_step_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(bulk_smem_bytes(kMaxStages)));
+    const int async_max = int(async_smem_bytes(kBulkMaxThreads, kFP32));  // up to 8 warps per block
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(coupled_step_async<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 async_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(coupled_step_async<__half, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 async_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(coupled_step_async<__nv_bfloat16, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, async_max);
     if (e == cudaSuccess) e = prepare_walls_kernels();
     return e;
 }
@@ -430,6 +440,11 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
         const int per = l.stages / (l.block / 32);
         cfg.dynamicSmemBytes = bulk_smem_bytes(l.stages);
         e = cudaLaunchKernelEx(&cfg, coupled_step_pipe, a, per);
+    } else if (l.variant == kVariantAsync) {
+        cfg.dynamicSmemBytes = async_smem_bytes(l.block, l.precision);
+        if (l.precision == kFP16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__half, false>, a);
+        else if (l.precision == kBF16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__nv_bfloat16, false>, a);
+        else e = cudaLaunchKernelEx(&cfg, coupled_step_async<float, false>, a);
     } else if (l.precision == kFP16) {
         e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__half, false>, a);
     } else if (l.precision == kBF16) {
@@ -465,6 +480,12 @@ cudaError_t steps_coop_occupancy(int block, int* blocks_per_sm)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_steps_coop, block, 0);
 }
 
+size_t async_smem_bytes(int block, int precision)
+{
+    const size_t per_warp = precision == kFP32 ? sizeof(AsyncStage<float>) : sizeof(AsyncStage<__half>);
+    return per_warp * size_t(block / 32);
+}
+
 cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s)
 {
     // a programmatic dependent of the step before it, like the steps
@@ -498,6 +519,17 @@ cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm)
     if (l.variant == kVariantPipe)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_pipe, l.block,
                                                              bulk_smem_bytes(l.stages));
+    if (l.variant == kVariantAsync) {
+        const size_t smem = async_smem_bytes(l.block, l.precision);
+        if (l.precision == kFP16)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_async<__half, false>,
+                                                                 l.block, smem);
+        if (l.precision == kBF16)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                                 coupled_step_async<__nv_bfloat16, false>, l.block, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_async<float, false>, l.block,
+                                                             smem);
+    }
     if (l.precision == kFP16)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__half, false>, l.block, 0);
     if (l.precision == kBF16)

@@ -75,6 +75,121 @@ __global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
     block_partials(a, diag);
 }
 
+// ---------------------------------------------------------------------------
+// Variant 4: register variant with the next tile prefetched into shared
+// memory by per-lane asynchronous copies (cp.async)
+// ---------------------------------------------------------------------------
+// Each warp owns one stage: the 14 plane rows of a tile, 128 values each
+// with 4 on both sides for the shifted planes' edge values.  A warp copies
+// its next tile's rows into the stage as soon as it has read the current one
+// into registers, so those loads are in flight while it computes; the copies
+// take no registers, so the 128-register budget and 16 warps per SM stay.
+// Lane l copies its own 4 values of each row it needs (lanes q0 .. q1 of the
+// tile's fluid range, one lane more on each side for the shifted planes);
+// lanes 0 and 31 also copy the neighbouring segments' 4 edge values.
+template <typename T>
+struct AsyncStage {
+    static constexpr int kRow = kTileNodes + 8;  // [4 halo | 128 | 4 halo]
+    T pl[kPlanes][kRow];
+};
+
+template <typename T>
+__device__ __forceinline__ void cp_async_quad(T* dst, const T* src)
+{
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void issue_tile_async(const StepArgs& a, const T* S, long long P, uint2 tile,
+                                                 AsyncStage<T>& st, int lane)
+{
+    const int y = int(tile.x >> kSegBits);
+    const int xs = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
+    const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
+    const long long rC = (long long)y * a.pitch + xs;
+    const long long rS = (long long)(y > 0 ? y - 1 : y) * a.pitch + xs;
+    const long long rN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + xs;
+    const bool own = lane >= q0 && lane <= q1;
+    const bool wide = lane >= q0 - 1 && lane <= q1 + 1;
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int sr = src_row(p), sc = src_col(p);
+        const T* row = S + p * P + (sr == 0 ? rC : sr == 1 ? rS : rN);
+        if (sc == 0 ? own : wide) cp_async_quad(&st.pl[p][4 + 4 * lane], row + 4 * lane);
+        if (sc == 1 && lane == 0 && q0 == 0 && xs > 0) cp_async_quad(&st.pl[p][0], row - 4);
+        if (sc == 2 && lane == 31 && q1 == 31 && xs + kTileNodes < a.pitch)
+            cp_async_quad(&st.pl[p][4 + kTileNodes], row + kTileNodes);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <typename T, bool kWalls>
+__global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const long long P = a.plane;
+    const T* __restrict__ S = reinterpret_cast<const T*>(a.src);
+    T* __restrict__ D = reinterpret_cast<T*>(a.dst);
+    AsyncStage<T>& st = reinterpret_cast<AsyncStage<T>*>(smem)[warp];
+
+    LaneDiag diag;
+    bool bad = false;
+
+    const int stride = gridDim.x * wpb;
+    int t = blockIdx.x * wpb + warp;
+    grid_dependency_sync();
+    uint2 tile = t < a.n_tiles ? tile_at(a.tiles, a.n_tiles, t, a.reverse) : make_uint2(0u, 0u);
+    if (t < a.n_tiles) issue_tile_async(a, S, P, tile, st, lane);
+    for (; t < a.n_tiles; t += stride) {
+        const bool more = t + stride < a.n_tiles;
+        const uint2 next = more ? tile_at(a.tiles, a.n_tiles, t + stride, a.reverse) : make_uint2(0u, 0u);
+        const int y = int(tile.x >> kSegBits);
+        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+        const long long oC = (long long)y * a.pitch + x0;
+        const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
+        const bool act = lk != 0xFFFFFFFFu;
+        // ---- free flight (pull) from the stage: the current tile's copies ----
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        float4 v[kPlanes];
+        if (act) {
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) {
+                const T* row = &st.pl[p][4 + 4 * lane];
+                const float4 c = Codec<T>::lds4(row, 0.f);
+                if (src_col(p) == 0) v[p] = c;
+                else if (src_col(p) == 1) v[p] = make_float4(Codec<T>::lds1(row - 1, 0.f), c.x, c.y, c.z);
+                else v[p] = make_float4(c.y, c.z, c.w, Codec<T>::lds1(row + 4, 0.f));
+            }
+        }
+        __syncwarp();
+        if (more) issue_tile_async(a, S, P, next, st, lane);  // the stage is free again
+        if (act) {
+            bounce_back<T, kWalls>(v, lk, S, P, oC, static_cast<const T*>(a.wallv));
+            const RowBC bw = a.rowbc[y];
+            const RowBC be = a.rowbc[a.ny + y];
+            QuadAcc q;
+            collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p)
+                Codec<T>::st4(D + p * P + oC, v[p], 0.f);
+            bad |= q.bad;
+            diag.add(q);
+        }
+        tile = next;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // nothing in flight at exit
+
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
+    block_partials(a, diag);
+}
+
 // One warp tile of the register variant as a function (the multi-step
 // kernel's body; coupled_step_regs keeps the same code written out, which
 // the register allocator handles without spills): pull, walls, ports,

@@ -89,7 +89,9 @@ def test_population_parity_random_lattices(nx, ny, seed, variant):
                                   dict(variant=2, pipeline_stages=1, consumer_warps=7, max_blocks=3),
                                   dict(variant=2, pipeline_stages=5, consumer_warps=3, max_blocks=7),
                                   dict(variant=3), dict(variant=3, pipeline_stages=3, consumer_warps=8),
-                                  dict(variant=3, pipeline_stages=1, consumer_warps=1, max_blocks=5)])
+                                  dict(variant=3, pipeline_stages=1, consumer_warps=1, max_blocks=5),
+                                  dict(variant=4), dict(variant=4, block_threads=256),
+                                  dict(variant=4, block_threads=64, max_blocks=3)])
 def test_kernel_variants_are_bit_identical(opts):
     """Both step kernels and any pipeline shape run the same arithmetic on
     the same values: identical bits after 300 steps with valve toggles and

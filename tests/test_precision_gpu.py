@@ -189,7 +189,8 @@ def test_large_chip_at_benchmark_launch_shape():
 @pytest.mark.parametrize("opts", [dict(variant=1, block_threads=128),
                                   dict(variant=2, consumer_warps=1, pipeline_stages=1),
                                   dict(variant=2, consumer_warps=7, pipeline_stages=3),
-                                  dict(variant=2, consumer_warps=3, pipeline_stages=2, max_blocks=5)])
+                                  dict(variant=2, consumer_warps=3, pipeline_stages=2, max_blocks=5),
+                                  dict(variant=4), dict(variant=4, block_threads=64, max_blocks=5)])
 def test_16bit_variants_are_bit_identical(prec, opts):
     """Every 16-bit kernel variant and launch shape rounds the same FP32
     values: identical stored bits after 300 steps (a 700-wide lattice whose
@@ -211,6 +212,7 @@ def test_16bit_variants_are_bit_identical(prec, opts):
 def test_16bit_save_load_and_fp32_only_calls(prec):
     prob = W.config_small()
     a = lbm.Chip.from_problem(prob, precision=prec)
+    assert a.info()["variant"] == 4  # the 16-bit default: registers + asynchronous prefetch
     a.set_valve_schedule(prob["period"], prob["states"])
     a.step(120)
     blob = a.save_state()
