@@ -29,12 +29,30 @@ struct NextGlobal {
     __device__ __forceinline__ float operator()(int i, int k) const { return __ldg(p + i * P + k); }
 };
 
-// A(t+1) of a thread's four nodes in shared memory, entry (i, k) at
-// s[(4 i + k) * stride] (stride = threads per block: conflict-free).
-struct NextShared {
-    float* s;
-    int stride;
-    __device__ __forceinline__ float& operator()(int i, int k) const { return s[(4 * i + k) * stride]; }
+// Per-warp stage of M(t+1) for a fused reverse step: plane p holds the row
+// that the transposed free flight pulls plane p from (y + e_y of p), columns
+// xs - 4 .. xs + 131 of the tile's segment starting at xs.
+struct MidStage {
+    float pl[kPlanes][kTileNodes + 8];
+};
+
+// Row (0 centre, 1 y - 1, 2 y + 1) and column (0 own, 1 x - 1, 2 x + 1) of
+// the transposed free flight's source for plane p: x + e_p.
+__device__ __forceinline__ constexpr int rev_row(int p) { return src_row(p) == 0 ? 0 : 3 - src_row(p); }
+__device__ __forceinline__ constexpr int rev_col(int p) { return src_col(p) == 0 ? 0 : 3 - src_col(p); }
+__device__ __forceinline__ constexpr int col_shift(int c) { return c == 1 ? -1 : c == 2 ? 1 : 0; }
+
+// A(t+1) of a lane's four nodes from the stage: entry (i, k) sits at column
+// 4 + 4 lane + k + (shift of plane i).  Each entry is the source of exactly
+// one (plane, node), so a lane may overwrite its own entries (bounce-back
+// links, do-nothing terms) without affecting any other lane.
+struct NextStage {
+    MidStage* st;
+    int lane;
+    __device__ __forceinline__ float& operator()(int i, int k) const
+    {
+        return st->pl[i][4 + 4 * lane + k + col_shift(rev_col(i))];
+    }
 };
 
 // Transpose of the collision and of the port completion for the four nodes
@@ -255,13 +273,37 @@ __device__ __forceinline__ void complete_quad(float4 (&x)[kPlanes], const QuadPo
     }
 }
 
-// A(t+1) = F^T M(t+1) for an active lane, v holding M(t+1) pulled from
-// x + e_i: a bounce-back link of direction i (the pull source of opp(i) is
-// not fluid) returns the node's own opposite entry; at an open pressure-port
-// node the scalar population with e_x = s gets the do-nothing term of step
-// t+1; solid nodes are zero.
-// kCoherent: M(t+1) and dn were written by other blocks of the same launch
-// (the multi-step kernel), so they are read through L2.
+// Copies of M(t+1) for the tile into the warp's stage (cp.async, 16 bytes a
+// lane and row, through L2): lane l copies its own 4 values of each row it
+// needs (lanes q0 .. q1 of the tile's fluid range, one more on each side for
+// the shifted planes), lanes 0 and 31 the neighbouring segments' 4 edge
+// values.  Only values that some fluid node of the tile pulls are used.
+__device__ __forceinline__ void issue_mid(const AdjointArgs& A, const QuadPos& q, uint2 tile, MidStage& st, int lane)
+{
+    const long long P = A.plane;
+    const int xs = q.x0 - 4 * lane;
+    const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
+    const bool own = lane >= q0 && lane <= q1;
+    const bool wide = lane >= q0 - 1 && lane <= q1 + 1;
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int sr = rev_row(p), sc = rev_col(p);
+        const float* row = A.mid_next + p * P + (sr == 0 ? q.oC : sr == 1 ? q.oS : q.oN) - 4 * lane;
+        if (sc == 0 ? own : wide) cp_async16(&st.pl[p][4 + 4 * lane], row + 4 * lane);
+        if (sc == 1 && lane == 0 && q0 == 0 && xs > 0) cp_async16(&st.pl[p][0], row - 4);
+        if (sc == 2 && lane == 31 && q1 == 31 && xs + kTileNodes < A.pitch)
+            cp_async16(&st.pl[p][4 + kTileNodes], row + kTileNodes);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// A(t+1) = F^T M(t+1) in the stage, once its copies have landed: a
+// bounce-back link of direction i (the pull source of opp(i) is not fluid)
+// takes the node's own opposite entry of M(t+1) (from global memory, only
+// next to walls); at an open pressure-port node the scalar population with
+// e_x = s gets the do-nothing term of step t+1.  kCoherent: M(t+1) and dn
+// were written by other blocks of the same launch (the multi-step kernel),
+// so they are read through L2.
 template <bool kCoherent>
 __device__ __forceinline__ float4 ld4_mid(const float* p)
 {
@@ -270,7 +312,7 @@ __device__ __forceinline__ float4 ld4_mid(const float* p)
 }
 
 template <bool kCoherent>
-__device__ __forceinline__ void transposed_flight(float4 (&v)[kPlanes], const QuadPos& q, const RowBC& bw,
+__device__ __forceinline__ void transposed_flight(const NextStage& next, const QuadPos& q, const RowBC& bw,
                                                   const RowBC& be, const AdjointArgs& A)
 {
     const long long P = A.plane;
@@ -290,9 +332,10 @@ __device__ __forceinline__ void transposed_flight(float4 (&v)[kPlanes], const Qu
                 const float4 ownc = i <= 4 ? ld4_mid<kCoherent>(M + (9 + o) * P + q.oC) : own;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    if ((q.lk >> (8 * k + o - 1)) & 1u) {
-                        at(v[i], k) = at(own, k);
-                        if (i <= 4) at(v[9 + i], k) = at(ownc, k);
+                    const unsigned lb = (q.lk >> (8 * k)) & 0xFFu;
+                    if (lb != kSolid && ((lb >> (o - 1)) & 1u)) {
+                        next(i, k) = at(own, k);
+                        if (i <= 4) next(9 + i, k) = at(ownc, k);
                     }
                 }
             }
@@ -301,16 +344,13 @@ __device__ __forceinline__ void transposed_flight(float4 (&v)[kPlanes], const Qu
     const uint32_t m = A.open_mask_next;
     const bool dn_w = bw.x >= 0 && ((m >> (bw.chan_kind & 31)) & 1u) && (bw.chan_kind >> 8) == 1;
     const bool dn_e = be.x >= 0 && ((m >> (be.chan_kind & 31)) & 1u) && (be.chan_kind >> 8) == 1;
+    if (dn_w || dn_e) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const unsigned lb = (q.lk >> (8 * k)) & 0xFFu;
-        if (lb == kSolid) {
-#pragma unroll
-            for (int p = 0; p < kPlanes; ++p) at(v[p], k) = 0.f;
-            continue;
+        for (int k = 0; k < 4; ++k) {
+            if (((q.lk >> (8 * k)) & 0xFFu) == kSolid) continue;
+            if (dn_w && bw.x == q.x0 + k) next(10, k) += kCoherent ? __ldcg(A.dn + q.y) : A.dn[q.y];
+            else if (dn_e && be.x == q.x0 + k) next(12, k) += kCoherent ? __ldcg(A.dn + A.ny + q.y) : A.dn[A.ny + q.y];
         }
-        if (dn_w && bw.x == q.x0 + k) at(v[10], k) += kCoherent ? __ldcg(A.dn + q.y) : A.dn[q.y];
-        else if (dn_e && be.x == q.x0 + k) at(v[12], k) += kCoherent ? __ldcg(A.dn + A.ny + q.y) : A.dn[A.ny + q.y];
     }
 }
 
@@ -342,48 +382,41 @@ __global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_collide(const Adjoin
 // one step to the next: the node that reads the entry of step t+1 is the
 // node that then writes the one of step t.
 // One tile of a fused reverse step (the body of adjoint_fused and of the
-// multi-step kernel).
+// multi-step kernel): the copies of M(t+1) into the warp's stage and the
+// loads of P(t) into registers are in flight together; then X, A(t+1) in
+// the stage, K'^T and B^T.
 template <bool kCoherent>
-__device__ __forceinline__ void fused_tile(const AdjointArgs& A, uint2 tile, int lane, const NextShared& next,
-                                           KahanF& dwg)
+__device__ __forceinline__ void fused_tile(const AdjointArgs& A, uint2 tile, int lane, MidStage& st, KahanF& dwg)
 {
     const long long P = A.plane;
     const QuadPos q = quad_pos(A, tile, lane);
-    const RowBC bw = A.rowbc[q.y];
-    const RowBC be = A.rowbc[A.ny + q.y];
-    {
-        float4 v[kPlanes];
-        if constexpr (kCoherent)
-            pull_quad<true>(v, reinterpret_cast<const F32Coherent*>(A.mid_next), P, q.oC, q.oS, q.oN, q.halo_w,
-                            q.halo_e, q.act, q.ld_w, q.ld_e, lane);
-        else
-            pull_quad<true>(v, A.mid_next, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
-        if (q.act) {
-            transposed_flight<kCoherent>(v, q, bw, be, A);
-#pragma unroll
-            for (int p = 0; p < kPlanes; ++p)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) next(p, k) = at(v[p], k);
-        }
-    }
+    issue_mid(A, q, tile, st, lane);
     float4 x[kPlanes];
     pull_quad<false>(x, A.state, P, q.oC, q.oS, q.oN, q.halo_w, q.halo_e, q.act, q.ld_w, q.ld_e, lane);
-    if (!q.act) return;
-    complete_quad(x, q, bw, be, A);
-    collide_adjoint_quad(x, q.lk, q.x0, q.y, q.oC, bw, be, A, next, dwg);
+    const RowBC bw = A.rowbc[q.y];
+    const RowBC be = A.rowbc[A.ny + q.y];
+    if (q.act) complete_quad(x, q, bw, be, A);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const NextStage next{&st, lane};
+    if (q.act) {
+        transposed_flight<kCoherent>(next, q, bw, be, A);
+        collide_adjoint_quad(x, q.lk, q.x0, q.y, q.oC, bw, be, A, next, dwg);
+    }
+    __syncwarp();  // the stage is read before the next tile's copies overwrite it
 }
 
 __global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_fused(const AdjointArgs A)
 {
-    extern __shared__ float next_smem[];
+    extern __shared__ __align__(16) unsigned char next_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const NextShared next{next_smem + threadIdx.x, int(blockDim.x)};
+    MidStage& st = reinterpret_cast<MidStage*>(next_smem)[warp];
     KahanF dwg;
     grid_dependency_sync();
     for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb)
-        fused_tile<false>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, next, dwg);
+        fused_tile<false>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, st, dwg);
     block_add(A.grad_w, dwg.value());
 }
 
@@ -397,11 +430,11 @@ __global__ void __launch_bounds__(kAdjointBlock, 4)
     adjoint_steps_coop(const AdjointArgs A0, int j_hi, int j_lo, const float* state_lo, long long stride,
                        const uint32_t* masks, float* mid_a, float* mid_b, unsigned* count)
 {
-    extern __shared__ float next_smem[];
+    extern __shared__ __align__(16) unsigned char next_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const NextShared next{next_smem + threadIdx.x, int(blockDim.x)};
+    MidStage& st = reinterpret_cast<MidStage*>(next_smem)[warp];
     KahanF dwg;
     for (int j = j_hi, s = 0; j >= j_lo; --j, ++s) {
         AdjointArgs A = A0;
@@ -412,7 +445,7 @@ __global__ void __launch_bounds__(kAdjointBlock, 4)
         A.adj_mid = (s & 1) ? mid_a : mid_b;
         A.reverse = A0.reverse ^ (s & 1);
         for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb)
-            fused_tile<true>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, next, dwg);
+            fused_tile<true>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, st, dwg);
         if (j > j_lo && !grid_barrier(count, unsigned(s + 1) * gridDim.x + A0.barrier_extra, A0.err)) break;
     }
     block_add(A0.grad_w, dwg.value());

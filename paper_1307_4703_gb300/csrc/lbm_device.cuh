@@ -267,6 +267,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
         if (clock64() - t0 > kWaitCycles) return false;
     return true;
 }
+// Per-lane asynchronous global -> shared copy of 16 bytes through L2
+// (cp.async.cg, 16-byte aligned addresses); the lane waits for its copies
+// with cp.async.wait_group, and the warp then syncs to see each other's.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 // Global -> shared bulk copy completing on an mbarrier (16-byte aligned
 // addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)

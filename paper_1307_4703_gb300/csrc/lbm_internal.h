@@ -113,10 +113,13 @@ struct AdjointArgs {
     unsigned barrier_extra; // test hook (see StepArgs)
 };
 
-// Threads per block of the reverse-step kernels; the fused one keeps A(t+1)
-// of its threads' nodes in shared memory (14 planes x 4 nodes x 4 B each).
+// Threads per block of the reverse-step kernels; the fused one stages
+// M(t+1) of each warp's tile in shared memory (14 rows of 136 floats a warp).
 constexpr int kAdjointBlock = 128;
-inline size_t adjoint_fused_smem(int block) { return size_t(kPlanes) * 4 * sizeof(float) * size_t(block); }
+inline size_t adjoint_fused_smem(int block)
+{
+    return size_t(kPlanes) * (kTileNodes + 8) * sizeof(float) * size_t(block / 32);
+}
 
 cudaError_t adjoint_occupancy(int* blocks_per_sm);
 // first: the first reverse step (A(n) from adj_next); else the fused step

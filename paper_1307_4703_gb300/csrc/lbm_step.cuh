@@ -97,7 +97,7 @@ template <typename T>
 __device__ __forceinline__ void cp_async_quad(T* dst, const T* src)
 {
     if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+        cp_async16(dst, src);
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }

@@ -328,3 +328,20 @@ def test_async_diagnostics_match_the_synchronous_read():
     assert ei.value.status == lbm.LBM_ERR_NUMERIC
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(multi_step=8), dict(precision="fp16")])
+def test_zero_steps_change_nothing(opts):
+    """lbm_step(0) and lbm_scalar_step(0) are no-ops: same stored bytes,
+    same step count, same diagnostics."""
+    prob = W.config_small()
+    chip = lbm.Chip.from_problem(prob, **opts)
+    chip.set_valve_schedule(prob["period"], prob["states"])
+    chip.step(3)
+    before, d0 = chip.save_state(), chip.diagnostics()
+    chip.step(0)
+    if opts.get("precision", "fp32") == "fp32":
+        chip.scalar_step(0, 1.0)
+    assert chip.save_state() == before and chip.step_count() == 3
+    assert np.array_equal(chip.diagnostics(), d0)
+    chip.close()
