@@ -155,7 +155,7 @@ typedef struct {
  * g_i - w_i C_ref with C_ref = 1/2 for the scalar, converted to FP32 on
  * loading and rounded to nearest on storing; this halves the bytes a step
  * moves (56 instead of 112 per fluid node) at the cost of a rounding of
- * every population in every step.  16-bit handles run variants 1 and 2
+ * every population in every step.  16-bit handles run variants 1, 2 and 4
  * (variant 3 is rejected with LBM_ERR_ARG) and support
  * lbm_step, the field, diagnostics and population calls and
  * lbm_save_state / lbm_load_state (which keep the 16-bit values bit for

@@ -416,7 +416,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (opt.precision != LBM_FP32 && opt.precision != LBM_FP16 && opt.precision != LBM_BF16)
         return fail(nullptr, LBM_ERR_ARG, "precision = %d: use LBM_FP32, LBM_FP16 or LBM_BF16", opt.precision);
     if (opt.precision != LBM_FP32 && opt.variant == 3)
-        return fail(nullptr, LBM_ERR_ARG, "precision = %d: 16-bit storage runs variants 1 and 2, not 3",
+        return fail(nullptr, LBM_ERR_ARG, "precision = %d: 16-bit storage runs variants 1, 2 and 4, not 3",
                     opt.precision);
     const int max_cw = opt.variant == 3 ? 8 : 7;
     if (opt.consumer_warps < 0 || opt.consumer_warps > max_cw)

@@ -82,7 +82,7 @@ def _create(lib, nx, ny, mask, tau=0.8, tau_c=0.6, ports=(), edge_u=None, edge_C
     (dict(opt="badsize"), "struct_size"),
     (dict(opt="badblock"), "block_threads"),
     (dict(opt="badprecision"), "precision = 3"),
-    (dict(opt="fp16pipe"), "variants 1 and 2"),
+    (dict(opt="fp16pipe"), "variants 1, 2 and 4"),
     (dict(opt="wallpipe"), "runs variants 1 and 2"),
     (dict(opt="badwall"), "wall_scheme = 2"),
     (dict(opt="badscalar"), "scalar_variant = 3"),
