@@ -46,8 +46,9 @@ def _args():
     p.add_argument("--skip-extras", action="store_true",
                    help="skip the end-to-end and CPU-baseline legs (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
-                   help="step kernel: 0 library default, 1 registers, 2 bulk-copy pipeline")
+    p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                   help="step kernel: 0 library default, 1 registers, 2 bulk-copy pipeline, "
+                        "3 self-refilling pipeline, 4 registers with async-copy prefetch")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                    help="storage of the populations of the timed chip (profiling runs)")
     p.add_argument("--kernel", default="step", choices=["step", "scalar", "adjoint"],
