@@ -86,6 +86,7 @@ def _create(lib, nx, ny, mask, tau=0.8, tau_c=0.6, ports=(), edge_u=None, edge_C
     (dict(opt="wallpipe"), "runs variants 1 and 2"),
     (dict(opt="badwall"), "wall_scheme = 2"),
     (dict(opt="badscalar"), "scalar_variant = 3"),
+    (dict(nx=524161, mask="wide"), "too large"),
     (dict(opt="multifp16"), "multi_step needs FP32"),
     (dict(opt="badmulti"), "multi_step = 70000"),
 ])
@@ -100,6 +101,8 @@ def test_create_rejects_invalid_arguments(lib, case, needle):
     elif m == "isolated":
         mask[:] = 1
         mask[2, 2] = 0
+    elif m == "wide":
+        pass  # all fluid, one node wider than the tile encoding admits
     opt = None
     if case.get("opt"):
         opt = lbm.lbm_options()
@@ -181,3 +184,12 @@ def test_create_reports_the_first_isolated_node_of_a_large_mask(lib):
     st, msg = _create(lib, nx, ny, mask)
     assert st == lbm.LBM_ERR_ARG
     assert "(500, 900)" in msg and "no fluid neighbour" in msg
+
+
+def test_create_rejects_grids_beyond_the_tile_encoding(lib):
+    """Rows are encoded in 19 bits and row segments in 12 (4095 segments of
+    128 nodes); one more row or column than that is rejected before any
+    device call."""
+    for nx, ny in ((4, 1 << 19), (524161, 2)):
+        st, msg = _create(lib, nx, ny, np.zeros((ny, nx), np.uint8))
+        assert st == lbm.LBM_ERR_ARG and "too large" in msg, (nx, ny, msg)

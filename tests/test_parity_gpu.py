@@ -51,7 +51,7 @@ def _field_errors(prob, chip, ref):
     return du, dC, dm
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("nx,ny,seed", [(8, 8, 1), (17, 9, 2), (64, 32, 3), (130, 12, 4),
                                         (300, 20, 5), (129, 16, 6), (300, 20, 7), (260, 8, 5)])
 def test_population_parity_random_lattices(nx, ny, seed, variant):
@@ -344,4 +344,30 @@ def test_zero_steps_change_nothing(opts):
         chip.scalar_step(0, 1.0)
     assert chip.save_state() == before and chip.step_count() == 3
     assert np.array_equal(chip.diagnostics(), d0)
+    chip.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(524160, 3), (4, 524287)])
+def test_largest_width_and_height(nx, ny):
+    """The largest lattices the tile encoding admits (4095 segments of 128
+    nodes in a row; 2^19 - 1 rows): a closed box (every edge a wall) from
+    random fields near rest, two steps, every population against the
+    oracle.  Exercises the last segment index and the last row in the tile
+    table, the row clamping at both edges and the halos at the last
+    segment."""
+    r = W.rng(77)
+    prob = {"solid": np.zeros((ny, nx), np.uint8), "tau": 0.7, "tau_c": 0.6, "ports": [],
+            "edge_u": np.zeros((2, ny)), "edge_C": np.zeros((2, ny)), "w0": 1.0 / 3.0, "u_max": 0.05}
+    init = {"rho": 1.0 + 0.01 * (r.random((ny, nx)) - 0.5), "ux": 0.04 * (r.random((ny, nx)) - 0.5),
+            "uy": 0.04 * (r.random((ny, nx)) - 0.5), "C": r.random((ny, nx))}
+    chip = lbm.Chip.from_problem(prob)
+    ref = oracle.from_problem(prob)
+    chip.init_equilibrium(**init)
+    ref.init_equilibrium(**init)
+    for _ in range(2):
+        chip.step(1)
+        ref.step(0)
+    f, g = chip.populations()
+    rf, rg = _oracle_pops(ref)
+    assert np.abs(f - rf).max() <= POP_ATOL and np.abs(g - rg).max() <= POP_ATOL
     chip.close()
