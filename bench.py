@@ -177,6 +177,14 @@ def _cpu_baseline(seconds):
                       "(%d fluid nodes), %.1f s" % (n, fluid, dt)}
 
 
+def _workload_config(prob, precision):
+    """The `config` keys that name the workload (both arms)."""
+    from paper_1307_4703_gb300 import workloads as W
+    return {"workload": "%s two-channel gradient chip, %s populations" % (prob["name"], precision.upper()),
+            "nx": prob["nx"], "ny": prob["ny"], "fluid_nodes": W.fluid_count(prob),
+            "tau": prob["tau"], "tau_c": prob["tau_c"], "valve_period": prob["period"]}
+
+
 def _reference(args):
     """The reference arm: the oracle, as it stands, on the host cores."""
     import oracle
@@ -200,8 +208,7 @@ def _reference(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": prob["name"] + " (sample of chip-4096x2048)", "nx": prob["nx"],
-                       "ny": prob["ny"], "fluid_nodes": fluid},
+            "config": _workload_config(W.config_large_chip(), "fp32"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -580,10 +587,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%s two-channel gradient chip, %s populations"
-                                   % (prob["name"], args.precision.upper()),
-                       "nx": prob["nx"], "ny": prob["ny"], "fluid_nodes": fluid,
-                       "tau": prob["tau"], "tau_c": prob["tau_c"], "valve_period": prob["period"],
+            "config": dict(_workload_config(prob, args.precision), **{
                        "l2": "inputs larger than L2 (%.2f GB of populations per copy)"
                              % (info["pitch"] * prob["ny"] * 14 * (4 if args.precision == "fp32" else 2) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU",
@@ -591,7 +595,7 @@ def main():
                                               4: "registers + async-copy prefetch"}[
                                       info["variant"]],
                                   "grid": info["grid"], "block": info["block"],
-                                  "stages": info["stages"], "tiles": info["n_tiles"]}},
+                                  "stages": info["stages"], "tiles": info["n_tiles"]}}),
             "all_node_glups": ws * prob["nx"] * prob["ny"] * args.steps / (ms / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
