@@ -293,6 +293,7 @@ def _reduced_precision(prob, steps, stream, device, peak):
     """The same coupled step with 16-bit population storage (FP16 and BF16
     deviations, FP32 arithmetic): 56 bytes per fluid node and step.  Device
     time over `steps` single-step calls after 50 warm-up steps."""
+    import numpy as np
     import torch
     from paper_1307_4703_gb300 import lbm, workloads as W
     fluid = W.fluid_count(prob)
@@ -319,13 +320,32 @@ def _reduced_precision(prob, steps, stream, device, peak):
                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                   "frac": achieved / peak,
                                   "bytes_per_launch": info["algorithmic_bytes_per_step"]}}
+    # accuracy: the fields after 1000 steps of the 512 x 256 copy of the chip
+    # against the same run with FP32 storage (which matches the FP64 oracle
+    # to 1e-6, tested)
+    small = W.config_large_chip(512, 256)
+    fields = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        chip = lbm.Chip.from_problem(small, stream=stream, torch_alloc=True, device=device, precision=prec)
+        chip.set_valve_schedule(small["period"], small["states"])
+        chip.step(1000)
+        fields[prec] = chip.fields()
+        chip.close()
+    fl = ~np.asarray(small["solid"], bool)
+    for prec in ("fp16", "bf16"):
+        du = max(np.abs(fields[prec][k] - fields["fp32"][k])[fl].max() for k in (1, 2)) / small["u_max"]
+        dC = np.abs(fields[prec][3] - fields["fp32"][3])[fl].max()
+        out[prec]["accuracy"] = {"max_du_over_u_max": float(du), "max_dC": float(dC),
+                                 "against": "FP32 storage, chip-512x256 copy, 1000 steps"}
     return out
 
 
 def _batch(steps, stream, device, peak, n_chips=64):
     """64 independent chips of 256 x 128 ... 1024 x 512 (seeded sizes,
     relaxation times and valve periods): all in one handle, one launch per
-    step, against the same chips stepped one handle after another."""
+    step; the same handle autotuned with CUDA graphs of 100 steps, and with
+    runs of up to 1000 steps in one persistent cooperative launch
+    (multi_step); against the same chips stepped one handle after another."""
     import torch
     from paper_1307_4703_gb300 import lbm, workloads as W
     chips = W.config_batch(n_chips)
@@ -350,6 +370,20 @@ def _batch(steps, stream, device, peak, n_chips=64):
     info = batch.info()
     batch.diagnostics()
     batch.close()
+    modes = {}
+    for key, kw in (("graphs_100_autotuned", {"graph_steps": 100}), ("multi_step_1000", {"multi_step": 1000})):
+        b = lbm.Chip.batch(chips, stream=stream, torch_alloc=True, device=device, **kw)
+        for k, p in enumerate(chips):
+            b.set_instance_schedule(k, p["period"], p["states"])
+        if "graph_steps" in kw:
+            b.autotune()
+        b.step(200)
+        b.synchronize()
+        s_mode = timed(lambda: b.step(steps), 1)
+        b.diagnostics()
+        b.close()
+        modes[key] = {"value": fluid * steps / s_mode / 1e9, "unit": UNIT, "steps": steps,
+                      "roofline_frac": info["algorithmic_bytes_per_step"] * steps / s_mode / 1e9 / peak}
     singles = [lbm.Chip.from_problem(p, stream=stream, torch_alloc=True, device=device) for p in chips]
     for c, p in zip(singles, chips):
         c.set_valve_schedule(p["period"], p["states"])
@@ -366,6 +400,7 @@ def _batch(steps, stream, device, peak, n_chips=64):
     achieved = info["algorithmic_bytes_per_step"] * steps / s_batch / 1e9
     return {"value": fluid * steps / s_batch / 1e9, "unit": UNIT, "chips": n_chips, "fluid_nodes": fluid,
             "steps": steps, "one_by_one": fluid * n_single / s_single / 1e9, "one_by_one_steps": n_single,
+            **modes,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "bytes_per_launch": info["algorithmic_bytes_per_step"]}}
 
@@ -572,7 +607,7 @@ def main():
     if not args.skip_extras:
         extras["frozen_scalar_step"] = _frozen_scalar(chip, prob, min(args.steps, 2000), stream, peak)
         extras["reduced_precision_storage"] = _reduced_precision(prob, min(args.steps, 5000), stream, local, peak)
-        extras["batch_64_chips"] = _batch(min(args.steps, 2000), stream, local, peak)
+        extras["batch_64_chips"] = _batch(min(args.steps, 10000), stream, local, peak)
         extras["small_chips"] = _small_chips(min(args.steps, 20000), stream, local, peak)
         e2e_steps = min(args.steps, 5000)
         e = _e2e(prob, e2e_steps, local)
