@@ -221,6 +221,37 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// A double-float value hi + lo (the unevaluated sum of two floats).  GB300
+// issues FP64 arithmetic at a small fraction of its FP32 rate, and every warp
+// of a step kernel reduces its diagnostics at the same moment, at the end of
+// the kernel, so a reduction of doubles there leaves the SMs waiting on the
+// FP64 pipe.  The step kernels' reductions add pairs of floats instead, with
+// Knuth's error-free TwoSum on the high parts (about 44 significant bits),
+// and form a double only for each block's final sum.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = a.hi + b.hi;
+    const float bv = s - a.hi;
+    const float e = (a.hi - (s - bv)) + (b.hi - bv);  // s + e = a.hi + b.hi exactly
+    const float lo = e + (a.lo + b.lo);
+    const float hi = s + lo;
+    return {hi, lo - (hi - s)};
+}
+
+__device__ __forceinline__ DF warp_sum(DF v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, DF{__shfl_xor_sync(kFull, v.hi, o), __shfl_xor_sync(kFull, v.lo, o)});
+    return v;
+}
+
+__device__ __forceinline__ double df_value(DF v) { return double(v.hi) + double(v.lo); }
+
 // ---------------------------------------------------------------------------
 // sm_90+ asynchronous bulk copies and mbarriers (inline PTX)
 // ---------------------------------------------------------------------------
@@ -346,6 +377,7 @@ struct KahanF {
         s = t;
     }
     __device__ __forceinline__ double value() const { return double(s) - double(e); }
+    __device__ __forceinline__ DF pair() const { return DF{s, -e}; }
 };
 
 // The lane totals of the four diagnostics.
@@ -646,12 +678,42 @@ __device__ __forceinline__ float2 row_rates(const StepArgs& a, int y)
     return make_float2(r.x, r.y);
 }
 
+// Port completion of node k of the quad (the port rules work on g_i itself,
+// so 16-bit deviations are shifted to g_i around them).  Returns true for an
+// outlet node.
 template <typename T>
+__device__ __forceinline__ bool port_node(float (&f)[9], float (&g)[5], bool west, const RowBC& b,
+                                          const StepArgs& a, const T* S, long long own)
+{
+    constexpr bool kDev = !kStoresF32<T>;
+    if constexpr (kDev) {
+        g[0] += a.gref0;
+#pragma unroll
+        for (int i = 1; i < 5; ++i) g[i] += a.gref1;
+    }
+    const bool outlet = complete_port(f, g, west, b, S, a.plane, own, a.gref1, a.wg1, a.inv_cs2g);
+    if constexpr (kDev) {
+        g[0] -= a.gref0;
+#pragma unroll
+        for (int i = 1; i < 5; ++i) g[i] -= a.gref1;
+    }
+    return outlet;
+}
+
+// Open ports, moments and both collisions of the quad.  Where the rare work
+// goes depends on the storage type, by measurement: the FP32 kernel waits on
+// its loads and is fastest with the port and solid-node handling inside the
+// per-node loop (63.7 us per step on the 4096 x 2048 chip, against 64.9 us
+// with passes); the 16-bit kernels are bound by instruction issue and are
+// fastest with that work in passes over the quad that only quads holding a
+// port or a solid node enter (FP16 50.1 us, against 52.3 us inside the loop).
+// kPasses selects the passes (the multi-step kernel takes them for FP32 too:
+// there they keep its registers from spilling).
+template <typename T, bool kPasses = !kStoresF32<T>>
 __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, int x0, const RowBC& bw,
                                              const RowBC& be, const StepArgs& a, const T* S, long long oC,
                                              float2 omega, QuadAcc& acc)
 {
-    const long long P = a.plane;
     const bool open_w = bw.x >= 0 && valve_open(a, bw.chan_kind);
     const bool open_e = be.x >= 0 && valve_open(a, be.chan_kind);
     const float dfac = a.decay != 0.f ? 1.f - a.decay / omega.y : 1.f;
@@ -661,6 +723,33 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     // on loading or subtracted on storing.  FP32 storage holds g_i itself.
     constexpr bool kDev = !kStoresF32<T>;
 
+    unsigned outlet = 0;  // passes: bit k = node x0 + k is an open outlet (flux diagnostics)
+    if constexpr (kPasses) {
+        // ---- open valve ports (Zou-He; held concentration / do-nothing):
+        //      only the first and last quads of a channel row hold a port
+        //      node (ports are fluid, and never on both sides of a row) ----
+        const int kw = open_w ? bw.x - x0 : -1;
+        const int ke = open_e ? be.x - x0 : -1;
+        if (unsigned(kw) < 4u || unsigned(ke) < 4u) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool pw = k == kw;
+                if (!pw && k != ke) continue;
+                float f[9], g[5];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = at(v[i], k);
+#pragma unroll
+                for (int i = 0; i < 5; ++i) g[i] = at(v[9 + i], k);
+                if (port_node(f, g, pw, pw ? bw : be, a, S, oC + k)) outlet |= 1u << k;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) at(v[i], k) = f[i];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) at(v[9 + i], k) = g[i];
+            }
+        }
+    }
+
+    float rmin = 1.f;  // smallest density of the quad's fluid nodes (passes)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const unsigned lb = (lk >> (8 * k)) & 0xFFu;
@@ -670,31 +759,19 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         for (int i = 0; i < 9; ++i) f[i] = at(v[i], k);
 #pragma unroll
         for (int i = 0; i < 5; ++i) g[i] = at(v[9 + i], k);
-        if (!fluid) {  // solid node: park it at the rest state rho = 1, C = 0
+        bool outlet_k = (outlet >> k) & 1u;
+        if constexpr (!kPasses) {
+            if (!fluid) {  // solid node: park it at the rest state rho = 1, C = 0
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = 0.f;
-            g[0] = kDev ? -a.gref0 : 0.f;
+                for (int i = 0; i < 9; ++i) f[i] = 0.f;
 #pragma unroll
-            for (int i = 1; i < 5; ++i) g[i] = kDev ? -a.gref1 : 0.f;
-        }
-
-        // ---- open valve ports (Zou-He; held concentration / do-nothing) ----
-        const int xk = x0 + k;
-        const bool pw = open_w && bw.x == xk;
-        const bool pe = !pw && open_e && be.x == xk;
-        bool pressure_node = false;
-        if (pw || pe) {  // the port rules work on g_i itself
-            if constexpr (kDev) {
-                g[0] += a.gref0;
-#pragma unroll
-                for (int i = 1; i < 5; ++i) g[i] += a.gref1;
+                for (int i = 0; i < 5; ++i) g[i] = 0.f;
             }
-            pressure_node = complete_port(f, g, pw, pw ? bw : be, S, P, oC + k, a.gref1, a.wg1, a.inv_cs2g);
-            if constexpr (kDev) {
-                g[0] -= a.gref0;
-#pragma unroll
-                for (int i = 1; i < 5; ++i) g[i] -= a.gref1;
-            }
+            // ---- open valve ports ----
+            const int xk = x0 + k;
+            const bool pw = open_w && bw.x == xk;
+            const bool pe = !pw && open_e && be.x == xk;
+            if (pw || pe) outlet_k = port_node(f, g, pw, pw ? bw : be, a, S, oC + k);
         }
 
         // ---- moments (Eq. moments) and BGK collision of f, in deviations
@@ -703,7 +780,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         const float rho = 1.f + rd;
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        const float inv = 1.f / rho;
+        const float inv = __fdividef(1.f, rho);  // fast reciprocal (2 ulp): rho stays near 1
         const float ux = jx * inv, uy = jy * inv;
         const float usq = 1.5f * (ux * ux + uy * uy);
         const float wo = omega.x;
@@ -749,39 +826,76 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
         for (int i = 0; i < 5; ++i) at(v[9 + i], k) = g[i];
 
         if (fluid) {
-            acc.bad |= !(rho > 0.f && rho < INFINITY) || !(fabsf(C) < INFINITY);
+            if constexpr (kPasses) {
+                rmin = fminf(rmin, rho);
+            } else {
+                acc.bad |= !(rho > 0.f && rho < INFINITY) || !(fabsf(C) < INFINITY);
+                ++acc.n;
+            }
             acc.m += rd;
             acc.c += C;
-            ++acc.n;
-            if (pressure_node) {
+            if (outlet_k) {
                 acc.q += jx;  // rho u_x
                 acc.qc += C * ux;
             }
         }
     }
+
+    if constexpr (kPasses) {
+        // a non-finite density or concentration makes its quad sum non-finite
+        acc.bad = !(rmin > 0.f) || !(fabsf(acc.m) < INFINITY) || !(fabsf(acc.c) < INFINITY);
+        // ---- solid nodes: parked at the rest state rho = 1, C = 0 (what
+        //      they computed above from their pulled values is dropped) ----
+        const unsigned sb = ~lk;  // a zero byte marks a solid node
+        // the top bit of each byte of sb that is zero (no carry between bytes)
+        const unsigned solid = ~(((sb & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | sb) & 0x80808080u;
+        acc.n = 4 - __popc(solid);
+        if (solid) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (((lk >> (8 * k)) & 0xFFu) != kSolid) continue;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) at(v[i], k) = 0.f;
+                at(v[9], k) = kDev ? -a.gref0 : 0.f;
+#pragma unroll
+                for (int i = 10; i < 14; ++i) at(v[i], k) = kDev ? -a.gref1 : 0.f;
+            }
+        }
+    }
 }
 
-// The block's partial sums of the four diagnostics (FP64 from here on).
-// The cross-block total is formed on demand by diag_finish.
+// The block's partial sums of the four diagnostics: lanes and warps combined
+// as double-float pairs, the fluid node count as an integer, and one double
+// per diagnostic written.  The cross-block total is formed on demand by
+// diag_finish.
 __device__ __forceinline__ void block_partials(const StepArgs& a, const LaneDiag& d)
 {
-    __shared__ double red[32][4];
+    __shared__ DF red[32][4];
+    __shared__ int red_n[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    double s0 = warp_sum(double(d.n) + d.m.value());
-    double s1 = warp_sum(d.c.value());
-    double s2 = warp_sum(d.q.value());
-    double s3 = warp_sum(d.qc.value());
+    const DF s0 = warp_sum(d.m.pair()), s1 = warp_sum(d.c.pair());
+    DF s2{0.f, 0.f}, s3{0.f, 0.f};
+    if (__any_sync(kFull, (d.q.s != 0.f || d.q.e != 0.f) || (d.qc.s != 0.f || d.qc.e != 0.f))) {  // outlet lanes
+        s2 = warp_sum(d.q.pair());
+        s3 = warp_sum(d.qc.pair());
+    }
+    const int n = __reduce_add_sync(kFull, d.n);
     if (lane == 0) {
         red[warp][0] = s0;
         red[warp][1] = s1;
         red[warp][2] = s2;
         red[warp][3] = s3;
+        red_n[warp] = n;
     }
     __syncthreads();
     if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int w = 0; w < wpb; ++w) s += red[w][threadIdx.x];
-        a.partials[blockIdx.x * 4 + threadIdx.x] = s;
+        DF s = red[0][threadIdx.x];
+        int nb = red_n[0];
+        for (int w = 1; w < wpb; ++w) {
+            s = df_add(s, red[w][threadIdx.x]);
+            nb += red_n[w];
+        }
+        a.partials[blockIdx.x * 4 + threadIdx.x] = (threadIdx.x == 0 ? double(nb) : 0.0) + df_value(s);
     }
 }
 

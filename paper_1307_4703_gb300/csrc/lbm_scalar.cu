@@ -114,18 +114,18 @@ __device__ __forceinline__ void scalar_quad(float4 (&v)[5], unsigned lk, int x0,
 // partials (and the bookkeeping of the slots of the coupled step's grid).
 __device__ __forceinline__ void scalar_partials(const ScalarArgs& a, const KahanF& sc, const KahanF& sq)
 {
-    __shared__ double red[32][2];
+    __shared__ DF red[32][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double s1 = warp_sum(sc.value()), s3 = warp_sum(sq.value());
+    const DF s1 = warp_sum(sc.pair()), s3 = warp_sum(sq.pair());
     if (lane == 0) {
         red[warp][0] = s1;
         red[warp][1] = s3;
     }
     __syncthreads();
     if (threadIdx.x < 2) {
-        double sum = 0.0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
-        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = sum;
+        DF sum = red[0][threadIdx.x];
+        for (int w = 1; w < int(blockDim.x >> 5); ++w) sum = df_add(sum, red[w][threadIdx.x]);
+        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = df_value(sum);
         for (int b = blockIdx.x + gridDim.x; b < a.n_partials; b += gridDim.x)
             a.partials[b * 4 + 1 + 2 * threadIdx.x] = 0.0;
         // blocks beyond the last coupled step's grid hold no fluid partial

@@ -218,7 +218,7 @@ __device__ __forceinline__ void regs_tile(const StepArgs& a, const T* __restrict
         const RowBC bw = a.rowbc[y];
         const RowBC be = a.rowbc[a.ny + y];
         QuadAcc q;
-        collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
+        collide_quad<T, true>(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p)
             Codec<T>::st4(D + p * P + oC, v[p], 0.f);
