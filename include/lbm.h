@@ -238,10 +238,12 @@ lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy,
  * out[0] = sum of rho over fluid nodes, out[1] = sum of C over fluid nodes,
  * out[2] = sum of rho u_x and out[3] = sum of C u_x over the nodes of the
  * PRESSURE ports open during that step.  Each lane of the step kernel sums
- * its nodes in compensated FP32; lanes and blocks are combined in FP64 in a
- * fixed order (run-to-run identical for a given launch shape).  Launches a
- * small reduction kernel and synchronises the stream; returns
- * LBM_ERR_NUMERIC / LBM_ERR_TIMEOUT if the error word is set. */
+ * its nodes in compensated FP32; the lanes of a block are combined as
+ * double-float pairs (about 44 significant bits) into one FP64 partial per
+ * block, and the blocks' partials in FP64, in a fixed order (run-to-run
+ * identical for a given launch shape).  Launches a small reduction kernel
+ * and synchronises the stream; returns LBM_ERR_NUMERIC / LBM_ERR_TIMEOUT if
+ * the error word is set. */
 lbm_status lbm_get_diagnostics(lbm_handle h, double out[4]);
 
 /* The same diagnostics, read without waiting: enqueues the reduction and a
@@ -255,6 +257,20 @@ lbm_status lbm_get_diagnostics(lbm_handle h, double out[4]);
  * lbm_synchronize.  For a driver loop that reads every step's result while
  * the GPU keeps stepping. */
 lbm_status lbm_get_diagnostics_async(lbm_handle h, double* out);
+
+/* Advance n >= 0 coupled time steps like lbm_step, one launch per step
+ * (graph_steps and multi_step do not apply), with each step's diagnostics
+ * (the four values of lbm_get_diagnostics) written to out[4k .. 4k+3] for
+ * the k-th of these steps by the step kernel itself: the last of its blocks
+ * to finish adds up the blocks' partials, in the same order as
+ * lbm_get_diagnostics, so no reduction launch follows the step.  out: 4 n
+ * doubles of device memory, or of page-locked host memory that the device
+ * can address (cudaHostAlloc / cudaMallocHost), owned by the caller and
+ * valid after the stream is synchronised.  LBM_ERR_ARG for NULL or any
+ * other memory (n = 0 touches nothing).  Errors are reported as by
+ * lbm_step.  For a driver loop that reads every step's result while the GPU
+ * keeps stepping. */
+lbm_status lbm_step_diagnostics(lbm_handle h, int64_t n, double* out);
 
 /* Current post-collision populations into HOST arrays: f = 9*nx*ny floats,
  * g = 5*nx*ny floats, layout [i][y][x].  Either may be NULL.  Synchronises. */

@@ -676,7 +676,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->partials_cap = std::max(h->launch.grid, sms * kMaxBlocksPerSM);
     h->diag_grid = h->launch.grid;
     h->partials = static_cast<double*>(dev_alloc(h, size_t(h->partials_cap) * 4 * sizeof(double)));
-    h->err = static_cast<unsigned*>(dev_alloc(h, sizeof(unsigned)));
+    // the error word, then the ticket counter of lbm_step_diagnostics
+    h->err = static_cast<unsigned*>(dev_alloc(h, 2 * sizeof(unsigned)));
     if (h->multi_step > 0) {
         int coop_per_sm = 0;
         e = lbm::steps_coop_occupancy(kDefaultRegsBlock, &coop_per_sm);
@@ -714,7 +715,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         e = cudaMemcpyAsync(h->rates, batch->rates.data(), size_t(ny) * sizeof(float4), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !woff.empty())
         e = cudaMemcpyAsync(h->woff, woff.data(), woff.size() * sizeof(long long), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, 2 * sizeof(unsigned), st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->partials, 0, size_t(h->partials_cap) * 4 * sizeof(double), st);
     if (e == cudaSuccess)
@@ -912,11 +913,11 @@ lbm_status lbm_set_valve_schedule(lbm_handle h, int64_t period, int32_t n, const
     return LBM_OK;
 }
 
-lbm_status lbm_step(lbm_handle h, int64_t n)
+}  // extern "C"
+
+// Arguments of the chip's coupled step that do not change from step to step.
+static lbm::StepArgs step_args(const lbm_ctx* h)
 {
-    if (check_ctx(h)) return LBM_ERR_ARG;
-    if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
-    if (lbm_status js = join_scalar(h)) return js;
     lbm::StepArgs a{};
     a.links = h->links;
     a.rowbc = h->rowbc;
@@ -939,6 +940,17 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
         a.gref0 = h->wg0 * lbm::kCRef;
         a.gref1 = h->wg1 * lbm::kCRef;
     }
+    return a;
+}
+
+extern "C" {
+
+lbm_status lbm_step(lbm_handle h, int64_t n)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
+    if (lbm_status js = join_scalar(h)) return js;
+    lbm::StepArgs a = step_args(h);
     const int G = h->graph_steps;
     for (int64_t k = 0; k < n;) {
         h->mask_words(h->step, a.open_mask);
@@ -984,6 +996,48 @@ lbm_status lbm_step(lbm_handle h, int64_t n)
         h->diag_grid = h->launch.grid;
         ++h->step;
         ++k;
+    }
+    return pending_numeric(h);
+}
+
+// The device address of caller memory the device can write: device memory,
+// or page-locked host memory mapped into the device's address space (null
+// for anything else).
+static double* device_address(double* p)
+{
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged || pa.type == cudaMemoryTypeHost)
+        return static_cast<double*>(pa.devicePointer);
+    return nullptr;
+}
+
+lbm_status lbm_step_diagnostics(lbm_handle h, int64_t n, double* out)
+{
+    if (check_ctx(h)) return LBM_ERR_ARG;
+    if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
+    if (n == 0) return LBM_OK;
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    double* dev = device_address(out);
+    if (!dev) return fail(h, LBM_ERR_ARG, "out must be device memory or page-locked host memory");
+    if (lbm_status js = join_scalar(h)) return js;
+    lbm::StepArgs a = step_args(h);
+    a.diag_ticket = h->err + 1;
+    for (int64_t k = 0; k < n; ++k) {
+        h->mask_words(h->step, a.open_mask);
+        a.src = h->pop[h->cur];
+        a.dst = h->pop[1 - h->cur];
+        a.reverse = h->cur;
+        a.diag_out = dev + 4 * k;  // the step's last block writes the totals here
+        cudaError_t e = launch_full_step(h, a, h->launch, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+        h->cur = 1 - h->cur;
+        h->gbuf = h->cur;
+        h->diag_grid = h->launch.grid;
+        ++h->step;
     }
     return pending_numeric(h);
 }

@@ -864,6 +864,49 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     }
 }
 
+// Totals of the four diagnostics from the partials of n blocks (4 doubles
+// each), in one fixed order whatever block runs it: the block's first 64
+// threads, thread i adding blocks i, i + 64, ... in turn, then the lanes of
+// each of the two warps by shuffles, then the two warps.  Partials written by
+// other blocks of a running grid are read through L2 (ld.global.cg).  Every
+// thread of the block calls this (it has a barrier).
+__device__ __forceinline__ void finish_partials(const double* partials, int n, double* out)
+{
+    __shared__ double red[2][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 64) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < n; b += 64)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[q] += __ldcg(partials + 4 * b + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t[q] = warp_sum(t[q]);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[warp][q] = t[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) out[threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+}
+
+// The totals of a step formed inside it: the last block to finish adds up
+// every block's partials (threadfence reduction: the partials are made
+// visible before the ticket is taken, and the block that draws the last
+// ticket reads them all after it).  Out of line, so that the step kernels
+// carry no more than a call when it is not asked for.
+__device__ __noinline__ void fold_totals(const double* partials, unsigned* ticket, double* out)
+{
+    __shared__ bool last;
+    if (threadIdx.x < 4) __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    finish_partials(partials, gridDim.x, out);
+    if (threadIdx.x == 0) *ticket = 0u;  // every block of this step has taken its ticket
+}
+
 // The block's partial sums of the four diagnostics: lanes and warps combined
 // as double-float pairs, the fluid node count as an integer, and one double
 // per diagnostic written.  The cross-block total is formed on demand by
@@ -897,6 +940,7 @@ __device__ __forceinline__ void block_partials(const StepArgs& a, const LaneDiag
         }
         a.partials[blockIdx.x * 4 + threadIdx.x] = (threadIdx.x == 0 ? double(nb) : 0.0) + df_value(s);
     }
+    if (a.diag_out != nullptr) fold_totals(a.partials, a.diag_ticket, a.diag_out);
 }
 
 }  // namespace

@@ -86,6 +86,10 @@ struct StepArgs {
     float gref0, gref1;     // 16-bit storage: offsets w_0 C_ref and w_1 C_ref of the scalar planes
     unsigned barrier_extra; // multi-step kernel: arrivals its barriers wait for beyond the grid's
                             // (0; a test hook sets 1 so that the bounded wait runs out)
+    double* diag_out;       // non-null: the step's last block to finish also forms the four
+                            // totals of the partials and writes them here (device-addressable)
+    unsigned int* diag_ticket;  // blocks of the step that have written their partials (zero
+                                // between steps: the last block resets it)
 };
 
 // One adjoint step (lbm_adjoint.cu): A(t) from A(t+1) and the state P(t).

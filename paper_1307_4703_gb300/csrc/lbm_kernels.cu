@@ -38,29 +38,13 @@
 
 namespace lbm {
 namespace {
-// Total of the block partials of the last step, in a fixed order (the same
-// bits on every run for a given launch shape).
+// Totals of the block partials of the last step (finish_partials: the same
+// order, and so the same bits, as the step kernels' own in-kernel totals).
 // out may be page-locked host memory (written over the interconnect).
 __global__ void diag_finish(const double* partials, int n_blocks, double* out)
 {
-    __shared__ double red[8][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
     grid_dependency_sync();  // the step kernel before it has written the partials
-    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) t[q] += partials[4 * b + q];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) t[q] = warp_sum(t[q]);
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) red[warp][q] = t[q];
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = s;
-    }
+    finish_partials(partials, n_blocks, out);
 }
 
 // Many steps in one cooperative launch (every block resident): the register
@@ -491,7 +475,7 @@ cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out
     // a programmatic dependent of the step before it, like the steps
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(64);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -121,6 +121,7 @@ SIGNATURES = {
                                              ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_get_diagnostics": (ctypes.c_int, [ctypes.c_void_p, _f64p]),
     "lbm_get_diagnostics_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_step_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lbm_get_populations": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p]),
     "lbm_set_populations": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p]),
     "lbm_init_equilibrium": (ctypes.c_int, [ctypes.c_void_p, _f32p, _f32p, _f32p, _f32p]),
@@ -455,6 +456,13 @@ class Chip:
         doubles, page-locked, e.g. a pinned torch tensor's data_ptr());
         valid after synchronize()."""
         self._check(self._lib.lbm_get_diagnostics_async(self._h, ctypes.c_void_p(int(out_ptr))))
+
+    def step_diagnostics(self, n, out_ptr):
+        """Advance n steps, one launch each, the k-th step's four diagnostics
+        written by the step kernel to out_ptr + 32 k (4 n doubles of device
+        memory or page-locked host memory, e.g. a CUDA or pinned torch
+        tensor's data_ptr()); valid after synchronize()."""
+        self._check(self._lib.lbm_step_diagnostics(self._h, int(n), ctypes.c_void_p(int(out_ptr))))
 
     def info(self):
         i = lbm_info()

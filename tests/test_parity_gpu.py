@@ -330,6 +330,54 @@ def test_async_diagnostics_match_the_synchronous_read():
     b.close()
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(variant=2, pipeline_stages=2, consumer_warps=3),
+                                  dict(variant=4, block_threads=64), dict(precision="fp16"),
+                                  dict(precision="bf16", variant=1), dict(wall_scheme=1)])
+def test_in_kernel_diagnostics_equal_the_reduction_launch(opts):
+    """lbm_step_diagnostics: the step kernel's last block writes the totals
+    of every step (into pinned host memory and into device memory); each row
+    has the same bits as lbm_get_diagnostics after that step (same order of
+    additions), the populations match lbm_step's, and the ticket counter is
+    back at zero after every step (a second run gives the same rows)."""
+    prob, init = W.random_case(41, 300, 48, solid_frac=0.1)
+    prob["states"] = [1, 2, 3, 0]
+    a = lbm.Chip.from_problem(prob, **opts)
+    b = lbm.Chip.from_problem(prob, **opts)
+    for c in (a, b):
+        c.init_equilibrium(**init)
+        c.set_valve_schedule(4, prob["states"])
+    n = 12
+    host = torch.zeros((n, 4), dtype=torch.float64, pin_memory=True)
+    dev = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    a.step_diagnostics(n // 2, host.data_ptr())
+    a.step_diagnostics(n - n // 2, host[n // 2].data_ptr())
+    want = []
+    for k in range(n):
+        b.step(1)
+        want.append(b.diagnostics())
+    a.synchronize()
+    assert np.array_equal(host.numpy(), np.array(want))
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    a.step_diagnostics(n, dev.data_ptr())
+    for k in range(n):
+        b.step(1)
+        want[k] = b.diagnostics()
+    a.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), np.array(want))
+    a.step_diagnostics(0, 0)  # no steps: out is not touched
+    pageable = np.zeros(8)
+    with pytest.raises(lbm.LbmError) as ei:
+        a.step_diagnostics(2, pageable.ctypes.data)
+    assert ei.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError):
+        a.step_diagnostics(1, 0)
+    assert a.step_count() == 2 * n
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("opts", [dict(), dict(multi_step=8), dict(precision="fp16")])
 def test_zero_steps_change_nothing(opts):
     """lbm_step(0) and lbm_scalar_step(0) are no-ops: same stored bytes,
