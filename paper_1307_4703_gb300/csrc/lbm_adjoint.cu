@@ -57,9 +57,12 @@ struct NextStage {
 
 // Transpose of the collision and of the port completion for the four nodes
 // of one lane.  x holds X (fluid planes as deviations); A(t+1) is read and
-// M(t) written one node at a time (fewer live registers than whole quads).
+// M(t) formed one node at a time (fewer live registers than whole quads):
+// node k's entries of M(t) replace its entries of X in x as soon as X of
+// the node has been read, and the quad is stored with 128-bit stores at the
+// end.
 template <typename Next>
-__device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes], unsigned lk, int x0, int y,
+__device__ __forceinline__ void collide_adjoint_quad(float4 (&x)[kPlanes], unsigned lk, int x0, int y,
                                                      long long oC, const RowBC& bw, const RowBC& be,
                                                      const AdjointArgs& A, const Next& next, KahanF& dwg)
 {
@@ -71,10 +74,9 @@ __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes],
     for (int k = 0; k < 4; ++k) {
         const unsigned lb = (lk >> (8 * k)) & 0xFFu;
         float af[9], ag[5];
-        const long long o = oC + k;
         if (lb == kSolid) {
 #pragma unroll
-            for (int i = 0; i < kPlanes; ++i) A.adj_mid[i * P + o] = 0.f;
+            for (int i = 0; i < kPlanes; ++i) at(x[i], k) = 0.f;
             continue;
         }
         float f[9], g[5];
@@ -108,7 +110,7 @@ __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes],
         const float rho = 1.f + rd;
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        const float irho = 1.f / rho;
+        const float irho = __fdividef(1.f, rho);  // fast reciprocal (2 ulp): rho stays near 1
         const float ux = jx * irho, uy = jy * irho;
         const float uu15 = 1.5f * (ux * ux + uy * uy);
         const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
@@ -197,24 +199,29 @@ __device__ __forceinline__ void collide_adjoint_quad(const float4 (&x)[kPlanes],
             }
         }
 #pragma unroll
-        for (int q = 0; q < 9; ++q) A.adj_mid[q * P + o] = nf[q];
+        for (int q = 0; q < 9; ++q) at(x[q], k) = nf[q];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) A.adj_mid[(9 + q) * P + o] = ng[q];
+        for (int q = 0; q < 5; ++q) at(x[9 + q], k) = ng[q];
     }
+#pragma unroll
+    for (int i = 0; i < kPlanes; ++i) stg4(A.adj_mid + i * P + oC, x[i]);
 }
 
-// Per-block running sum of dJ/d(1/tau_g), one slot per block.
-__device__ __forceinline__ void block_add(double* slot, double v)
+// Per-block running sum of dJ/d(1/tau_g), one FP64 slot per block: the
+// block's lanes are combined as double-float pairs (every warp gets here at
+// the same moment, and the FP64 pipe is narrow), then one thread adds the
+// block's sum to its slot in FP64.
+__device__ __forceinline__ void block_add(double* slot, const KahanF& k)
 {
-    __shared__ double red[32];
+    __shared__ DF red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    v = warp_sum(v);
+    const DF v = warp_sum(k.pair());
     if (lane == 0) red[warp] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < wpb; ++i) s += red[i];
-        slot[blockIdx.x] += s;
+        DF s = red[0];
+        for (int i = 1; i < wpb; ++i) s = df_add(s, red[i]);
+        slot[blockIdx.x] += df_value(s);
     }
 }
 
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_collide(const Adjoin
         complete_quad(x, q, bw, be, A);
         collide_adjoint_quad(x, q.lk, q.x0, q.y, q.oC, bw, be, A, NextGlobal{A.adj_next + q.oC, P}, dwg);
     }
-    block_add(A.grad_w, dwg.value());
+    block_add(A.grad_w, dwg);
 }
 
 // Every later reverse step: A(t+1) = F^T M(t+1) gathered into shared memory
@@ -417,7 +424,7 @@ __global__ void __launch_bounds__(kAdjointBlock, 4) adjoint_fused(const AdjointA
     grid_dependency_sync();
     for (int t = blockIdx.x * wpb + warp; t < A.n_tiles; t += gridDim.x * wpb)
         fused_tile<false>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, st, dwg);
-    block_add(A.grad_w, dwg.value());
+    block_add(A.grad_w, dwg);
 }
 
 // Reverse steps j = j_hi down to j_lo in one cooperative launch (every block
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(kAdjointBlock, 4)
             fused_tile<true>(A, tile_at(A.tiles, A.n_tiles, t, A.reverse), lane, st, dwg);
         if (j > j_lo && !grid_barrier(count, unsigned(s + 1) * gridDim.x + A0.barrier_extra, A0.err)) break;
     }
-    block_add(A0.grad_w, dwg.value());
+    block_add(A0.grad_w, dwg);
 }
 
 // J = sum w (C - target)^2 at the final state, and its derivative with

@@ -1495,7 +1495,12 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         h->diag_grid = h->launch.grid;
         h->step += n;
     } else {
-        for (int64_t t = 0; t < n; ++t) {
+        // a checkpoint every K steps; the states of the last segment go
+        // straight into the segment slots (its checkpoint, then slots 1 ..
+        // len - 1), where the reverse sweep starts, so that segment is never
+        // recomputed
+        const int64_t s_last = (n_ck - 1) * K;
+        for (int64_t t = 0; t < s_last; ++t) {
             if (t % K == 0)
                 LBM_CUDA(h, cudaMemcpyAsync(ckpt + size_t(t / K) * S, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
             a.src = h->pop[h->cur];
@@ -1509,6 +1514,30 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
             h->diag_grid = h->launch.grid;
             ++h->step;
         }
+        float* last = reinterpret_cast<float*>(ckpt + size_t(n_ck - 1) * S);
+        LBM_CUDA(h, cudaMemcpyAsync(last, h->pop[h->cur], S, cudaMemcpyDeviceToDevice, st));
+        const int64_t len = n - s_last;
+        if (len >= 2) {
+            float* slot1 = reinterpret_cast<float*>(seg);
+            a.src = last;
+            a.dst = slot1;
+            a.reverse = h->cur;
+            a.open_mask[0] = h->mask_at(t0 + s_last);
+            cudaError_t e = lbm::launch_step(a, h->launch, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+            if (lbm_status fs = forward_slots(a, slot1, s_last + 1, len - 2)) return fs;
+            last = reinterpret_cast<float*>(seg + size_t(len - 2) * S);
+        }
+        a.src = last;
+        a.dst = h->pop[1 - h->cur];
+        a.reverse = int((h->cur + len - 1) & 1);
+        a.open_mask[0] = h->mask_at(t0 + n - 1);
+        cudaError_t e = lbm::launch_step(a, h->launch, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
+        h->cur = 1 - h->cur;
+        h->gbuf = h->cur;
+        h->diag_grid = h->launch.grid;
+        h->step += len;
     }
 
     // J and dJ/dP(n)
@@ -1605,7 +1634,8 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
             return reinterpret_cast<float*>(j == 0 ? ckpt + size_t(sg) * S : seg + size_t(j - 1) * S);
         };
         // recompute the segment's states 1 .. len - 1 from its checkpoint
-        if (len >= 2) {
+        // (the last segment's are still there from the forward sweep)
+        if (len >= 2 && sg != n_ck - 1) {
             r.src = state(0);
             r.dst = state(1);
             r.reverse = 1;
