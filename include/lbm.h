@@ -100,8 +100,10 @@ typedef struct {
 } lbm_port;
 
 /* Device allocator hooks.  alloc returns a device pointer (>= 256-byte
- * aligned) or NULL; free releases it.  Both are called only from
- * lbm_create / lbm_destroy (and lbm_init_equilibrium for a temporary). */
+ * aligned) or NULL; free releases it.  A pointer that is not 256-byte
+ * aligned is passed back to free at once and the allocation fails
+ * (LBM_ERR_OOM).  Both are called only from lbm_create / lbm_destroy (and
+ * for temporaries of lbm_init_equilibrium, lbm_adjoint and similar calls). */
 typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
 typedef void (*lbm_free_fn)(void* ptr, size_t bytes, void* user);
 

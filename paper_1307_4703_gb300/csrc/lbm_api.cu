@@ -215,12 +215,25 @@ lbm_status cuda_fail(lbm_ctx* h, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
     } while (0)
 
+// A caller's allocator must return 256-byte aligned memory (the kernels
+// use 16-byte vector accesses); anything else is handed back and counts as
+// a failed allocation, so no kernel ever sees a misaligned buffer.
+void* hook_alloc(lbm_ctx* h, size_t bytes)
+{
+    void* p = h->alloc_fn(bytes, h->alloc_user);
+    if (p && (reinterpret_cast<uintptr_t>(p) & 255u)) {
+        if (h->free_fn) h->free_fn(p, bytes, h->alloc_user);
+        p = nullptr;
+    }
+    return p;
+}
+
 void* dev_alloc(lbm_ctx* h, size_t bytes)
 {
     bytes = (bytes + 255) & ~size_t(255);
     void* p = nullptr;
     if (h->alloc_fn) {
-        p = h->alloc_fn(bytes, h->alloc_user);
+        p = hook_alloc(h, bytes);
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
@@ -1156,7 +1169,7 @@ struct Scratch {
         bytes = (bytes + 255) & ~size_t(255);
         void* p = nullptr;
         if (h->alloc_fn) {
-            p = h->alloc_fn(bytes, h->alloc_user);
+            p = hook_alloc(h, bytes);
         } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;

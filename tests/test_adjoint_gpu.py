@@ -124,19 +124,26 @@ def test_adjoint_leaves_the_forward_state_and_diagnostics():
     b.close()
 
 
-def test_adjoint_keeping_every_state_equals_checkpointed():
+@pytest.mark.parametrize("K", [13, 7, 69, 70, 100])
+def test_adjoint_keeping_every_state_equals_checkpointed(K):
+    """Checkpoints every K of 70 steps (last segment 5, 7 = K, 1, 70 = the
+    whole run, and K > n): the forward sweep keeps the last segment's states
+    and the others are recomputed, so every reverse step reads the same
+    states as with every state kept: the same J, the gradients up to the
+    order of the FP64 gradient atomics, and the same final populations."""
     prob = W.config_large_chip(96, 48)
     prob["period"] = 30
     obj = _objective(prob)
     res = []
-    for K in (1, 13):
+    for k in (1, K):
         c = lbm.Chip.from_problem(prob)
         c.set_valve_schedule(prob["period"], prob["states"])
-        res.append(c.adjoint(70, obj[0], obj[1], obj[2], obj[3], ckpt_every=K))
+        res.append(c.adjoint(70, obj[0], obj[1], obj[2], obj[3], ckpt_every=k))
+        res.append(c.populations())
+        assert c.step_count() == 70
         c.close()
-    # the same kernels on the same states: identical up to the order of the
-    # FP64 gradient atomics
-    (J1, t1, u1, c1), (J2, t2, u2, c2) = res
+    (J1, t1, u1, c1), (f1, g1), (J2, t2, u2, c2), (f2, g2) = res
+    assert np.array_equal(f1, f2) and np.array_equal(g1, g2)
     assert J1 == J2
     assert abs(t1 - t2) <= 1e-9 * abs(t2)
     assert np.allclose(u1, u2, rtol=1e-9, atol=0) and np.allclose(c1, c2, rtol=1e-9, atol=0)

@@ -378,6 +378,28 @@ def test_in_kernel_diagnostics_equal_the_reduction_launch(opts):
     b.close()
 
 
+def test_misaligned_allocator_memory_is_refused(monkeypatch):
+    """A caller's allocator that returns memory off the 256-byte boundary:
+    lbm_create hands every such pointer straight back and fails with
+    LBM_ERR_OOM before any kernel runs on it."""
+    held = {}
+
+    def _alloc(nbytes, user):
+        base = torch.cuda.caching_allocator_alloc(int(nbytes) + 256)
+        held[base + 16] = base
+        return base + 16
+
+    def _free(ptr, nbytes, user):
+        torch.cuda.caching_allocator_delete(held.pop(int(ptr)))
+
+    hooks = (lbm.ALLOC_FN(_alloc), lbm.FREE_FN(_free))
+    monkeypatch.setattr(lbm, "_torch_hooks", lambda device: hooks)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Chip.from_problem(W.config_small(), torch_alloc=True)
+    assert ei.value.status == lbm.LBM_ERR_OOM
+    assert not held  # every pointer went back to the caller's free
+
+
 @pytest.mark.parametrize("opts", [dict(), dict(multi_step=8), dict(precision="fp16")])
 def test_zero_steps_change_nothing(opts):
     """lbm_step(0) and lbm_scalar_step(0) are no-ops: same stored bytes,
