@@ -23,7 +23,9 @@
  *     D = c_s^2 (tau_c - 1/2).  w0 = 1/3 (default) is D2Q5; w0 = 0 is the
  *     paper's D2Q4 lattice, g_eq = C/4 (1 + 2 e.u), D = (2 tau_c - 1)/4.
  *   - Fluid viscosity nu = (tau - 1/2)/3 (c_s^2 = 1/3).
- *   - Populations are FP32.  Diagnostics are accumulated in FP64.
+ *   - Populations are FP32 (or 16-bit, see lbm_options.precision).
+ *     Diagnostics: compensated FP32 per lane, double-float pairs within a
+ *     block, FP64 across blocks.
  *   - Every call returns lbm_status; no C++ exception crosses the ABI.  On
  *     an error, lbm_last_error(handle) (or lbm_last_error(NULL) for
  *     lbm_create) gives a one-line reason.  A handle is not thread-safe:
@@ -345,7 +347,9 @@ typedef struct {
  * Device memory: ceil(n_steps / ckpt_every) + ckpt_every - 1 population
  * copies and three adjoint buffers, taken through the handle's allocator
  * and released before returning (LBM_ERR_OOM if they do not fit).  The
- * derivatives are accumulated in FP64; the adjoint populations are FP32.
+ * derivatives are accumulated in FP64 (d/d(1/tau_c): compensated FP32 per
+ * lane and double-float pairs within a block for each reverse step, FP64
+ * across blocks and steps); the adjoint populations are FP32.
  * The diagnostics of lbm_get_diagnostics stay those of the last forward
  * step.  Synchronises the stream. */
 lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n_steps, int32_t ckpt_every,
