@@ -133,6 +133,8 @@ def test_create_rejects_invalid_arguments(lib, case, needle):
 
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_step_diagnostics(None, 1, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_get_diagnostics_async(None, None) == lbm.LBM_ERR_ARG
     assert lib.lbm_set_valves(None, 1) == lbm.LBM_ERR_ARG
     lib.lbm_destroy(None)
     assert lib.lbm_status_string(4) == b"LBM_ERR_NUMERIC"
