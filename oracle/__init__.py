@@ -25,13 +25,15 @@ class _Port(ctypes.Structure):
                 ("rho", ctypes.c_double)]
 
 
-_lib = None
+_libs = {}
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build_oracle())
+def _load(parallel=False):
+    """The serial library, or (``parallel``) the OpenMP build of the same
+    source, whose row loops run on all host cores with the same bits."""
+    lib = _libs.get(bool(parallel))
+    if lib is None:
+        lib = ctypes.CDLL(build_oracle(parallel=bool(parallel)))
         P = ctypes.POINTER
         d = P(ctypes.c_double)
         lib.orc_new.restype = ctypes.c_void_p
@@ -55,8 +57,21 @@ def _load():
         lib.orc_adjoint.restype = ctypes.c_double
         lib.orc_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_uint), ctypes.c_int,
                                     P(ctypes.c_int), P(ctypes.c_int), d, d, d, d, d]
-        _lib = lib
-    return _lib
+        lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_num_threads.argtypes = []
+        lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+        _libs[bool(parallel)] = lib
+    return lib
+
+
+def num_threads(parallel=False):
+    """Host threads the oracle's row loops use (1 for the serial build)."""
+    return int(_load(parallel).orc_num_threads())
+
+
+def set_num_threads(n):
+    """Team size of the OpenMP build (the serial build ignores it)."""
+    _load(True).orc_set_num_threads(int(n))
 
 
 def _dptr(a):
@@ -76,6 +91,7 @@ def lattice_vectors():
 class OracleLattice:
     """One lattice held by the oracle.
 
+    ``parallel``: run on the OpenMP build (all host cores, same bits).
     ``solid``: (ny, nx) array, non-zero = solid.  ``ports``: iterable of
     dicts with keys channel, side, x, y0, y1, kind and (pressure ports) rho.
     ``edge_u`` / ``edge_C``: (2, ny) arrays of u_x and C_in per side and row
@@ -84,8 +100,8 @@ class OracleLattice:
     """
 
     def __init__(self, solid, tau_f, tau_g, w0=1.0 / 3.0, periodic=False, ports=(),
-                 edge_u=None, edge_C=None, decay=0.0, wall_scheme=0):
-        lib = _load()
+                 edge_u=None, edge_C=None, decay=0.0, wall_scheme=0, parallel=False):
+        lib = _load(parallel)
         solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
         self.ny, self.nx = solid.shape
         self.solid = solid.astype(bool)

@@ -19,6 +19,18 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Row loops whose iterations write disjoint memory (every destination value
+ * has exactly one writer) run on all host cores in the OpenMP build of this
+ * file (liblbm_oracle_omp.so).  Each value is computed by the same
+ * expression in either build, so both give the same bits.  Sums over the
+ * lattice (diagnostics, the adjoint's parameter derivatives) stay serial. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_ROWS _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_ROWS
+#endif
+
 /* Eq. lattice: i = 0 rest; i = 1..4 the axis directions at angles
  * pi (i-1)/2 (east, north, west, south); i = 5..8 the diagonals at angles
  * pi (i - 9/2)/2 with length sqrt(2) (north-east, north-west, south-west,
@@ -100,6 +112,24 @@ static double scalar_moment(const double* gn)
     double C = 0.0;
     for (int i = 0; i < 5; ++i) C += gn[i];
     return C;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 void orc_lattice_vectors(int ex[9], int ey[9], double w[9])
@@ -234,6 +264,7 @@ static double wall_population(const orc_lattice* L, int x, int y, int m)
 void orc_init_equilibrium(orc_lattice* L, const double* rho, const double* ux,
                           const double* uy, const double* C)
 {
+    ORC_ROWS
     for (int y = 0; y < L->ny; ++y)
         for (int x = 0; x < L->nx; ++x) {
             if (!is_fluid(L, x, y)) continue;
@@ -250,6 +281,7 @@ void orc_init_equilibrium(orc_lattice* L, const double* rho, const double* ux,
  * node (the velocity "transferred from the fluid solver"). */
 static void collide_all(const orc_lattice* L, double* fp, double* gp)
 {
+    ORC_ROWS
     for (int y = 0; y < L->ny; ++y)
         for (int x = 0; x < L->nx; ++x) {
             if (!is_fluid(L, x, y)) continue;
@@ -336,7 +368,8 @@ void orc_step(orc_lattice* L, unsigned open_mask)
     const int nx = L->nx, ny = L->ny;
 
     /* moments at the start of the step, for the paper's wall scheme */
-    if (L->wall_scheme == 1)
+    if (L->wall_scheme == 1) {
+        ORC_ROWS
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 if (!is_fluid(L, x, y)) continue;
@@ -347,6 +380,7 @@ void orc_step(orc_lattice* L, unsigned open_mask)
                 L->mom[(size_t)c * 3 + 1] = r * ux;
                 L->mom[(size_t)c * 3 + 2] = r * uy;
             }
+    }
 
     /* 1. collision (moments of Eq. moments, relaxation of Eq. lbequation) */
     collide_all(L, L->fp, L->gp);
@@ -356,6 +390,7 @@ void orc_step(orc_lattice* L, unsigned open_mask)
      *    ghost column) is a wall: the population returns to x with the
      *    opposite direction (halfway bounce-back, zero flux).  Every
      *    population of every fluid node is written exactly once here. */
+    ORC_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             if (!is_fluid(L, x, y)) continue;
@@ -427,6 +462,7 @@ void orc_step(orc_lattice* L, unsigned open_mask)
 void orc_fields(const orc_lattice* L, double* rho, double* ux, double* uy,
                 double* C)
 {
+    ORC_ROWS
     for (int y = 0; y < L->ny; ++y)
         for (int x = 0; x < L->nx; ++x) {
             int c = node(L, x, y);
@@ -744,6 +780,7 @@ void orc_scalar_step(orc_lattice* L, unsigned open_mask, const double* ux, const
     const int nx = L->nx, ny = L->ny;
     /* collision with the given velocity (scalar counterpart of Eq. lbequation
      * with the equilibrium of Eq. cdeequilibrium) */
+    ORC_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             if (!is_fluid(L, x, y)) continue;
@@ -755,6 +792,7 @@ void orc_scalar_step(orc_lattice* L, unsigned open_mask, const double* ux, const
                 L->gp[c * 5 + i] = gn[i] - (gn[i] - geq(L, i, C, ux[c], uy[c])) / L->tau_g + wg(L, i) * R;
         }
     /* free flight with halfway bounce-back */
+    ORC_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             if (!is_fluid(L, x, y)) continue;

@@ -124,6 +124,12 @@ void orc_diagnostics(const orc_lattice* L, unsigned open_mask, double out[4]);
 /* Lattice tables as the oracle uses them (for checks against Eq. lattice). */
 void orc_lattice_vectors(int ex[9], int ey[9], double w[9]);
 
+/* Host threads the row loops use: 1 in the serial build
+ * (liblbm_oracle.so), the OpenMP team size in the all-cores build of the
+ * same source (liblbm_oracle_omp.so).  Both builds give the same bits. */
+int orc_num_threads(void);
+void orc_set_num_threads(int n);   /* no effect in the serial build */
+
 /* Scalar-only step with a given velocity field (section "Results": the
  * stationary velocity fields are computed once and the advection-diffusion
  * solver reads them; the fluid populations do not change).  ux, uy: ny*nx
