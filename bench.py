@@ -18,7 +18,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -33,7 +32,7 @@ UNIT = "GLUPS"
 BYTES_PER_NODE = 112  # 14 FP32 populations read + written per fluid node and step
 KERNEL_SRC = [os.path.join(ROOT, "paper_1307_4703_gb300", "csrc", f)
               for f in ("lbm_device.cuh", "lbm_internal.h", "lbm_step.cuh", "lbm_kernels.cu")]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "coupled_step_chip-4096x2048.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "coupled_step_chip-4096x2048.json")
 
 
 def _args():
@@ -45,7 +44,8 @@ def _args():
     p.add_argument("--workload", default="large", choices=["large", "full", "small"])
     p.add_argument("--skip-extras", action="store_true",
                    help="skip the end-to-end and CPU-baseline legs (profiling runs)")
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--cpu-seconds", type=float, default=8.0,
+                   help="host time of the single-thread oracle sample")
     p.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3, 4],
                    help="step kernel: 0 library default, 1 registers, 2 bulk-copy pipeline, "
                         "3 self-refilling pipeline, 4 registers with async-copy prefetch")
@@ -90,19 +90,23 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(nodes_now):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def _traffic(nodes_now, precision):
+    """DRAM bytes (read + written) per launch of the step kernel from the
+    committed ncu figures, if they were taken on the current kernel source
+    and storage type (else None).  They come from one launch that ncu runs
+    with cold caches: reads include the first touch of every row, and writes
+    leave out what is still dirty in L2 when the kernel ends."""
     try:
-        text = open(TRAFFIC_FILE).read()
-    except OSError:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
         return None
-    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    n = re.search(r"fluid_nodes:\s*(\d+)", text)
-    if not (h and b and n) or h.group(1) != _kernel_hash():
+    if rec.get("kernel_source_sha256_16") != _kernel_hash():
         return None
-    return float(b.group(1)) * nodes_now / float(n.group(1))
+    per = rec.get("per_precision", {}).get(precision)
+    if not per:
+        return None
+    return float(per["dram_bytes_per_launch"]) * nodes_now / float(rec["fluid_nodes"])
 
 
 class _Clocks:
@@ -115,9 +119,20 @@ class _Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.before = ""
         self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
 
+    def _once(self):
+        """One read-only query (no setting is changed)."""
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            return out.stdout
+        except (OSError, subprocess.SubprocessError):
+            return ""
+
     def start(self):
+        self.before = self._once()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
@@ -127,6 +142,7 @@ class _Clocks:
             self.proc = None
 
     def stop(self):
+        after = self._once()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -136,7 +152,10 @@ class _Clocks:
             self.proc.kill()
         self.out.flush()
         self.out.seek(0)
-        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        # a sample right before and right after the timed region, beside the
+        # 50 ms poll (a short timed region may fall between two polls)
+        text = self.before + self.out.read() + after
+        rows = [r.split(",") for r in text.strip().splitlines() if r.strip()]
         self.out.close()
         os.unlink(self.out.name)
         sm, smax, reasons = [], None, set()
@@ -152,29 +171,49 @@ class _Clocks:
                 if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "reasons": sorted(reasons),
+                "sampling": "nvidia-smi read-only queries: one right before and one right after the timed "
+                            "region, and every 50 ms during it"}
 
 
 def _cpu_baseline(seconds):
-    """The FP64 oracle as it stands, single thread, on a 512 x 256 downscaled
-    copy of the chip; runs for about `seconds` of host time."""
+    """The FP64 oracle as it stands, timed on the host cores on the 512 x 256
+    downscaled copy of the chip: the serial build for about `seconds` of one
+    core, then the all-cores build of the same source (OpenMP over rows, the
+    same bits) over the first 1000 steps from rest.  Returns the
+    cpu_baseline record and the all-cores run's fields after those 1000
+    steps, the reference of the storage-precision accuracy figures."""
     import oracle
     from paper_1307_4703_gb300 import workloads as W
     prob = W.config_large_chip(512, 256)
-    ref = oracle.from_problem(prob)
     fluid = W.fluid_count(prob)
+    sched = lambda t: W.valve_word(prob, t)  # noqa: E731
+    ref = oracle.from_problem(prob)
     ref.step(1, 5)
     t0 = time.perf_counter()
     n = 0
     while True:
         ref.step(W.valve_word(prob, n), 10)
         n += 10
-        dt = time.perf_counter() - t0
-        if dt >= seconds:
+        dt1 = time.perf_counter() - t0
+        if dt1 >= seconds:
             break
-    return {"value": fluid * n / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 C oracle, 1 thread, %d steps of the 512x256 downscaled copy "
-                      "(%d fluid nodes), %.1f s" % (n, fluid, dt)}
+    ref.close()
+    single = fluid * n / dt1 / 1e9
+    par = oracle.from_problem(prob, parallel=True)
+    threads = oracle.num_threads(True)
+    t0 = time.perf_counter()
+    par.run(1000, sched)
+    dtp = time.perf_counter() - t0
+    fields = par.fields()
+    par.close()
+    record = {"value": fluid * 1000 / dtp / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+              "nproc": os.cpu_count(),
+              "sample": "FP64 C oracle, all-cores build (OpenMP over rows, %d threads), the first 1000 steps "
+                        "of the 512x256 downscaled copy (%d fluid nodes) from rest, %.1f s" % (threads, fluid, dtp),
+              "single_thread": {"value": single, "unit": UNIT, "cores": 1,
+                                "sample": "serial build, %d steps of the same copy, %.1f s" % (n, dt1)}}
+    return record, (prob, fields)
 
 
 def _workload_config(prob, precision):
@@ -186,44 +225,55 @@ def _workload_config(prob, precision):
 
 
 def _reference(args):
-    """The reference arm: the oracle, as it stands, on the host cores."""
+    """The reference arm: the oracle, as it stands, on the host cores (its
+    all-cores build).  Each step is one time step of the 4096 x 2048 chip
+    itself when the run holds at most 200 steps (warm-up included), else of
+    its 512 x 256 downscaled copy, so that the run ends within minutes."""
     import oracle
     from paper_1307_4703_gb300 import workloads as W
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    prob = W.config_large_chip(256, 128)
+    full = args.steps + args.warmup <= 200
+    prob = W.config_large_chip() if full else W.config_large_chip(512, 256)
     fluid = W.fluid_count(prob)
-    ref = oracle.from_problem(prob)
+    ref = oracle.from_problem(prob, parallel=True)
+    threads = oracle.num_threads(True)
     for t in range(args.warmup):
         ref.step(W.valve_word(prob, t))
     t0 = time.perf_counter()
     for t in range(args.steps):
         ref.step(W.valve_word(prob, args.warmup + t))
     dt = time.perf_counter() - t0
+    ref.close()
     value = fluid * args.steps / dt / 1e9
-    sample = ("FP64 C oracle, 1 thread; each step one time step of the 256x128 downscaled copy "
-              "of the 4096x2048 chip (%d fluid nodes)" % fluid)
+    sample = ("FP64 C oracle, all-cores build (OpenMP over rows, %d threads, %s host cores); each step one time "
+              "step of the %s (%d fluid nodes)"
+              % (threads, os.cpu_count(), "4096x2048 chip" if full else "512x256 downscaled copy of the chip",
+                 fluid))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _workload_config(W.config_large_chip(), "fp32"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def _adjoint_ratio(device):
-    """Cost of the gradient relative to the forward run on the gradient
-    workload (1024 x 512 chip, 4000 steps, two valve toggles): (time of
-    lbm_adjoint - time of 4000 plain steps) / time of 4000 plain steps, wall
+    """Cost of the gradient on the gradient workload (the 1024 x 512 chip,
+    4000 steps, two valve toggles) relative to a forward run of the same
+    4000 steps with the same options: the whole lbm_adjoint call (its own
+    forward sweep, the recomputation of every checkpoint segment but the
+    last, and the reverse sweep) over the forward run, and (call - forward
+    run) / forward run, the reverse sweep and recomputation alone.  Wall
     clock with the stream synchronised, best of two calls (device memory from
-    PyTorch's caching allocator, so the second call allocates nothing).  With
-    every state kept in HBM (ckpt_every = 1, 117 GB) nothing is recomputed;
-    with a checkpoint every 250 steps each segment is recomputed once.  Once
-    with one launch per step, once with multi_step runs of up to 1000 steps
-    (forward steps and adjoint alike)."""
+    PyTorch's caching allocator, so the second call allocates nothing).
+    Checkpoints every 250 steps (the workload's setting) and every state
+    kept (ckpt_every = 1, 117 GB, nothing recomputed); one launch per step,
+    and multi_step runs of up to 1000 steps (forward run and adjoint
+    alike)."""
     import numpy as np
     from paper_1307_4703_gb300 import lbm, workloads as W
     prob = W.config_adjoint_chip()
@@ -234,7 +284,7 @@ def _adjoint_ratio(device):
     n = prob["steps"]
     out = {}
     for ms in (0, 1000):
-        for K in (1, 250):
+        for K in (250, 1):
             best = None
             for _ in range(2):
                 chip = lbm.Chip.from_problem(prob, device=device, torch_alloc=True, multi_step=ms)
@@ -249,19 +299,17 @@ def _adjoint_ratio(device):
                 chip.adjoint(n, ox, oy, target, ckpt_every=K)
                 ta = time.perf_counter() - t0
                 chip.close()
-                r = ((ta - tf) / tf, tf / n * 1e6, (ta - tf) / n * 1e6)
-                best = r if best is None or r[0] < best[0] else best
+                r = {"whole_call": ta / tf, "beyond_forward": (ta - tf) / tf,
+                     "forward_us_per_step": tf / n * 1e6, "adjoint_call_us_per_step": ta / n * 1e6}
+                best = r if best is None or r["whole_call"] < best["whole_call"] else best
             out[(ms, K)] = best
     import torch
     torch.cuda.empty_cache()
-    return {"value": out[(0, 1)][0], "workload": "chip-1024x512, 4000 steps",
-            "ckpt_every_1": out[(0, 1)][0], "ckpt_every_250": out[(0, 250)][0],
-            "forward_us_per_step": out[(0, 1)][1], "adjoint_us_per_step": out[(0, 1)][2],
-            "multi_step_1000": {"ckpt_every_1": out[(1000, 1)][0], "ckpt_every_250": out[(1000, 250)][0],
-                                "forward_us_per_step": out[(1000, 1)][1],
-                                "adjoint_us_per_step": out[(1000, 1)][2]},
-            "definition": "(adjoint call - forward steps) / forward steps; value: every state kept (ckpt_every 1), "
-                          "one launch per step"}
+    return {"value": out[(0, 250)]["whole_call"], "workload": "chip-1024x512, 4000 steps, checkpoints every 250",
+            "definition": "whole lbm_adjoint call (forward sweep + recomputation + reverse sweep) / forward run "
+                          "of the same steps; one launch per step",
+            "ckpt_every_250": out[(0, 250)], "ckpt_every_1": out[(0, 1)],
+            "multi_step_1000": {"ckpt_every_250": out[(1000, 250)], "ckpt_every_1": out[(1000, 1)]}}
 
 
 def _frozen_scalar(chip, prob, steps, stream, peak):
@@ -289,10 +337,14 @@ def _frozen_scalar(chip, prob, steps, stream, peak):
                          "frac": achieved / peak, "bytes_per_launch": fluid * 48}}
 
 
-def _reduced_precision(prob, steps, stream, device, peak):
+def _reduced_precision(prob, steps, stream, device, peak, reference=None):
     """The same coupled step with 16-bit population storage (FP16 and BF16
     deviations, FP32 arithmetic): 56 bytes per fluid node and step.  Device
-    time over `steps` single-step calls after 50 warm-up steps."""
+    time over `steps` single-step calls after 50 warm-up steps.  Accuracy:
+    the fields of each storage type after the first 1000 steps of the
+    512 x 256 copy against `reference` = (problem, FP64 oracle fields) of the
+    CPU-baseline leg, or, without it (ranks of a multi-GPU run), against
+    FP32 storage."""
     import numpy as np
     import torch
     from paper_1307_4703_gb300 import lbm, workloads as W
@@ -320,10 +372,7 @@ def _reduced_precision(prob, steps, stream, device, peak):
                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                   "frac": achieved / peak,
                                   "bytes_per_launch": info["algorithmic_bytes_per_step"]}}
-    # accuracy: the fields after 1000 steps of the 512 x 256 copy of the chip
-    # against the same run with FP32 storage (which matches the FP64 oracle
-    # to 1e-6, tested)
-    small = W.config_large_chip(512, 256)
+    small = W.config_large_chip(512, 256) if reference is None else reference[0]
     fields = {}
     for prec in ("fp32", "fp16", "bf16"):
         chip = lbm.Chip.from_problem(small, stream=stream, torch_alloc=True, device=device, precision=prec)
@@ -332,11 +381,19 @@ def _reduced_precision(prob, steps, stream, device, peak):
         fields[prec] = chip.fields()
         chip.close()
     fl = ~np.asarray(small["solid"], bool)
-    for prec in ("fp16", "bf16"):
-        du = max(np.abs(fields[prec][k] - fields["fp32"][k])[fl].max() for k in (1, 2)) / small["u_max"]
-        dC = np.abs(fields[prec][3] - fields["fp32"][3])[fl].max()
-        out[prec]["accuracy"] = {"max_du_over_u_max": float(du), "max_dC": float(dC),
-                                 "against": "FP32 storage, chip-512x256 copy, 1000 steps"}
+    ref = fields["fp32"] if reference is None else reference[1]
+    against = ("FP32 storage" if reference is None else "the FP64 oracle") + ", chip-512x256 copy, 1000 steps from rest"
+    out["fp32"] = {}
+    for prec in ("fp32", "fp16", "bf16") if reference is not None else ("fp16", "bf16"):
+        f = fields[prec]
+        drho = np.abs(f[0] - ref[0])[fl].max()
+        du = max(np.abs(f[k] - ref[k])[fl].max() for k in (1, 2)) / small["u_max"]
+        dC = np.abs(f[3] - ref[3])[fl].max()
+        dm = abs(f[0][fl].astype(np.float64).sum() - ref[0][fl].sum()) / ref[0][fl].sum()
+        out[prec]["accuracy"] = {"max_drho": float(drho), "max_du_over_u_max": float(du), "max_dC": float(dC),
+                                 "mass_rel": float(dm), "against": against}
+    if not out["fp32"]:
+        del out["fp32"]
     return out
 
 
@@ -463,11 +520,15 @@ def _e2e(prob, steps, device):
     rows = torch.zeros((steps, 4), dtype=torch.float64, pin_memory=True)
     t0 = time.perf_counter()
     chip = lbm.Chip.from_problem(prob, device=device)
+    chip.synchronize()
+    t1 = time.perf_counter()
     for t in range(steps):
         chip.set_valves(W.valve_word(prob, t))
         chip.step_diagnostics(1, rows[t].data_ptr())
     chip.synchronize()
+    t2 = time.perf_counter()
     fields = chip.fields()
+    t3 = time.perf_counter()
     chip.close()
     dt = time.perf_counter() - t0
     assert np.isfinite(rows.numpy()).all()
@@ -476,7 +537,8 @@ def _e2e(prob, steps, device):
     return {"value": fluid * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": 4 + h2d_once / steps,
             "d2h_bytes_per_step": 32 + d2h_once / steps,
-            "steps": steps, "seconds": dt}
+            "steps": steps, "seconds": dt,
+            "breakdown_s": {"create": t1 - t0, "steps": t2 - t1, "read_fields": t3 - t2, "destroy": dt - (t3 - t0)}}
 
 
 def reduce_max(value, world_size):
@@ -604,17 +666,20 @@ def main():
     achieved = info["algorithmic_bytes_per_step"] / (ms_per_step / 1e3) / 1e9
     extras = {}
     if not args.skip_extras:
+        reference = None
+        if ws == 1 and rank == 0:
+            extras["cpu_baseline"], reference = _cpu_baseline(args.cpu_seconds)
         extras["frozen_scalar_step"] = _frozen_scalar(chip, prob, min(args.steps, 2000), stream, peak)
-        extras["reduced_precision_storage"] = _reduced_precision(prob, min(args.steps, 5000), stream, local, peak)
+        extras["reduced_precision_storage"] = _reduced_precision(prob, min(args.steps, 5000), stream, local, peak,
+                                                                 reference)
         extras["batch_64_chips"] = _batch(min(args.steps, 10000), stream, local, peak)
         extras["small_chips"] = _small_chips(min(args.steps, 20000), stream, local, peak)
         e2e_steps = args.steps  # the device-timed region's step count
         e = _e2e(prob, e2e_steps, local)
         e["value"] = aggregate_glups(fluid * e2e_steps, e["seconds"], ws)
-        extras["e2e"] = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+        extras["e2e"] = {k: e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "steps",
+                                           "breakdown_s")}
         extras["adjoint_forward_ratio"] = _adjoint_ratio(local)
-        if ws == 1 and rank == 0:
-            extras["cpu_baseline"] = _cpu_baseline(args.cpu_seconds)
     chip.close()
     if rank == 0:
         line = {
@@ -633,7 +698,10 @@ def main():
             "all_node_glups": ws * prob["nx"] * prob["ny"] * args.steps / (ms / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": _traffic(fluid) if args.precision == "fp32" else None,
+                         "traffic": _traffic(fluid, args.precision),
+                         "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch with "
+                                         "cold caches (committed figures, null when the kernel source changed); "
+                                         "writes still dirty in L2 at the kernel's end are not counted",
                          "peak_source": "%s (hbm_gbs)" % peak_src,
                          "bytes_per_launch": info["algorithmic_bytes_per_step"]},
             "gpu_launches": args.steps,

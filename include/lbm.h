@@ -152,8 +152,8 @@ typedef struct {
                                identical; a barrier that waits too long gives LBM_ERR_TIMEOUT. */
 } lbm_options;
 
-/* Storage precision.  The paper computes in double precision ("Numerical
- * Methods"); the library always does the arithmetic of a step in FP32.
+/* Storage precision.  The paper states no arithmetic precision; the library
+ * always does the arithmetic of a step in FP32.
  * LBM_FP32 (default) stores every population in FP32.  LBM_FP16 and LBM_BF16
  * store 16-bit deviations instead: f_i - w_i for the fluid and
  * g_i - w_i C_ref with C_ref = 1/2 for the scalar, converted to FP32 on
@@ -494,7 +494,9 @@ lbm_status lbm_set_instance_schedule(lbm_handle h, int32_t k, int64_t period, in
 
 typedef struct {
     int32_t x;             /* port node column of this side and row, -1 = none */
-    int32_t channel_kind;  /* valve channel | (LBM_PORT_VELOCITY or LBM_PORT_PRESSURE) << 8 */
+    int32_t channel_kind;  /* valve channel | (LBM_PORT_VELOCITY or LBM_PORT_PRESSURE) << 8; channels
+                              0..31 (bit `channel` of open_mask opens the port); an entry naming
+                              channel 32 or above is never opened, so it stays a wall */
     float a;               /* velocity port: u_x; pressure port: rho - 1 */
     float c;               /* velocity port: held concentration */
 } lbm_row_port;
@@ -514,7 +516,9 @@ typedef struct {
     const lbm_tile* tiles;
     int32_t n_tiles;
     int32_t max_blocks;    /* 0 = one wave of resident blocks; at most LBM_NOALLOC_MAX_BLOCKS */
-    double tau, tau_c, w0; /* as for lbm_create and lbm_options.w0 */
+    double tau, tau_c, w0; /* as for lbm_create and lbm_options.w0, but w0 has no default here:
+                              0 selects the paper's D2Q4 scalar lattice, 1/3 the D2Q5 lattice
+                              that lbm_create uses when lbm_options.w0 is left at its default */
     uint32_t open_mask;    /* valve word of this step */
     double* diag;          /* device, 4 doubles: the step's diagnostics as lbm_get_diagnostics; NULL = skip */
     uint32_t* err;         /* device word the kernel ORs its flags into: bit 0 numeric, bit 1 timeout */

@@ -114,12 +114,25 @@ def config_large_chip(nx=4096, ny=2048, tau_c=0.51, steps=50000):
                             name="chip-%dx%d" % (nx, ny))
 
 
-def config_adjoint_chip():
+def config_adjoint_chip(nx=1024, ny=512, seed=SEED):
     """1024 x 512 chip for the gradient workload: channels rows 0..99 and
     412..511 over x = 0..999, chamber 200 wide; tau = 0.6, tau_c = 0.51,
-    u_max = 0.04, valve period 1500, 4000 steps."""
-    return two_channel_chip(1024, 512, 100, 1000, 200, 0.6, 0.51, 0.04, 1500, 4000,
-                            name="chip-1024x512")
+    u_max = 0.04, valve period 1500 (two toggles in 4000 steps), 4000
+    steps.  The top inlet holds a per-row concentration vector drawn
+    uniformly from [0.8, 1.0) with PCG64 (``seed``), one entry per inlet row
+    (100 on this chip); its rows are ``c_in_rows``.  Other sizes keep the
+    proportions (the 128 x 64 copy: channels 12 rows wide and 125 long,
+    chamber 25 wide, the first 12 draws of the same vector)."""
+    ch_w = int(round(ny * 100 / 512))
+    ch_len = int(round(nx * 1000 / 1024))
+    cw = int(round(nx * 200 / 1024))
+    prob = two_channel_chip(nx, ny, ch_w, ch_len, cw, 0.6, 0.51, 0.04, 1500, 4000,
+                            name="chip-%dx%d" % (nx, ny))
+    top = [p for p in prob["ports"] if p["channel"] == 0 and p["side"] == WEST][0]
+    rows = np.arange(top["y0"], top["y1"])
+    prob["edge_C"][WEST, rows] = rng(seed).uniform(0.8, 1.0, size=len(rows))
+    prob["c_in_rows"] = rows
+    return prob
 
 
 def config_batch(n=64, steps=10000, seed=SEED):

@@ -82,9 +82,9 @@ def test_adjoint_every_port_kind():
 
 def test_adjoint_on_the_128x64_copy_of_the_gradient_chip():
     """The gradient workload scaled to 128 x 64 (the size the FP64 reference
-    adjoint runs at): 4000 steps, valves toggling every 1500 steps,
-    checkpoints every 250 steps."""
-    prob = W.two_channel_chip(128, 64, 12, 125, 25, 0.6, 0.51, 0.04, 1500, 4000, name="chip-128x64")
+    adjoint runs at), with the seeded per-row inlet concentrations: 4000
+    steps, valves toggling every 1500 steps, checkpoints every 250 steps."""
+    prob = W.config_adjoint_chip(128, 64)
     n = 4000
     masks = [W.valve_word(prob, t) for t in range(n)]
     obj = _objective(prob)

@@ -157,6 +157,53 @@ def test_full_chip_parity(prec):
     chip.close()
 
 
+@pytest.fixture(scope="module")
+def _oracle_runs():
+    """The FP64 oracle (its all-cores build) on the 4096 x 2048 chip and its
+    512 x 256 downscaled copy, 1000 steps from rest, computed once."""
+    cache = {}
+
+    def get(nx, ny):
+        if (nx, ny) not in cache:
+            prob = W.config_large_chip(nx, ny)
+            ref = oracle.from_problem(prob, parallel=True)
+            ref.run(1000, lambda t: W.valve_word(prob, t))
+            cache[(nx, ny)] = (prob, ref, ref.fields())
+        return cache[(nx, ny)]
+
+    yield get
+    for _, ref, _ in cache.values():
+        ref.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(512, 256), (4096, 2048)])
+def test_large_chip_1000_steps_against_oracle(nx, ny, _oracle_runs):
+    """The precision workload (the 4096 x 2048 chip, tau = 0.6, tau_c =
+    0.51) and its 512 x 256 copy, 1000 steps from rest with the valve
+    schedule, stored as FP32, FP16 and BF16: every field against the FP64
+    oracle.  Bounds: FP32 max |du| / u_max and max |dC| <= 1e-4 and the
+    relative mass <= 1e-6; 16-bit storage the 20 u bounds above.  The
+    errors are printed (pytest -s)."""
+    prob, ref, (r_rho, r_ux, r_uy, r_C) = _oracle_runs(nx, ny)
+    fl = ~ref.solid
+    for prec in ("fp32", "fp16", "bf16"):
+        with lbm.Chip.from_problem(prob, precision=prec) as chip:
+            chip.set_valve_schedule(prob["period"], prob["states"])
+            chip.step(1000)
+            rho, ux, uy, C = chip.fields()
+        drho = np.abs(rho - r_rho)[fl].max()
+        du = max(np.abs(ux - r_ux)[fl].max(), np.abs(uy - r_uy)[fl].max()) / prob["u_max"]
+        dC = np.abs(C - r_C)[fl].max()
+        dm = abs(rho[fl].astype(np.float64).sum() - r_rho[fl].sum()) / r_rho[fl].sum()
+        print("chip-%dx%d 1000 steps %s vs FP64 oracle: max|drho| %.3e max|du|/u_max %.3e max|dC| %.3e "
+              "mass %.3e" % (nx, ny, prec, drho, du, dC, dm))
+        if prec == "fp32":
+            assert du <= 1e-4 and dC <= 1e-4 and dm <= 1e-6, (prec, du, dC, dm)
+        else:
+            u = UNIT_ROUNDOFF[prec]
+            assert du <= 20 * u and dC <= 20 * u and dm <= u, (prec, du, dC, dm)
+
+
 def test_large_chip_at_benchmark_launch_shape():
     """The 4096 x 2048 chip in FP16 from a perturbed state: three steps,
     every node against the oracle, and the 16-bit handle's bytes and

@@ -8,7 +8,8 @@ runs the same step kernel with its scratch in a fixed array of the library.
 This test prepares the caller-owned buffers (the allocation is the caller's
 job, so the test makes it with PyTorch), fills them with the same state and
 tables a handle uses, then runs two no-alloc calls in a row and compares
-populations and diagnostics with two steps of lbm_step.  It lives in a file
+populations and diagnostics with two steps of lbm_step, and the populations
+with the FP64 oracle.  It lives in a file
 of its own, collected last, and passes alone or after the other tests.
 """
 import ctypes
@@ -85,9 +86,27 @@ def _pitched(arr, pitch):
     return out
 
 
-def test_noalloc_step_matches_handle_step_twice():
+def _case(name):
+    if name == "random-300x40":  # about 120 tiles: at most one per block
+        return W.random_case(41, 300, 40, solid_frac=0.15)
+    # 1100 x 280: 9 segments x 280 rows = 2520 tiles, more than the 2048-block cap;
+    # the grid is one wave of resident blocks, so the reduction reads over 256 partials
+    return W.random_case(43, 1100, 280, solid_frac=0.1)
+
+
+@pytest.mark.parametrize("name,max_blocks", [("random-300x40", 0), ("random-300x40", 5),
+                                             ("random-1100x280", 0), ("random-1100x280", 7)])
+def test_noalloc_step_matches_handle_step_twice(name, max_blocks):
+    """Two no-alloc calls in a row: the stored populations equal the handle
+    path's bit for bit and the FP64 oracle's post-collision populations
+    within the FP32 parity bound (n x 30 x 2^-24 for n steps), and the
+    diagnostics equal the handle's.  max_blocks = 5 or 7 makes every block
+    take many tiles; the 1100 x 280 lattice has more tiles than the fixed
+    scratch has block slots."""
+    import oracle
+
     lib = lbm.load()
-    prob, init = W.random_case(41, 300, 40, solid_frac=0.15)
+    prob, init = _case(name)
     ny, nx = prob["ny"], prob["nx"]
     pitch = (nx + TILE - 1) // TILE * TILE
     words = [5, 3]  # valve words of the two steps
@@ -95,8 +114,12 @@ def test_noalloc_step_matches_handle_step_twice():
     chip = lbm.Chip.from_problem(prob)
     chip.init_equilibrium(**init)
     start = _raw_state(chip)
+    ref = oracle.from_problem(prob)
+    ref.init_equilibrium(**init)
 
     links, ports, tiles = _tables(prob, pitch)
+    if name == "random-1100x280":
+        assert len(tiles) > 2048
     dev = torch.device("cuda")
     bufs = [torch.from_numpy(_pitched(start, pitch)).to(dev), torch.zeros((14, ny, pitch), device=dev)]
     links_d = torch.from_numpy(links).to(dev)
@@ -106,6 +129,7 @@ def test_noalloc_step_matches_handle_step_twice():
     err_d = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     msg = ctypes.create_string_buffer(256)
+    fl = ~np.asarray(prob["solid"], bool)
 
     for call, word in enumerate(words):
         # ordinary path: one step with this valve word
@@ -113,6 +137,7 @@ def test_noalloc_step_matches_handle_step_twice():
         chip.step(1)
         ref_diag = chip.diagnostics()
         ref_state = _raw_state(chip)
+        ref.step(word)
         # allocation-free path: one call, src -> dst
         src, dst = bufs[call % 2], bufs[(call + 1) % 2]
         d = lbm.lbm_noalloc_step()
@@ -121,7 +146,7 @@ def test_noalloc_step_matches_handle_step_twice():
         d.src, d.dst = src.data_ptr(), dst.data_ptr()
         d.links, d.ports, d.tiles = links_d.data_ptr(), ports_d.data_ptr(), tiles_d.data_ptr()
         d.n_tiles = len(tiles)
-        d.max_blocks = 0
+        d.max_blocks = max_blocks
         d.tau, d.tau_c, d.w0 = prob["tau"], prob["tau_c"], prob["w0"]
         d.open_mask = word
         d.diag, d.err = diag_d.data_ptr(), err_d.data_ptr()
@@ -133,11 +158,19 @@ def test_noalloc_step_matches_handle_step_twice():
         torch.cuda.synchronize()
         assert int(err_d.item()) == 0
         got = dst.cpu().numpy()[:, :, :nx]
-        fl = ~np.asarray(prob["solid"], bool)
         # same kernel, same inputs: identical bits on every fluid node
         assert np.array_equal(got[:, fl], ref_state[:, fl]), "populations differ after call %d" % (call + 1)
         got_diag = diag_d.cpu().numpy()
         assert np.allclose(got_diag, ref_diag, rtol=1e-6, atol=1e-6), (got_diag, ref_diag)
+        # and against the FP64 oracle directly: stored f_i - w_i and g_i
+        fp, gp = ref.post_collision()
+        w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+        rf = np.moveaxis(fp, -1, 0) - w9[:, None, None]
+        rg = np.moveaxis(gp, -1, 0)
+        tol = (call + 1) * 30 * 2.0 ** -24
+        ef = np.abs(got[:9].astype(np.float64) - rf)[:, fl].max()
+        eg = np.abs(got[9:].astype(np.float64) - rg)[:, fl].max()
+        assert ef <= tol and eg <= tol, (ef, eg, tol)
     chip.close()
 
 
