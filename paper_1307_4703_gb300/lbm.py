@@ -222,7 +222,9 @@ class Chip:
                  graph_steps=0, decay=0.0, wall_scheme=0, scalar_variant=0, multi_step=0, _batch=None):
         self._lib = load()
         if _batch is None:
-            solid = np.ascontiguousarray(np.asarray(solid) != 0, dtype=np.uint8)
+            solid = np.asarray(solid)
+            if solid.dtype != np.uint8 or not solid.flags.c_contiguous:
+                solid = np.ascontiguousarray(solid != 0, dtype=np.uint8)  # the library reads non-zero as solid
             self.ny, self.nx = solid.shape
             parr = _ports(ports)
             eu = _f32(np.zeros((2, self.ny)) if edge_u is None else edge_u, (2, self.ny))
@@ -263,14 +265,22 @@ class Chip:
             raise LbmError(st, self._lib.lbm_last_error(None).decode())
         self._h = h
         if _batch is None:
-            self.solid = solid.astype(bool)
+            self._mask = solid
+            self._solid = None
         else:
             inf = self.info()
             self.nx, self.ny = inf["nx"], inf["ny"]
-            self.solid = np.ones((self.ny, self.nx), bool)
+            self._solid = np.ones((self.ny, self.nx), bool)
             for k in range(inf["instances"]):
                 i = self.instance(k)
-                self.solid[i["row0"]:i["row0"] + i["ny"], :i["nx"]] = keep[4 * k] != 0
+                self._solid[i["row0"]:i["row0"] + i["ny"], :i["nx"]] = keep[4 * k] != 0
+
+    @property
+    def solid(self):
+        """(ny, nx) bool, True = solid (formed on first use)."""
+        if self._solid is None:
+            self._solid = self._mask != 0
+        return self._solid
 
     @classmethod
     def from_problem(cls, prob, **kw):
@@ -358,8 +368,17 @@ class Chip:
     def step(self, n=1):
         self._check(self._lib.lbm_step(self._h, int(n)))
 
-    def fields(self):
-        out = [np.empty((self.ny, self.nx), np.float32) for _ in range(4)]
+    def fields(self, out=None):
+        """rho, ux, uy, C as (ny, nx) float32 arrays; ``out``: four
+        C-contiguous float32 arrays of that shape to fill instead (e.g.
+        page-locked ones, which the device copies into faster)."""
+        if out is None:
+            out = [np.empty((self.ny, self.nx), np.float32) for _ in range(4)]
+        else:
+            out = list(out)
+            for a in out:
+                if a.dtype != np.float32 or a.shape != (self.ny, self.nx) or not a.flags.c_contiguous:
+                    raise ValueError("fields(out=...): four C-contiguous float32 (ny, nx) arrays")
         self._check(self._lib.lbm_get_fields(self._h, *[_fp(a) for a in out]))
         return tuple(out)  # rho, ux, uy, C
 

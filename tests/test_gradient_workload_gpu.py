@@ -18,14 +18,28 @@ FP64 oracle on the 128 x 64 copy: D(1e-3) = -10.830 against the exact
 extrapolation (4 D(h/2) - D(h)) / 3 of the central differences at h = 1e-3
 and h/2, which removes the h^2 term, within 1e-3 relative; the plain
 D(1e-3) must agree within 1e-3 plus its own truncation error, estimated as
-(4/3) |D(h) - D(h/2)|.  J is linear in C_in (the scalar is linear in its
-boundary values for a given flow), so those differences are exact up to
-rounding.
+(4/3) |D(h) - D(h/2)|.
+
+The forward runs are FP32, so J itself carries rounding noise; between two
+runs whose inputs differ slightly it is about 2e-6 on these workloads
+(measured: the C_in differences below at h = 1e-3 and h/2 scatter by 1e-3
+around the exact value), i.e. about 1e-3 in D(1e-3).  That is small next to
+dJ/dtau_c and dJ/du_max (10 to 180 here) but not next to a C_in derivative
+(0.017 to 0.4 on the copy).  J is exactly quadratic in C_in, though: for a
+given flow the scalar lattice is linear in its populations and affine in the
+held concentrations, so C at the objective is affine in C_in and a central
+difference is exact at any step.  The C_in rows therefore take the step
+H_CIN = 0.5, where the noise is 2e-6 relative to the differences in J; the
+differences at h = 1e-3 are printed beside them.
 
 The full-size chip starts the 4000-step window from the state a spin-up of
 SPINUP steps from rest leaves: from rest, the scalar front advances about
 100 nodes in 4000 steps and stays 300 nodes short of the chamber, so every
 derivative of the chamber objective would be zero to working precision.
+The window ends (step 30000) before the compound reaches the outlets: at
+tau_c = 0.51 the scalar's do-nothing outlet does not stay bounded once it
+carries compound (the FP64 oracle on this chip: max C 1.09 at step 30000,
+1e15 at 35000, growing from the outlet column next to the channel walls).
 Within any 4000-step window a change at the inlet travels at most about 160
 nodes (u_max = 0.04), so dJ/dC_in is zero on this chip: the adjoint gives
 zero and the differences give zero, which the test checks as such; the
@@ -42,9 +56,10 @@ from paper_1307_4703_gb300 import lbm, workloads as W  # noqa: E402
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
-H = 1e-3        # finite-difference step
+H = 1e-3        # finite-difference step (tau_c, u_max)
+H_CIN = 0.5     # step of the C_in rows, on which J depends quadratically
 GRAD_TOL = 1e-3  # relative
-SPINUP = 40000   # steps from rest before the window of the full-size chip
+SPINUP = 26000   # steps from rest before the window of the full-size chip
 
 
 def _objective(prob):
@@ -65,6 +80,7 @@ def _J(prob, blob, n, obj):
             c.load_state(blob)
         c.step(n)
         C = c.fields()[3].astype(np.float64)
+    assert np.abs(C).max() < 2.0  # the run stayed in the stable regime (see SPINUP)
     return float((wt * (C[oy, ox] - tg) ** 2).sum())
 
 
@@ -90,12 +106,27 @@ def _perturbations(prob, rows):
     return [("tau_c", tau), ("u_max", umax)] + [("C_in[%d]" % r, cin(r)) for r in rows]
 
 
+def _D(prob, blob, n, obj, perturb, h):
+    """Central difference at step h."""
+    return (_J(perturb(prob, h), blob, n, obj) - _J(perturb(prob, -h), blob, n, obj)) / (2 * h)
+
+
 def _differences(prob, blob, n, obj, perturb):
     """Central differences at h and h/2."""
-    def D(h):
-        return (_J(perturb(prob, h), blob, n, obj) - _J(perturb(prob, -h), blob, n, obj)) / (2 * h)
+    return _D(prob, blob, n, obj, perturb, H), _D(prob, blob, n, obj, perturb, H / 2)
 
-    return D(H), D(H / 2)
+
+def _check_cin(name, adj, prob, blob, n, obj, perturb, zero_scale=None):
+    """A C_in row: the adjoint against the (exact) central difference at
+    H_CIN; zero_scale set: the derivative is zero, within the FP32 noise."""
+    d = _D(prob, blob, n, obj, perturb, H_CIN)
+    d3 = _D(prob, blob, n, obj, perturb, H)
+    print("%-10s adjoint %.8g  D(%.1f) %.8g  rel %.2e  (D(1e-3) %.8g)"
+          % (name, adj, H_CIN, d, abs(adj - d) / max(abs(adj), 1e-300), d3))
+    if zero_scale is None:
+        assert abs(adj - d) <= GRAD_TOL * abs(adj), (name, adj, d)
+    else:
+        assert abs(adj) <= 1e-9 * zero_scale and abs(d) <= 1e-6 * zero_scale, (name, adj, d)
 
 
 def _adjoint_values(prob, got, rows):
@@ -103,19 +134,21 @@ def _adjoint_values(prob, got, rows):
     return [dt, float((du * prob["edge_u"]).sum() / prob["u_max"])] + [float(dc[W.WEST, r]) for r in rows]
 
 
-def _check_against_differences(name, adj, dh, dh2, scale):
+def _check_against_differences(name, adj, dh, dh2):
     rich = (4 * dh2 - dh) / 3
     trunc = 4.0 / 3.0 * abs(dh - dh2)
-    floor = 1e-9 * scale  # a derivative that is zero to working precision
-    assert abs(adj - rich) <= GRAD_TOL * abs(adj) + floor, (name, adj, rich, dh, dh2)
-    assert abs(adj - dh) <= GRAD_TOL * abs(adj) + trunc + floor, (name, adj, dh, trunc)
+    print("%-10s adjoint %.8g  D(h) %.8g  D(h/2) %.8g  Richardson %.8g  rel %.2e (D(h): %.2e)"
+          % (name, adj, dh, dh2, rich, abs(adj - rich) / max(abs(adj), 1e-300), abs(adj - dh) / max(abs(adj), 1e-300)))
+    assert abs(adj - rich) <= GRAD_TOL * abs(adj), (name, adj, rich, dh, dh2)
+    assert abs(adj - dh) <= GRAD_TOL * abs(adj) + trunc, (name, adj, dh, trunc)
     return rich
 
 
 def test_gradient_chip_against_central_differences():
     """1024 x 512, 4000 steps from the spun-up state, checkpoints every 250
-    steps: dJ/dtau_c, dJ/du_max and five C_in rows against central
-    differences (h = 1e-3, with Richardson extrapolation against h/2)."""
+    steps: dJ/dtau_c and dJ/du_max against central differences (h = 1e-3,
+    with Richardson extrapolation against h/2); five C_in rows, whose
+    derivatives are zero on this chip, both ways."""
     prob = W.config_adjoint_chip()
     n = prob["steps"]
     obj = _objective(prob)
@@ -130,17 +163,19 @@ def test_gradient_chip_against_central_differences():
         got = c.adjoint(n, *obj, ckpt_every=250)
     adj = _adjoint_values(prob, got, rows)
     J0 = _J(prob, blob, n, obj)
+    print("chip-1024x512 window %d..%d: J %.9g, adjoint dJ/dtau_c %.6g dJ/du_max %.6g dJ/dC_in %s"
+          % (SPINUP, SPINUP + n, got[0], adj[0], adj[1], adj[2:]))
     assert abs(got[0] / J0 - 1) < 1e-6
     # the spun-up state puts compound at the chamber's centre column
-    assert abs(adj[0]) > 1e-2 and abs(adj[1]) > 1e-2, adj
+    assert abs(adj[0]) > 1e-4 and abs(adj[1]) > 1e-4, adj
     scale = max(abs(adj[0]), abs(adj[1]))
     for (name, perturb), a in zip(_perturbations(prob, rows), adj):
-        dh, dh2 = _differences(prob, blob, n, obj, perturb)
-        _check_against_differences(name, a, dh, dh2, scale)
         if name.startswith("C_in"):
             # no inlet change reaches the chamber within the window
-            assert abs(a) <= 1e-9 * scale and abs(dh) <= 1e-9 * scale and abs(dh2) <= 1e-9 * scale, \
-                (name, a, dh, dh2)
+            _check_cin(name, a, prob, blob, n, obj, perturb, zero_scale=scale)
+        else:
+            dh, dh2 = _differences(prob, blob, n, obj, perturb)
+            _check_against_differences(name, a, dh, dh2)
 
 
 def test_gradient_copy_128x64_against_central_differences():
@@ -156,7 +191,9 @@ def test_gradient_copy_128x64_against_central_differences():
     adj = _adjoint_values(prob, got, rows)
     assert abs(got[0] / _J(prob, None, n, obj) - 1) < 1e-6
     assert min(abs(a) for a in adj) > 1e-3, adj
-    scale = max(abs(a) for a in adj)
     for (name, perturb), a in zip(_perturbations(prob, rows), adj):
-        dh, dh2 = _differences(prob, None, n, obj, perturb)
-        _check_against_differences(name, a, dh, dh2, scale)
+        if name.startswith("C_in"):
+            _check_cin(name, a, prob, None, n, obj, perturb)
+        else:
+            dh, dh2 = _differences(prob, None, n, obj, perturb)
+            _check_against_differences(name, a, dh, dh2)
