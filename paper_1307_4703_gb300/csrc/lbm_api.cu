@@ -15,6 +15,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_internal.h"
 
@@ -190,6 +192,22 @@ struct lbm_ctx {
 };
 
 namespace {
+
+// A named range on the host timeline for the duration of a library call (or
+// a phase of one), for profilers that read NVTX; with none attached a range
+// costs a test and a branch.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { end(); }
+    void end()
+    {
+        if (open) nvtxRangePop();
+        open = false;
+    }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+    bool open = true;
+};
 
 lbm_status fail(lbm_ctx* h, lbm_status s, const char* fmt, ...)
 {
@@ -779,11 +797,13 @@ lbm_status lbm_create(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* ma
                       double tau_c, int32_t n_ports, const lbm_port* ports, const float* edge_u,
                       const float* edge_C, const lbm_options* opt_in)
 {
+    Range range("lbm_create");
     return create_impl(out, nx, ny, mask, tau, tau_c, n_ports, ports, edge_u, edge_C, opt_in, nullptr);
 }
 
 lbm_status lbm_create_batch(lbm_handle* out, int32_t n, const lbm_chip_desc* chips, const lbm_options* opt)
 {
+    Range range("lbm_create_batch");
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > kMaxInstances) return fail(nullptr, LBM_ERR_ARG, "n = %d outside [1, %d]", n, kMaxInstances);
@@ -986,6 +1006,7 @@ extern "C" {
 
 lbm_status lbm_step(lbm_handle h, int64_t n)
 {
+    Range range("lbm_step");
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
     if (lbm_status js = join_scalar(h)) return js;
@@ -1056,6 +1077,7 @@ static double* device_address(double* p)
 
 lbm_status lbm_step_diagnostics(lbm_handle h, int64_t n, double* out)
 {
+    Range range("lbm_step_diagnostics");
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (n < 0) return fail(h, LBM_ERR_ARG, "n = %lld < 0", (long long)n);
     if (n == 0) return LBM_OK;
@@ -1136,6 +1158,7 @@ lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy,
 
 lbm_status lbm_get_fields(lbm_handle h, float* rho, float* ux, float* uy, float* C)
 {
+    Range range("lbm_get_fields");
     if (check_ctx(h)) return LBM_ERR_ARG;
     const size_t n = size_t(h->nx) * h->ny;
     float* t = h->fields_tmp;
@@ -1347,6 +1370,7 @@ struct StateHeader {
 
 lbm_status lbm_save_state(lbm_handle h, void* buf, size_t* bytes)
 {
+    Range range("lbm_save_state");
     if (check_ctx(h) || !bytes) return fail(h, LBM_ERR_ARG, "bytes is NULL");
     const size_t pop = size_t(h->nx) * h->ny * lbm::kPlanes * h->elem;
     const size_t need = sizeof(StateHeader) + h->schedule.size() * 4 + pop;
@@ -1373,6 +1397,7 @@ lbm_status lbm_save_state(lbm_handle h, void* buf, size_t* bytes)
 
 lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes)
 {
+    Range range("lbm_load_state");
     if (check_ctx(h) || !buf) return fail(h, LBM_ERR_ARG, "buf is NULL");
     StateHeader hd;
     if (bytes < sizeof(hd)) return fail(h, LBM_ERR_ARG, "state buffer too short");
@@ -1405,6 +1430,7 @@ namespace {
 lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_t K, double* J,
                        double* dJ_dtau_c, double* dJ_du_in, double* dJ_dC_in)
 {
+    Range range("lbm_adjoint");
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_adjoint");
     if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_adjoint");
@@ -1461,6 +1487,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
                     n_ck, seg_slots);
 
     // forward sweep with checkpoints (the handle advances as in lbm_step)
+    Range forward_range("lbm_adjoint: forward sweep");
     lbm::StepArgs a{};
     a.links = h->links;
     a.rowbc = h->rowbc;
@@ -1579,6 +1606,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         h->step += len;
     }
 
+    forward_range.end();
     // J and dJ/dP(n)
     std::vector<int> hx(obj->x, obj->x + obj->n), hy(obj->y, obj->y + obj->n);
     LBM_CUDA(h, cudaMemcpyAsync(ox, hx.data(), hx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1604,6 +1632,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     }
 
     // backward, segment by segment
+    Range reverse_range("lbm_adjoint: recomputation and reverse sweep");
     lbm::AdjointArgs A{};
     A.links = h->links;
     A.rowbc = h->rowbc;
@@ -1758,6 +1787,7 @@ lbm_status lbm_set_velocity_field(lbm_handle h, uint32_t open_mask, const float*
 
 lbm_status lbm_scalar_step(lbm_handle h, int64_t n, double u_scale)
 {
+    Range range("lbm_scalar_step");
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (h->precision != LBM_FP32) return fail(h, LBM_ERR_STATE, "%s needs FP32 storage", "lbm_scalar_step");
     if (!h->inst.empty()) return fail(h, LBM_ERR_STATE, "%s works on a single chip, not a batch", "lbm_scalar_step");
@@ -1836,6 +1866,7 @@ lbm_status lbm_get_step(lbm_handle h, int64_t* t)
 
 lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
 {
+    Range range("lbm_autotune");
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (trial_steps < 0 || trial_steps > 10000) return fail(h, LBM_ERR_ARG, "trial_steps = %d outside [0, 10000]", trial_steps);
     if (trial_steps == 0) trial_steps = 20;

@@ -135,6 +135,30 @@ def config_adjoint_chip(nx=1024, ny=512, seed=SEED):
     return prob
 
 
+def channel_flow_fields(problem):
+    """Stand-in stationary velocity fields of a two-channel chip, one per
+    valve word of its schedule, for the scalar-only workflow of the paper
+    (section "Results": the flow of each valve state is computed once and
+    stored, and the compound is advanced on it): every open channel carries
+    its inlet's parabolic profile u_x(y) unchanged from its inlet column to
+    its outlet column; the closed channel and the chamber are at rest.
+    Returns {valve word: (ux, uy)} of (ny, nx) arrays."""
+    ny, nx = problem["ny"], problem["nx"]
+    eu = np.asarray(problem["edge_u"], np.float64)
+    out = {}
+    for word in sorted(set(int(w) for w in problem["states"])):
+        ux = np.zeros((ny, nx))
+        for p in problem["ports"]:
+            if p["side"] != WEST or p["kind"] != VELOCITY or not (word >> p["channel"]) & 1:
+                continue
+            east = [q for q in problem["ports"] if q["channel"] == p["channel"] and q["side"] == EAST]
+            x1 = east[0]["x"] if east else nx - 1
+            ux[p["y0"]:p["y1"], p["x"]:x1 + 1] = eu[WEST, p["y0"]:p["y1"], None]
+        ux[np.asarray(problem["solid"]) != 0] = 0.0
+        out[word] = (ux, np.zeros((ny, nx)))
+    return out
+
+
 def config_batch(n=64, steps=10000, seed=SEED):
     """``n`` independent two-channel chips for the batched step, drawn with
     PCG64: nx uniform over the multiples of 64 in [256, 1024], ny = nx / 2,

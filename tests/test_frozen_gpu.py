@@ -155,3 +155,49 @@ def test_scalar_kernel_variants_are_bit_identical(paper_ports, decay):
         chip.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert np.allclose(out[0][2], out[1][2], rtol=1e-12, atol=1e-9)
+
+
+def test_full_chip_chamber_profile_in_the_papers_workflow():
+    """The 1024 x 768 chip (tau_c = 0.52, the largest diffusivity of its
+    range) in the paper's workflow: a stationary velocity field per valve
+    state (the channel-flow stand-ins of workloads.channel_flow_fields) and
+    40000 scalar-only steps with the valves switching every 2000 steps, so
+    that compound has reached the chamber (the top channel's front passes
+    the chamber's centre column near step 22000) and the gradient along y at
+    its centre column has started to form.  Every concentration against the
+    FP64 oracle (its all-cores build) within the whole-run bound 1e-4.
+    (The steady chamber gradient itself needs about (568 rows)^2 / D = 5e7
+    steps at this size, out of the oracle's reach.)"""
+    prob = W.config_full_chip(tau_c=0.52)
+    fields = W.channel_flow_fields(prob)
+    n, period = 40000, prob["period"]
+    chip = lbm.Chip.from_problem(prob)
+    for w, (fx, fy) in fields.items():
+        chip.set_velocity_field(w, fx, fy)
+    chip.set_valve_schedule(period, prob["states"])
+    chip.scalar_step(n, 1.0)
+    C = chip.fields()[3]
+    chip.close()
+    # the oracle: step t completes the ports of w(t) and collides with the
+    # field of w(t - 1) (see the module docstring); both start at C = 0
+    L = oracle.from_problem(prob, parallel=True)
+    t = 0
+    while t < n:
+        w = W.valve_word(prob, t)
+        L.scalar_step(w, *fields[W.valve_word(prob, max(t - 1, 0))], n=1)
+        t += 1
+        m = min(period - t % period, n - t) if t % period else 0
+        if m:
+            L.scalar_step(w, *fields[w], n=m)
+            t += m
+    rC = L.fields()[3]
+    fl = ~L.solid
+    dC = np.abs(C - rC)[fl].max()
+    cx0, cx1, cy0, cy1 = prob["chamber"]
+    col = rC[cy0:cy1, (cx0 + cx1) // 2]
+    print("chip-1024x768 frozen-velocity run, %d steps: max|dC| %.3e; chamber centre column C top %.4f, "
+          "rows above 1e-3: %d" % (n, dC, col[-1], int((col > 1e-3).sum())))
+    assert dC <= 1e-4, dC
+    # compound has entered the chamber from the top channel, and none from the bottom one
+    assert col[-1] > 1e-3 and abs(col[0]) < 1e-6
+    L.close()
