@@ -654,6 +654,20 @@ __device__ __forceinline__ void pull_quad(float4 (&v)[kN], const T* __restrict__
     }
 }
 
+// Which lanes of a warp tile load plane values, from the tile's table entry
+// alone: own = the lane lies in the quad range [q0, q1] that holds the
+// tile's fluid; west / east = its edge value feeds a lane of that range
+// through the x - 1 / x + 1 shift.  Every lane holding fluid is in the
+// range, so the loads can go out before the lane's wall-link word arrives.
+struct LoadRange {
+    bool own, west, east;
+};
+__device__ __forceinline__ LoadRange load_range(uint2 tile, int lane)
+{
+    const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
+    return LoadRange{lane >= q0 && lane <= q1, lane >= q0 - 1 && lane <= q1, lane >= q0 && lane <= q1 + 1};
+}
+
 // Open ports, moments and both collisions for the four nodes x0..x0+3 of a
 // row whose port entries are bw (west) and be (east); v holds the streamed
 // populations on entry and the post-collision populations on exit (fluid

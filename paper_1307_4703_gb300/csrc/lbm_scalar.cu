@@ -292,14 +292,15 @@ __global__ void __launch_bounds__(128) scalar_frozen_regs(const ScalarArgs a)
         const int halo_w = x0 > 0 ? -1 : 0;
         const int halo_e = x0 + 4 < a.pitch ? 4 : 3;
         const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
-        const bool act = lk != 0xFFFFFFFFu;
-        const unsigned ball = __ballot_sync(kFull, act);
-        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;
-        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;
+        // loads from the tile's fluid range, beside the wall-link word (see
+        // load_range)
+        const LoadRange r = load_range(tile, lane);
         float4 v[5];
-        pull_quad<false, float, 9, 5>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
+        pull_quad<false, float, 9, 5>(v, S, P, oC, oS, oN, halo_w, halo_e, r.own, r.west, r.east, lane);
+        const float4 ux4 = r.own ? ldg4(a.ux + oC) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 uy4 = r.own ? ldg4(a.uy + oC) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool act = lk != 0xFFFFFFFFu;
         if (!act) continue;
-        const float4 ux4 = ldg4(a.ux + oC), uy4 = ldg4(a.uy + oC);
         const RowBC bw = a.rowbc[y];
         const RowBC be = a.rowbc[a.ny + y];
         scalar_quad(v, lk, x0, bw, be, ux4, uy4, a, S, P, oC, sc, sq, bad);
