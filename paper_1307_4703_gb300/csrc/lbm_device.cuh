@@ -677,6 +677,7 @@ __device__ __forceinline__ LoadRange load_range(uint2 tile, int lane)
 __device__ __forceinline__ bool valve_open(const StepArgs& a, int chan_kind)
 {
     const int ch = chan_kind & 0xFF;
+    if (ch < 32) return (a.open_mask[0] >> ch) & 1u;  // a single chip's channels
     uint32_t w = a.open_mask[0];
 #pragma unroll
     for (int j = 1; j < kMaskWords; ++j)
@@ -728,8 +729,11 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
                                              const RowBC& be, const StepArgs& a, const T* S, long long oC,
                                              float2 omega, QuadAcc& acc)
 {
-    const bool open_w = bw.x >= 0 && valve_open(a, bw.chan_kind);
-    const bool open_e = be.x >= 0 && valve_open(a, be.chan_kind);
+    // a port entry exists on a few rows only (the entries are the same for
+    // the whole warp, so the tests below branch uniformly)
+    bool open_w = false, open_e = false;
+    if (bw.x >= 0) open_w = valve_open(a, bw.chan_kind);
+    if (be.x >= 0) open_e = valve_open(a, be.chan_kind);
     const float dfac = a.decay != 0.f ? 1.f - a.decay / omega.y : 1.f;
     // With 16-bit storage the scalar populations stay in their stored form
     // g_i - w_i C_ref here (C_ref = kCRef), as the fluid ones stay f_i - w_i:
