@@ -587,7 +587,8 @@ def _profile_target(args, device):
         e1.record(stream)
         stream.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / max(args.steps, 1)
-        out = {"kernel": "scalar_frozen_bulk", "workload": prob["name"], "us_per_step": us,
+        out = {"kernel": "lbm_scalar_step (default kernel: scalar_frozen_regs)", "workload": prob["name"],
+               "us_per_step": us,
                "glups": W.fluid_count(prob) / us / 1e3}
     else:
         prob = W.config_adjoint_chip()
