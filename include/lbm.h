@@ -127,7 +127,11 @@ typedef struct {
                                2 = bulk-copy pipeline through shared memory with a producer warp,
                                3 = bulk-copy pipeline in which every warp refills its own stages,
                                4 = registers, each warp's next tile prefetched into shared memory
-                                   by per-lane asynchronous copies (halfway bounce-back only) */
+                                   by per-lane asynchronous copies (halfway bounce-back only),
+                                   5 = registers and warp shuffles on 64-node tiles, two nodes per
+                                   lane (FP32 storage, halfway bounce-back, blocks of at most 128
+                                   threads): more, smaller tiles for small chips.
+                               Every variant gives the same bits. */
     int32_t pipeline_stages;/* variants 2, 3: shared-memory stages per computing warp, 0 = default
                                (1, or 2 with 16-bit storage);
                                computing warps x stages <= 24 */
@@ -384,7 +388,8 @@ typedef struct {
     int32_t pitch;          /* elements per stored row (multiple of 128) */
     int32_t n_tiles;        /* 128-node row segments that hold fluid */
     int32_t grid, block;    /* step kernel launch shape */
-    int32_t variant;        /* 1 registers, 2 bulk-copy pipeline with producer warp, 3 self-refilling warps */
+    int32_t variant;        /* 1 registers, 2 bulk-copy pipeline with producer warp, 3 self-refilling warps,
+                               4 registers with asynchronous prefetch, 5 registers on 64-node tiles */
     int32_t stages;         /* shared-memory stages per block (variants 2, 3), 0 otherwise */
     int64_t fluid_nodes;
     int64_t algorithmic_bytes_per_step;  /* fluid_nodes * 28 * element size: 14 populations read and

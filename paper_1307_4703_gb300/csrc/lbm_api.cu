@@ -73,12 +73,14 @@ struct lbm_ctx {
     uint8_t* links = nullptr;
     lbm::RowBC* rowbc = nullptr;
     uint2* tiles = nullptr;
+    uint2* tiles64 = nullptr;  // the same row segments in 64-node halves (variant 5)
     double* partials = nullptr;
     double* diag = nullptr;       // 4 totals formed by lbm_get_diagnostics
     unsigned int* err = nullptr;
     float* fields_tmp = nullptr;  // 4 * nx * ny floats
 
     int n_tiles = 0;
+    int n_tiles64 = 0;
     int sms = 0;
     int partials_cap = 0;  // blocks the partials buffer holds (any launch shape fits)
     int diag_grid = 0;     // blocks whose partials the last step wrote
@@ -281,10 +283,6 @@ bool is_fluid(const uint8_t* mask, int nx, int ny, int x, int y)
     return x >= 0 && x < nx && y >= 0 && y < ny && mask[size_t(y) * nx + x] == 0;
 }
 
-// Eq. lattice directions 1..8 (index 0 is the rest direction).
-constexpr int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-constexpr int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-
 // One step: the paper's wall values first (when that wall scheme is on),
 // then the step kernel.
 cudaError_t launch_full_step(const lbm_ctx* h, const lbm::StepArgs& a, const lbm::StepLaunch& L, cudaStream_t s)
@@ -339,7 +337,8 @@ lbm_status step_graph(lbm_ctx* h, lbm::StepArgs a, cudaGraphExec_t* out)
 int wave_grid(const lbm_ctx* h, const lbm::StepLaunch& L, int per_sm)
 {
     const int tiles_per_block = L.variant == lbm::kVariantBulk ? 1 : L.block / 32;  // tiles in flight at once
-    const int need = (h->n_tiles + tiles_per_block - 1) / tiles_per_block;
+    const int tiles = L.variant == lbm::kVariantPairs ? h->n_tiles64 : h->n_tiles;
+    const int need = (tiles + tiles_per_block - 1) / tiles_per_block;
     return std::max(1, std::min(need, per_sm * h->sms));
 }
 
@@ -442,8 +441,13 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         return fail(nullptr, LBM_ERR_ARG, "block_threads = %d: use 0 or a multiple of 32 in [64, 256]",
                     opt.block_threads);
     if (opt.max_blocks < 0) return fail(nullptr, LBM_ERR_ARG, "max_blocks = %d < 0", opt.max_blocks);
-    if (opt.variant < 0 || opt.variant > 4)
-        return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1, 2, 3 or 4", opt.variant);
+    if (opt.variant < 0 || opt.variant > 5)
+        return fail(nullptr, LBM_ERR_ARG, "variant = %d: use 0, 1, 2, 3, 4 or 5", opt.variant);
+    if (opt.variant == 5 && (opt.precision != LBM_FP32 || opt.wall_scheme != LBM_WALL_BOUNCE_BACK))
+        return fail(nullptr, LBM_ERR_ARG, "variant 5 needs FP32 storage and bounce-back walls");
+    if (opt.variant == 5 && opt.block_threads > 128)
+        return fail(nullptr, LBM_ERR_ARG, "block_threads = %d: variant 5 runs blocks of 64 or 128 threads",
+                    opt.block_threads);
     if (opt.precision != LBM_FP32 && opt.precision != LBM_FP16 && opt.precision != LBM_BF16)
         return fail(nullptr, LBM_ERR_ARG, "precision = %d: use LBM_FP32, LBM_FP16 or LBM_BF16", opt.precision);
     if (opt.precision != LBM_FP32 && opt.variant == 3)
@@ -554,7 +558,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     // reported)
     std::vector<uint8_t> links(size_t(pitch) * ny, lbm::kSolid);
     struct RowsOut {
-        std::vector<uint2> tiles;
+        std::vector<uint2> tiles, tiles64;
         long long fluid = 0;
         int bad_x = -1, bad_y = -1;
     };
@@ -581,6 +585,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
             const uint8_t* N = rows[2] + 1;
             uint8_t* L = links.data() + size_t(y) * pitch;
             int s_cur = -1, q0 = -1, q1 = -1;  // segment and its first and last quad holding fluid
+            int h_cur = -1, p0 = -1, p1 = -1;  // the same for 64-node segments and node pairs
             for (int x = 0; x < nx; ++x) {
                 if (C[x]) continue;
                 // bit i - 1: the pull source x - e_i is not fluid (directions of Eq. lattice)
@@ -603,10 +608,22 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
                     q0 = q;
                 }
                 q1 = q;
+                const int hg = x / lbm::kPairTileNodes, pr = (x % lbm::kPairTileNodes) / 2;
+                if (hg != h_cur) {
+                    if (h_cur >= 0)
+                        out.tiles64.push_back(make_uint2((uint32_t(y) << lbm::kSegBits64) | uint32_t(h_cur),
+                                                         uint32_t(p0) | (uint32_t(p1) << 8)));
+                    h_cur = hg;
+                    p0 = pr;
+                }
+                p1 = pr;
             }
             if (s_cur >= 0)
                 out.tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s_cur),
                                                uint32_t(q0) | (uint32_t(q1) << 8)));
+            if (h_cur >= 0)
+                out.tiles64.push_back(make_uint2((uint32_t(y) << lbm::kSegBits64) | uint32_t(h_cur),
+                                                 uint32_t(p0) | (uint32_t(p1) << 8)));
             std::swap(rows[0], rows[1]);
             std::swap(rows[1], rows[2]);
         }
@@ -623,12 +640,13 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         build_rows(0, int((long long)ny / n_thr), parts[0]);
         for (auto& t : pool) t.join();
     }
-    std::vector<uint2> tiles;
+    std::vector<uint2> tiles, tiles64;
     long long fluid = 0;
     for (const RowsOut& r : parts) {
         if (r.bad_y >= 0)
             return fail(nullptr, LBM_ERR_ARG, "fluid node (%d, %d) has no fluid neighbour", r.bad_x, r.bad_y);
         tiles.insert(tiles.end(), r.tiles.begin(), r.tiles.end());
+        tiles64.insert(tiles64.end(), r.tiles64.begin(), r.tiles64.end());
         fluid += r.fluid;
     }
     if (fluid == 0) return fail(nullptr, LBM_ERR_ARG, "the mask has no fluid node");
@@ -654,6 +672,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->free_fn = opt.free;
     h->alloc_user = opt.alloc_user;
     h->n_tiles = int(tiles.size());
+    h->n_tiles64 = int(tiles64.size());
     h->solid.assign(mask, mask + size_t(nx) * ny);
     h->fluid = fluid;
     h->precision = opt.precision;
@@ -692,6 +711,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     L.variant = variant == 1   ? lbm::kVariantRegs
                 : variant == 3 ? lbm::kVariantPipe
                 : variant == 4 ? lbm::kVariantAsync
+                : variant == 5 ? lbm::kVariantPairs
                                : lbm::kVariantBulk;
     L.precision = opt.precision;
     L.pdl = true;  // consecutive steps overlap launch and set-up with the previous step's tail
@@ -730,6 +750,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->links = static_cast<uint8_t*>(dev_alloc(h, links.size()));
     h->rowbc = static_cast<lbm::RowBC*>(dev_alloc(h, rowbc.size() * sizeof(lbm::RowBC)));
     h->tiles = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, tiles.size()) * sizeof(uint2)));
+    h->tiles64 = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, tiles64.size()) * sizeof(uint2)));
     h->partials_cap = std::max(h->launch.grid, sms * kMaxBlocksPerSM);
     h->diag_grid = h->launch.grid;
     h->partials = static_cast<double*>(dev_alloc(h, size_t(h->partials_cap) * 4 * sizeof(double)));
@@ -755,7 +776,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         h->wallv = dev_alloc(h, size_t(8) * h->plane * h->elem);
         h->woff = static_cast<long long*>(dev_alloc(h, std::max<size_t>(1, woff.size()) * sizeof(long long)));
     }
-    if (!h->pop[0] || !h->pop[1] || !h->links || !h->rowbc || !h->tiles || !h->partials ||
+    if (!h->pop[0] || !h->pop[1] || !h->links || !h->rowbc || !h->tiles || !h->tiles64 || !h->partials ||
         !h->err || !h->diag || !h->fields_tmp || (batch && !h->rates) ||
         (opt.wall_scheme == LBM_WALL_EQUILIBRIUM && (!h->wallv || !h->woff)))
         return bail(fail(h, LBM_ERR_OOM, "device allocation of %zu bytes failed", 2 * pop_bytes));
@@ -768,6 +789,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !tiles.empty())
         e = cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !tiles64.empty())
+        e = cudaMemcpyAsync(h->tiles64, tiles64.data(), tiles64.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && batch)
         e = cudaMemcpyAsync(h->rates, batch->rates.data(), size_t(ny) * sizeof(float4), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !woff.empty())
@@ -982,6 +1005,8 @@ static lbm::StepArgs step_args(const lbm_ctx* h)
     a.rowbc = h->rowbc;
     a.tiles = h->tiles;
     a.n_tiles = h->n_tiles;
+    a.tiles64 = h->tiles64;
+    a.n_tiles64 = h->n_tiles64;
     a.ny = h->ny;
     a.pitch = h->pitch;
     a.plane = h->plane;
@@ -1493,6 +1518,8 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     a.rowbc = h->rowbc;
     a.tiles = h->tiles;
     a.n_tiles = h->n_tiles;
+    a.tiles64 = h->tiles64;
+    a.n_tiles64 = h->n_tiles64;
     a.ny = h->ny;
     a.pitch = h->pitch;
     a.plane = h->plane;
@@ -1877,6 +1904,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
                                {2, 4, 1}, {2, 2, 2}, {2, 3, 2}, {2, 4, 2}};
     if (h->precision == LBM_FP32) cands.push_back({3, 4, 1});
     else cands.push_back({2, 3, 3});
+    if (h->precision == LBM_FP32 && !h->wallv) cands.push_back({5, 4, 0});
     // trials write to scratch buffers: the state, step count and diagnostics stay as they are
     Scratch sc(h);
     void* dst = sc.get(size_t(h->plane) * lbm::kPlanes * h->elem);
@@ -1891,6 +1919,8 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     a.rowbc = h->rowbc;
     a.tiles = h->tiles;
     a.n_tiles = h->n_tiles;
+    a.tiles64 = h->tiles64;
+    a.n_tiles64 = h->n_tiles64;
     a.ny = h->ny;
     a.pitch = h->pitch;
     a.plane = h->plane;
@@ -1924,8 +1954,8 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         L.pdl = true;
         L.walls = h->wallv != nullptr;
         if (L.walls && (c.variant == 3 || c.variant == 4)) continue;
-        if (c.variant == 1 || c.variant == 4) {
-            L.variant = c.variant == 1 ? lbm::kVariantRegs : lbm::kVariantAsync;
+        if (c.variant == 1 || c.variant == 4 || c.variant == 5) {
+            L.variant = c.variant == 1 ? lbm::kVariantRegs : c.variant == 4 ? lbm::kVariantAsync : lbm::kVariantPairs;
             L.block = 32 * c.warps;
             L.stages = 0;
         } else if (c.variant == 2) {

@@ -57,6 +57,16 @@ __device__ __forceinline__ void stg4(float* p, const float4& v)
 {
     *reinterpret_cast<float4*>(p) = v;
 }
+__device__ __forceinline__ float2 ldg2(const float* p)
+{
+    return __ldg(reinterpret_cast<const float2*>(p));
+}
+__device__ __forceinline__ void stg2(float* p, const float2& v)
+{
+    *reinterpret_cast<float2*>(p) = v;
+}
+__device__ __forceinline__ float& at(float2& v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ float at(const float2& v, int k) { return k == 0 ? v.x : v.y; }
 __device__ __forceinline__ float& at(float4& v, int k)
 {
     return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
@@ -715,6 +725,68 @@ __device__ __forceinline__ bool port_node(float (&f)[9], float (&g)[5], bool wes
     return outlet;
 }
 
+// Moments (Eq. moments) and both BGK collisions of one node, in place: f as
+// deviations f_i - w_i from the rest state, g as stored (FP32: g_i; kDev:
+// g_i - w_i C_ref).  omega = {1 / tau_f, 1 / tau_g}; dfac = 1 - k / omega_g
+// with decay rate k (1 without decay).  Returns the moments the diagnostics
+// need.
+struct NodeMoments {
+    float rd, rho, jx, ux, C;
+};
+
+template <bool kDev>
+__device__ __forceinline__ NodeMoments collide_node(float (&f)[9], float (&g)[5], float2 omega, float dfac,
+                                                    const StepArgs& a)
+{
+    // ---- moments (Eq. moments) and BGK collision of f, in deviations
+    //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
+    const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const float rho = 1.f + rd;
+    const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const float inv = __fdividef(1.f, rho);  // fast reciprocal (2 ulp): rho stays near 1
+    const float ux = jx * inv, uy = jy * inv;
+    const float usq = 1.5f * (ux * ux + uy * uy);
+    const float wo = omega.x;
+    {
+        // f_eq_i - w_i = w_i [rho - 1 + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]
+        const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
+        const float q1 = rho * (4.5f * e1 * e1 - usq), q2 = rho * (4.5f * e2 * e2 - usq);
+        const float q5 = rho * (4.5f * e5 * e5 - usq), q6 = rho * (4.5f * e6 * e6 - usq);
+        const float t1 = 3.f * jx, t2 = 3.f * jy, t5 = t1 + t2, t6 = t2 - t1;
+        f[0] += wo * (kWr * (rd - rho * usq) - f[0]);
+        f[1] += wo * (kWa * (rd + t1 + q1) - f[1]);
+        f[3] += wo * (kWa * (rd - t1 + q1) - f[3]);
+        f[2] += wo * (kWa * (rd + t2 + q2) - f[2]);
+        f[4] += wo * (kWa * (rd - t2 + q2) - f[4]);
+        f[5] += wo * (kWd * (rd + t5 + q5) - f[5]);
+        f[7] += wo * (kWd * (rd - t5 + q5) - f[7]);
+        f[6] += wo * (kWd * (rd + t6 + q6) - f[6]);
+        f[8] += wo * (kWd * (rd - t6 + q6) - f[8]);
+    }
+    // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
+    float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+    if constexpr (kDev) C += kCRef;  // the weights add up to one
+    {
+        const float wg = omega.y;
+        // the reaction term R = -k C of Eq. cde enters as w_i R, which is
+        // omega (w_i R / omega): the equilibrium's isotropic part scaled by
+        // dfac = 1 - k / omega (exactly 1 without decay); for deviations
+        // the isotropic part is w_i (C dfac - C_ref)
+        const float Cd = kDev ? fmaf(C, dfac, -kCRef) : C * dfac;
+        const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
+        const float c1d = a.wg1 * Cd;
+        // rest equilibrium w0 C formed as the remainder, so that the five
+        // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)
+        g[0] += wg * ((Cd - 4.f * c1d) - g[0]);
+        g[1] += wg * ((c1d + cx) - g[1]);
+        g[3] += wg * ((c1d - cx) - g[3]);
+        g[2] += wg * ((c1d + cy) - g[2]);
+        g[4] += wg * ((c1d - cy) - g[4]);
+    }
+    return NodeMoments{rd, rho, jx, ux, C};
+}
+
 // Open ports, moments and both collisions of the quad.  Where the rare work
 // goes depends on the storage type, by measurement: the FP32 kernel waits on
 // its loads and is fastest with the port and solid-node handling inside the
@@ -792,52 +864,8 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
             if (pw || pe) outlet_k = port_node(f, g, pw, pw ? bw : be, a, S, oC + k);
         }
 
-        // ---- moments (Eq. moments) and BGK collision of f, in deviations
-        //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
-        const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const float rho = 1.f + rd;
-        const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        const float inv = __fdividef(1.f, rho);  // fast reciprocal (2 ulp): rho stays near 1
-        const float ux = jx * inv, uy = jy * inv;
-        const float usq = 1.5f * (ux * ux + uy * uy);
-        const float wo = omega.x;
-        {
-            // f_eq_i - w_i = w_i [rho - 1 + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]
-            const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
-            const float q1 = rho * (4.5f * e1 * e1 - usq), q2 = rho * (4.5f * e2 * e2 - usq);
-            const float q5 = rho * (4.5f * e5 * e5 - usq), q6 = rho * (4.5f * e6 * e6 - usq);
-            const float t1 = 3.f * jx, t2 = 3.f * jy, t5 = t1 + t2, t6 = t2 - t1;
-            f[0] += wo * (kWr * (rd - rho * usq) - f[0]);
-            f[1] += wo * (kWa * (rd + t1 + q1) - f[1]);
-            f[3] += wo * (kWa * (rd - t1 + q1) - f[3]);
-            f[2] += wo * (kWa * (rd + t2 + q2) - f[2]);
-            f[4] += wo * (kWa * (rd - t2 + q2) - f[4]);
-            f[5] += wo * (kWd * (rd + t5 + q5) - f[5]);
-            f[7] += wo * (kWd * (rd - t5 + q5) - f[7]);
-            f[6] += wo * (kWd * (rd + t6 + q6) - f[6]);
-            f[8] += wo * (kWd * (rd - t6 + q6) - f[8]);
-        }
-        // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
-        float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
-        if constexpr (kDev) C += kCRef;  // the weights add up to one
-        {
-            const float wg = omega.y;
-            // the reaction term R = -k C of Eq. cde enters as w_i R, which is
-            // omega (w_i R / omega): the equilibrium's isotropic part scaled by
-            // dfac = 1 - k / omega (exactly 1 without decay); for deviations
-            // the isotropic part is w_i (C dfac - C_ref)
-            const float Cd = kDev ? fmaf(C, dfac, -kCRef) : C * dfac;
-            const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
-            const float c1d = a.wg1 * Cd;
-            // rest equilibrium w0 C formed as the remainder, so that the five
-            // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)
-            g[0] += wg * ((Cd - 4.f * c1d) - g[0]);
-            g[1] += wg * ((c1d + cx) - g[1]);
-            g[3] += wg * ((c1d - cx) - g[3]);
-            g[2] += wg * ((c1d + cy) - g[2]);
-            g[4] += wg * ((c1d - cy) - g[4]);
-        }
+        const NodeMoments nm = collide_node<kDev>(f, g, omega, dfac, a);
+        const float rd = nm.rd, rho = nm.rho, jx = nm.jx, ux = nm.ux, C = nm.C;
 #pragma unroll
         for (int i = 0; i < 9; ++i) at(v[i], k) = f[i];
 #pragma unroll

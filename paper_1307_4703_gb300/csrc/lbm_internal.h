@@ -36,12 +36,14 @@ constexpr int kBulkMaxThreads = 256;        // bulk variant: at most 7 consumer 
 constexpr int kMaxStages = 24;             // bulk variant: largest shared-memory ring
 constexpr int kMaskWords = 8;              // valve channels per lattice: 32 * kMaskWords
 
-enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3, kVariantAsync = 4 };
+enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3, kVariantAsync = 4, kVariantPairs = 5 };
+constexpr int kPairTileNodes = 64;  // nodes per warp tile of variant 5: 32 lanes x 2 nodes
+constexpr int kSegBits64 = 13;      // 64-node tile encoding: segment in the low 13 bits
 enum Precision { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 constexpr float kCRef = 0.5f;  // reference concentration of 16-bit scalar storage
 
 struct StepLaunch {
-    int variant;  // kVariantRegs, kVariantBulk, kVariantPipe or kVariantAsync
+    int variant;  // kVariantRegs, kVariantBulk, kVariantPipe, kVariantAsync or kVariantPairs
     int grid;
     int block;
     int stages;   // shared-memory stages per block (computing warps x stages per warp)
@@ -65,6 +67,9 @@ struct StepArgs {
     const RowBC* rowbc;
     const uint2* tiles;
     int n_tiles;
+    const uint2* tiles64;   // the same lattice in 64-node row segments (variant 5):
+                            // x = (y << 13) | segment, y = first | (last << 8) lane (node pair) holding fluid
+    int n_tiles64;
     int reverse;            // 1: take the tiles from the end of the table (see tile_at)
     int ny;
     int pitch;

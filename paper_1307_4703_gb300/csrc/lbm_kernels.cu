@@ -429,6 +429,8 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
         if (l.precision == kFP16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__half, false>, a);
         else if (l.precision == kBF16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__nv_bfloat16, false>, a);
         else e = cudaLaunchKernelEx(&cfg, coupled_step_async<float, false>, a);
+    } else if (l.variant == kVariantPairs) {
+        e = cudaLaunchKernelEx(&cfg, coupled_step_pairs, a);  // FP32 storage only
     } else if (l.precision == kFP16) {
         e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__half, false>, a);
     } else if (l.precision == kBF16) {
@@ -514,6 +516,8 @@ cudaError_t step_kernel_occupancy(const StepLaunch& l, int* blocks_per_sm)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_async<float, false>, l.block,
                                                              smem);
     }
+    if (l.variant == kVariantPairs)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_pairs, l.block, 0);
     if (l.precision == kFP16)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, coupled_step_regs<__half, false>, l.block, 0);
     if (l.precision == kBF16)

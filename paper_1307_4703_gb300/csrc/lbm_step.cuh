@@ -190,6 +190,170 @@ __global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
     block_partials(a, diag);
 }
 
+// ---------------------------------------------------------------------------
+// Variant 5: registers and warp shuffles, two nodes per lane (FP32 storage,
+// halfway bounce-back)
+// ---------------------------------------------------------------------------
+// The register variant on 64-node warp tiles: a lane holds two nodes, so a
+// tile's populations take 28 registers instead of 56 and more warps fit on
+// an SM, and a lattice has twice as many (half-size) tiles to spread over
+// them.  Meant for small chips, whose steps give each warp about one
+// 128-node tile: the warps that draw a second one set the step's length.
+// The per-node arithmetic is collide_node, as in every other variant, so the
+// results are the same bits.
+
+// Free flight (pull) of one lane's two nodes x0, x0 + 1 (64-bit loads; the
+// +-1 column shifts move between lanes by shuffle, lanes 0 and 31 load the
+// value that comes from the neighbouring segment).  act / ld_w / ld_e as
+// in pull_quad.
+__device__ __forceinline__ void pull_pair(float2 (&v)[kPlanes], const float* __restrict__ S, long long P,
+                                          long long oC, long long oS, long long oN, int halo_w, int halo_e,
+                                          bool act, bool ld_w, bool ld_e, int lane)
+{
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const int sr = src_row(p), sc = src_col(p);
+        const long long o = p * P + (sr == 0 ? oC : sr == 1 ? oS : oN);
+        const bool ld = sc == 0 ? act : sc == 1 ? ld_w : ld_e;
+        float2 r = ld ? ldg2(S + o) : make_float2(0.f, 0.f);
+        if (sc == 1) {  // from column x - 1
+            float h = 0.f;
+            if (act && lane == 0) h = __ldg(S + o + halo_w);
+            float w = __shfl_up_sync(kFull, r.y, 1);
+            if (lane == 0) w = h;
+            r = make_float2(w, r.x);
+        } else if (sc == 2) {  // from column x + 1
+            float h = 0.f;
+            if (act && lane == 31) h = __ldg(S + o + halo_e);
+            float e = __shfl_down_sync(kFull, r.x, 1);
+            if (lane == 31) e = h;
+            r = make_float2(r.y, e);
+        }
+        v[p] = r;
+    }
+}
+
+// Halfway bounce-back of the two nodes (wall-link bytes in the low 16 bits
+// of lk2), as bounce_back.
+__device__ __forceinline__ void bounce_back_pair(float2 (&v)[kPlanes], unsigned lk2, const float* S, long long P,
+                                                 long long oC)
+{
+    unsigned wall = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const unsigned lb = (lk2 >> (8 * k)) & 0xFFu;
+        if (lb != kSolid) wall |= lb;
+    }
+    if (!wall) return;
+#pragma unroll
+    for (int i = 1; i <= 8; ++i) {
+        if (wall & (1u << (i - 1))) {
+            const float2 own = ldg2(S + opp(i) * P + oC);
+            const float2 ownc = i <= 4 ? ldg2(S + (9 + opp(i)) * P + oC) : own;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if ((lk2 >> (8 * k + i - 1)) & 1u) {
+                    at(v[i], k) = at(own, k);
+                    if (i <= 4) at(v[9 + i], k) = at(ownc, k);
+                }
+            }
+        }
+    }
+}
+
+// Open ports, moments and both collisions of the two nodes, the port and
+// solid-node handling inside the node loop as for FP32 quads.
+__device__ __forceinline__ void collide_pair(float2 (&v)[kPlanes], unsigned lk2, int x0, const RowBC& bw,
+                                             const RowBC& be, const StepArgs& a, const float* S, long long oC,
+                                             float2 omega, QuadAcc& acc)
+{
+    bool open_w = false, open_e = false;
+    if (bw.x >= 0) open_w = valve_open(a, bw.chan_kind);
+    if (be.x >= 0) open_e = valve_open(a, be.chan_kind);
+    const float dfac = a.decay != 0.f ? 1.f - a.decay / omega.y : 1.f;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const unsigned lb = (lk2 >> (8 * k)) & 0xFFu;
+        const bool fluid = lb != kSolid;
+        float f[9], g[5];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fluid ? at(v[i], k) : 0.f;  // solid: parked at rho = 1, C = 0
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = fluid ? at(v[9 + i], k) : 0.f;
+        bool outlet_k = false;
+        const int xk = x0 + k;
+        const bool pw = open_w && bw.x == xk;
+        const bool pe = !pw && open_e && be.x == xk;
+        if (pw || pe) outlet_k = port_node(f, g, pw, pw ? bw : be, a, S, oC + k);
+        const NodeMoments nm = collide_node<false>(f, g, omega, dfac, a);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) at(v[i], k) = f[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) at(v[9 + i], k) = g[i];
+        if (fluid) {
+            acc.bad |= !(nm.rho > 0.f && nm.rho < INFINITY) || !(fabsf(nm.C) < INFINITY);
+            ++acc.n;
+            acc.m += nm.rd;
+            acc.c += nm.C;
+            if (outlet_k) {
+                acc.q += nm.jx;  // rho u_x
+                acc.qc += nm.C * nm.ux;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128, 5) coupled_step_pairs(const StepArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const long long P = a.plane;
+    const float* __restrict__ S = a.src;
+    float* __restrict__ D = a.dst;
+
+    LaneDiag diag;
+    bool bad = false;
+
+    const int n = a.n_tiles64;
+    const int stride = gridDim.x * wpb;
+    int t = blockIdx.x * wpb + warp;
+    uint2 next = t < n ? tile_at(a.tiles64, n, t, a.reverse) : make_uint2(0u, 0u);
+    grid_dependency_sync();
+    for (; t < n; t += stride) {
+        const uint2 tile = next;  // the following entry is fetched one tile ahead
+        if (t + stride < n) next = tile_at(a.tiles64, n, t + stride, a.reverse);
+        const int y = int(tile.x >> kSegBits64);
+        const int x0 = int(tile.x & ((1u << kSegBits64) - 1)) * kPairTileNodes + 2 * lane;
+        const long long oC = (long long)y * a.pitch + x0;
+        const long long oS = (long long)(y > 0 ? y - 1 : y) * a.pitch + x0;  // rows outside: as coupled_step_regs
+        const long long oN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + x0;
+        const int halo_w = x0 > 0 ? -1 : 0;
+        const int halo_e = x0 + 2 < a.pitch ? 2 : 1;
+        const unsigned lk2 = __ldg(reinterpret_cast<const unsigned short*>(a.links + oC));
+        const bool act = lk2 != 0xFFFFu;  // some node of this lane is fluid
+        const unsigned ball = __ballot_sync(kFull, act);
+        const bool ld_w = ((ball | (ball >> 1)) >> lane) & 1u;  // feeds lane + 1
+        const bool ld_e = ((ball | (ball << 1)) >> lane) & 1u;  // feeds lane - 1
+        float2 v[kPlanes];
+        pull_pair(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
+        if (act) {
+            bounce_back_pair(v, lk2, S, P, oC);
+            const RowBC bw = a.rowbc[y];
+            const RowBC be = a.rowbc[a.ny + y];
+            QuadAcc q;
+            collide_pair(v, lk2, x0, bw, be, a, S, oC, row_rates(a, y), q);
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) stg2(D + p * P + oC, v[p]);
+            bad |= q.bad;
+            diag.add(q);
+        }
+    }
+
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
+    block_partials(a, diag);
+}
+
 // One warp tile of the register variant as a function (the multi-step
 // kernel's body; coupled_step_regs keeps the same code written out, which
 // the register allocator handles without spills): pull, walls, ports,

@@ -89,6 +89,10 @@ def _create(lib, nx, ny, mask, tau=0.8, tau_c=0.6, ports=(), edge_u=None, edge_C
     (dict(nx=524161, mask="wide"), "too large"),
     (dict(opt="multifp16"), "multi_step needs FP32"),
     (dict(opt="badmulti"), "multi_step = 70000"),
+    (dict(opt="badvariant"), "variant = 6"),
+    (dict(opt="pairs16"), "variant 5 needs FP32"),
+    (dict(opt="pairswall"), "variant 5 needs FP32"),
+    (dict(opt="pairsblock"), "variant 5 runs blocks"),
 ])
 def test_create_rejects_invalid_arguments(lib, case, needle):
     nx, ny = case.get("nx", 8), 6
@@ -123,6 +127,14 @@ def test_create_rejects_invalid_arguments(lib, case, needle):
             opt.precision, opt.multi_step = lbm.LBM_FP16, 8
         elif case["opt"] == "badmulti":
             opt.multi_step = 70000
+        elif case["opt"] == "badvariant":
+            opt.variant = 6
+        elif case["opt"] == "pairs16":
+            opt.precision, opt.variant = lbm.LBM_BF16, 5
+        elif case["opt"] == "pairswall":
+            opt.wall_scheme, opt.variant = lbm.LBM_WALL_EQUILIBRIUM, 5
+        elif case["opt"] == "pairsblock":
+            opt.variant, opt.block_threads = 5, 256
         else:
             opt.block_threads = 100
     st, msg = _create(lib, nx, ny, mask, tau=case.get("tau", 0.8), tau_c=case.get("tau_c", 0.6),

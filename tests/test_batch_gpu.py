@@ -46,7 +46,7 @@ def _mixed_chips():
     return chips, inits
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(variant=1), dict(variant=3), dict(precision="fp16"),
+@pytest.mark.parametrize("opts", [dict(), dict(variant=1), dict(variant=3), dict(variant=5), dict(precision="fp16"),
                                   dict(precision="bf16", variant=1)])
 def test_batch_equals_chips_run_alone(opts):
     chips, inits = _mixed_chips()

@@ -69,7 +69,7 @@ def test_autotune_keeps_the_state_and_the_results(prec):
     d0 = b.diagnostics()
     f0, g0 = b.populations()
     info = b.autotune(trial_steps=5)
-    assert info["variant"] in (1, 2, 3, 4) and info["grid"] >= 1
+    assert info["variant"] in (1, 2, 3, 4, 5) and info["grid"] >= 1
     assert b.step_count() == 100
     f1, g1 = b.populations()
     assert np.array_equal(f0, f1) and np.array_equal(g0, g1)

@@ -51,7 +51,7 @@ def _field_errors(prob, chip, ref):
     return du, dC, dm
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("nx,ny,seed", [(8, 8, 1), (17, 9, 2), (64, 32, 3), (130, 12, 4),
                                         (300, 20, 5), (129, 16, 6), (300, 20, 7), (260, 8, 5)])
 def test_population_parity_random_lattices(nx, ny, seed, variant):
@@ -91,7 +91,8 @@ def test_population_parity_random_lattices(nx, ny, seed, variant):
                                   dict(variant=3), dict(variant=3, pipeline_stages=3, consumer_warps=8),
                                   dict(variant=3, pipeline_stages=1, consumer_warps=1, max_blocks=5),
                                   dict(variant=4), dict(variant=4, block_threads=256),
-                                  dict(variant=4, block_threads=64, max_blocks=3)])
+                                  dict(variant=4, block_threads=64, max_blocks=3),
+                                  dict(variant=5), dict(variant=5, block_threads=64, max_blocks=3)])
 def test_kernel_variants_are_bit_identical(opts):
     """Both step kernels and any pipeline shape run the same arithmetic on
     the same values: identical bits after 300 steps with valve toggles and
@@ -331,7 +332,7 @@ def test_async_diagnostics_match_the_synchronous_read():
 
 
 @pytest.mark.parametrize("opts", [dict(), dict(variant=2, pipeline_stages=2, consumer_warps=3),
-                                  dict(variant=4, block_threads=64), dict(precision="fp16"),
+                                  dict(variant=4, block_threads=64), dict(variant=5), dict(precision="fp16"),
                                   dict(precision="bf16", variant=1), dict(wall_scheme=1)])
 def test_in_kernel_diagnostics_equal_the_reduction_launch(opts):
     """lbm_step_diagnostics: the step kernel's last block writes the totals
