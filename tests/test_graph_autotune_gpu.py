@@ -25,13 +25,14 @@ def _same(a, b):
     return np.array_equal(fa, fb) and np.array_equal(ga, gb)
 
 
-@pytest.mark.parametrize("graph_steps", [2, 10, 64])
-def test_graph_replay_is_bit_identical(graph_steps):
+@pytest.mark.parametrize("graph_steps,variant", [(2, 0), (10, 0), (64, 0), (10, 5)])
+def test_graph_replay_is_bit_identical(graph_steps, variant):
     """Valve switches every 25 steps split the runs: graphs where the valve
-    word holds for graph_steps steps, single launches elsewhere."""
+    word holds for graph_steps steps, single launches elsewhere (with the
+    default kernel and with variant 5)."""
     prob, init = W.random_case(12, 300, 20)
     a = lbm.Chip.from_problem(prob)
-    b = lbm.Chip.from_problem(prob, graph_steps=graph_steps)
+    b = lbm.Chip.from_problem(prob, graph_steps=graph_steps, variant=variant)
     for c in (a, b):
         c.init_equilibrium(**init)
         c.set_valve_schedule(25, prob["states"])
