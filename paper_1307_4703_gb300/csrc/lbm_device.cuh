@@ -730,6 +730,14 @@ __device__ __forceinline__ bool port_node(float (&f)[9], float (&g)[5], bool wes
 // g_i - w_i C_ref).  omega = {1 / tau_f, 1 / tau_g}; dfac = 1 - k / omega_g
 // with decay rate k (1 without decay).  Returns the moments the diagnostics
 // need.
+//
+// Two evaluations of the same update, chosen by storage type so that every
+// kernel of one storage type gives the same bits.  FP32 storage (kernels
+// bound by memory latency at their 128-register limit) keeps the direct
+// form f_i + omega (f_eq_i - f_i), which holds the fewest constants.  The
+// 16-bit kernels are bound by instruction issue and take the factored form
+// (1 - omega) f_i + omega f_eq_i with the equilibrium built from shared
+// terms: about a third fewer FP32 instructions per node.
 struct NodeMoments {
     float rd, rho, jx, ux, C;
 };
@@ -738,53 +746,109 @@ template <bool kDev>
 __device__ __forceinline__ NodeMoments collide_node(float (&f)[9], float (&g)[5], float2 omega, float dfac,
                                                     const StepArgs& a)
 {
-    // ---- moments (Eq. moments) and BGK collision of f, in deviations
-    //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
-    const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const float rho = 1.f + rd;
-    const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const float inv = __fdividef(1.f, rho);  // fast reciprocal (2 ulp): rho stays near 1
-    const float ux = jx * inv, uy = jy * inv;
-    const float usq = 1.5f * (ux * ux + uy * uy);
-    const float wo = omega.x;
-    {
-        // f_eq_i - w_i = w_i [rho - 1 + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]
-        const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
-        const float q1 = rho * (4.5f * e1 * e1 - usq), q2 = rho * (4.5f * e2 * e2 - usq);
-        const float q5 = rho * (4.5f * e5 * e5 - usq), q6 = rho * (4.5f * e6 * e6 - usq);
-        const float t1 = 3.f * jx, t2 = 3.f * jy, t5 = t1 + t2, t6 = t2 - t1;
-        f[0] += wo * (kWr * (rd - rho * usq) - f[0]);
-        f[1] += wo * (kWa * (rd + t1 + q1) - f[1]);
-        f[3] += wo * (kWa * (rd - t1 + q1) - f[3]);
-        f[2] += wo * (kWa * (rd + t2 + q2) - f[2]);
-        f[4] += wo * (kWa * (rd - t2 + q2) - f[4]);
-        f[5] += wo * (kWd * (rd + t5 + q5) - f[5]);
-        f[7] += wo * (kWd * (rd - t5 + q5) - f[7]);
-        f[6] += wo * (kWd * (rd + t6 + q6) - f[6]);
-        f[8] += wo * (kWd * (rd - t6 + q6) - f[8]);
+    if constexpr (kDev) {
+        // ---- moments of the deviations f'_i = f_i - w_i:
+        //      rho = 1 + sum f'_i, j = sum e_i f'_i ----
+        const float s56 = f[5] + f[6], s78 = f[7] + f[8];
+        const float rd = ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + (s56 + s78);
+        const float rho = 1.f + rd;
+        const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const float jy = (f[2] - f[4]) + (s56 - s78);
+        const float inv = __fdividef(1.f, rho);  // fast reciprocal (2 ulp): rho stays near 1
+        const float ux = jx * inv, uy = jy * inv;
+        // ---- BGK collision of f.  With j = rho u the equilibrium deviation
+        //      is f_eq_i - w_i = w_i [B + 3 e_i.j + 9/2 (e_i.j)(e_i.u)],
+        //      B = rho - 1 - 3/2 rho u^2 = (rho - 1) - 3/2 j.u; directions
+        //      +-e share B + 9/2 (e.j)(e.u) and differ in the sign of 3 e.j.
+        //      The weights are 4/9, 1/9 and 1/36, so omega w_rest = 4 wa and
+        //      omega w_diag = wa / 4 with wa = omega w_axis, exactly (a power
+        //      of two commutes with rounding): the diagonal terms are formed
+        //      a quarter of the size and share wa ----
+        {
+            const float om = 1.f - omega.x, wa = omega.x * kWa;
+            const float p1 = jx * ux, p2 = jy * uy;
+            const float B = fmaf(-1.5f, p1 + p2, rd);
+            const float j5 = jx + jy, j6 = jy - jx;  // e.j along (1, 1) and (-1, 1)
+            const float y1 = fmaf(4.5f, p1, B), y2 = fmaf(4.5f, p2, B);
+            const float Bq = 0.25f * B;
+            const float y5 = fmaf(1.125f * j5, ux + uy, Bq), y6 = fmaf(1.125f * j6, uy - ux, Bq);
+            f[0] = fmaf(wa, 4.f * B, om * f[0]);
+            f[1] = fmaf(wa, fmaf(3.f, jx, y1), om * f[1]);
+            f[3] = fmaf(wa, fmaf(-3.f, jx, y1), om * f[3]);
+            f[2] = fmaf(wa, fmaf(3.f, jy, y2), om * f[2]);
+            f[4] = fmaf(wa, fmaf(-3.f, jy, y2), om * f[4]);
+            f[5] = fmaf(wa, fmaf(0.75f, j5, y5), om * f[5]);
+            f[7] = fmaf(wa, fmaf(-0.75f, j5, y5), om * f[7]);
+            f[6] = fmaf(wa, fmaf(0.75f, j6, y6), om * f[6]);
+            f[8] = fmaf(wa, fmaf(-0.75f, j6, y6), om * f[8]);
+        }
+        // ---- scalar: C = sum g + C_ref (the weights add up to one) ----
+        const float C = (((g[0] + g[1]) + (g[2] + g[3])) + g[4]) + kCRef;
+        {
+            // omega_g (g_eq_i - w_i C_ref) = w_i wC + omega_g w_i C e_i.u / c_s^2,
+            // wC = omega_g (C dfac - C_ref): the reaction term R = -k C of
+            // Eq. cde enters as w_i R = omega_g (w_i R / omega_g), the
+            // isotropic part scaled by dfac = 1 - k / omega_g
+            const float wg = omega.y, om = 1.f - wg;
+            const float wC = fmaf(C, wg * dfac, -(wg * kCRef));
+            const float w1C = a.wg1 * wC;
+            const float ck = ((wg * a.wg1) * a.inv_cs2g) * C;
+            const float cx = ck * ux, cy = ck * uy;
+            // rest direction as the remainder wC - 4 w_1 wC (float(w0) + 4 float(w1) != 1)
+            g[0] = fmaf(om, g[0], fmaf(-4.f, w1C, wC));
+            g[1] = fmaf(om, g[1], w1C + cx);
+            g[3] = fmaf(om, g[3], w1C - cx);
+            g[2] = fmaf(om, g[2], w1C + cy);
+            g[4] = fmaf(om, g[4], w1C - cy);
+        }
+        return NodeMoments{rd, rho, jx, ux, C};
+    } else {
+        // ---- moments (Eq. moments) and BGK collision of f, in deviations
+        //      from the rest state: f'_i = f_i - w_i, rho = 1 + sum f'_i ----
+        const float rd = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const float rho = 1.f + rd;
+        const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        const float inv = __fdividef(1.f, rho);  // fast reciprocal (2 ulp): rho stays near 1
+        const float ux = jx * inv, uy = jy * inv;
+        const float usq = 1.5f * (ux * ux + uy * uy);
+        const float wo = omega.x;
+        {
+            // f_eq_i - w_i = w_i [rho - 1 + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u^2)]
+            const float e1 = ux, e2 = uy, e5 = ux + uy, e6 = uy - ux;
+            const float q1 = rho * (4.5f * e1 * e1 - usq), q2 = rho * (4.5f * e2 * e2 - usq);
+            const float q5 = rho * (4.5f * e5 * e5 - usq), q6 = rho * (4.5f * e6 * e6 - usq);
+            const float t1 = 3.f * jx, t2 = 3.f * jy, t5 = t1 + t2, t6 = t2 - t1;
+            f[0] += wo * (kWr * (rd - rho * usq) - f[0]);
+            f[1] += wo * (kWa * (rd + t1 + q1) - f[1]);
+            f[3] += wo * (kWa * (rd - t1 + q1) - f[3]);
+            f[2] += wo * (kWa * (rd + t2 + q2) - f[2]);
+            f[4] += wo * (kWa * (rd - t2 + q2) - f[4]);
+            f[5] += wo * (kWd * (rd + t5 + q5) - f[5]);
+            f[7] += wo * (kWd * (rd - t5 + q5) - f[7]);
+            f[6] += wo * (kWd * (rd + t6 + q6) - f[6]);
+            f[8] += wo * (kWd * (rd - t6 + q6) - f[8]);
+        }
+        // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
+        const float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+        {
+            const float wg = omega.y;
+            // the reaction term R = -k C of Eq. cde enters as w_i R, which is
+            // omega (w_i R / omega): the equilibrium's isotropic part scaled by
+            // dfac = 1 - k / omega (exactly 1 without decay)
+            const float Cd = C * dfac;
+            const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
+            const float c1d = a.wg1 * Cd;
+            // rest equilibrium w0 C formed as the remainder, so that the five
+            // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)
+            g[0] += wg * ((Cd - 4.f * c1d) - g[0]);
+            g[1] += wg * ((c1d + cx) - g[1]);
+            g[3] += wg * ((c1d - cx) - g[3]);
+            g[2] += wg * ((c1d + cy) - g[2]);
+            g[4] += wg * ((c1d - cy) - g[4]);
+        }
+        return NodeMoments{rd, rho, jx, ux, C};
     }
-    // ---- scalar: C = sum g, relaxation towards g_eq(C, u of this node) ----
-    float C = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
-    if constexpr (kDev) C += kCRef;  // the weights add up to one
-    {
-        const float wg = omega.y;
-        // the reaction term R = -k C of Eq. cde enters as w_i R, which is
-        // omega (w_i R / omega): the equilibrium's isotropic part scaled by
-        // dfac = 1 - k / omega (exactly 1 without decay); for deviations
-        // the isotropic part is w_i (C dfac - C_ref)
-        const float Cd = kDev ? fmaf(C, dfac, -kCRef) : C * dfac;
-        const float c1 = a.wg1 * C, cx = c1 * a.inv_cs2g * ux, cy = c1 * a.inv_cs2g * uy;
-        const float c1d = a.wg1 * Cd;
-        // rest equilibrium w0 C formed as the remainder, so that the five
-        // equilibria add up to C exactly (float(w0) + 4 float(w1) != 1)
-        g[0] += wg * ((Cd - 4.f * c1d) - g[0]);
-        g[1] += wg * ((c1d + cx) - g[1]);
-        g[3] += wg * ((c1d - cx) - g[3]);
-        g[2] += wg * ((c1d + cy) - g[2]);
-        g[4] += wg * ((c1d - cy) - g[4]);
-    }
-    return NodeMoments{rd, rho, jx, ux, C};
 }
 
 // Open ports, moments and both collisions of the quad.  Where the rare work
