@@ -81,6 +81,7 @@ struct lbm_ctx {
 
     int n_tiles = 0;
     int n_tiles64 = 0;
+    int n_plain = 0;  // tiles without a port node, listed first in the tile table
     int sms = 0;
     int partials_cap = 0;  // blocks the partials buffer holds (any launch shape fits)
     int diag_grid = 0;     // blocks whose partials the last step wrote
@@ -650,6 +651,25 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         fluid += r.fluid;
     }
     if (fluid == 0) return fail(nullptr, LBM_ERR_ARG, "the mask has no fluid node");
+    // tiles whose row segment holds a port node, listed after the others
+    for (uint2& t : tiles) {
+        const int y = int(t.x >> lbm::kSegBits), x0 = int(t.x & ((1u << lbm::kSegBits) - 1)) * lbm::kTileNodes;
+        for (int side = 0; side < 2; ++side) {
+            const int px = rowbc[size_t(side) * ny + y].x;
+            if (px >= x0 && px < x0 + lbm::kTileNodes) t.y |= lbm::kPortTile;
+        }
+    }
+    const int n_plain = int(std::stable_partition(tiles.begin(), tiles.end(),
+                                                  [](const uint2& t) { return !(t.y & lbm::kPortTile); }) -
+                            tiles.begin());
+    for (uint2& t : tiles64) {
+        const int y = int(t.x >> lbm::kSegBits64);
+        const int x0 = int(t.x & ((1u << lbm::kSegBits64) - 1)) * lbm::kPairTileNodes;
+        for (int side = 0; side < 2; ++side) {
+            const int px = rowbc[size_t(side) * ny + y].x;
+            if (px >= x0 && px < x0 + lbm::kPairTileNodes) t.y |= lbm::kPortTile;
+        }
+    }
 
     // ---- device set-up ----
     lbm_ctx* h = new (std::nothrow) lbm_ctx();
@@ -673,6 +693,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->alloc_user = opt.alloc_user;
     h->n_tiles = int(tiles.size());
     h->n_tiles64 = int(tiles64.size());
+    h->n_plain = n_plain;
     h->solid.assign(mask, mask + size_t(nx) * ny);
     h->fluid = fluid;
     h->precision = opt.precision;
@@ -1005,6 +1026,7 @@ static lbm::StepArgs step_args(const lbm_ctx* h)
     a.rowbc = h->rowbc;
     a.tiles = h->tiles;
     a.n_tiles = h->n_tiles;
+    a.n_plain = h->n_plain;
     a.tiles64 = h->tiles64;
     a.n_tiles64 = h->n_tiles64;
     a.ny = h->ny;
@@ -1518,6 +1540,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     a.rowbc = h->rowbc;
     a.tiles = h->tiles;
     a.n_tiles = h->n_tiles;
+    a.n_plain = h->n_plain;
     a.tiles64 = h->tiles64;
     a.n_tiles64 = h->n_tiles64;
     a.ny = h->ny;
@@ -1919,6 +1942,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     a.rowbc = h->rowbc;
     a.tiles = h->tiles;
     a.n_tiles = h->n_tiles;
+    a.n_plain = h->n_plain;
     a.tiles64 = h->tiles64;
     a.n_tiles64 = h->n_tiles64;
     a.ny = h->ny;

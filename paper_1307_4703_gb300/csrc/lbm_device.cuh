@@ -859,8 +859,13 @@ __device__ __forceinline__ NodeMoments collide_node(float (&f)[9], float (&g)[5]
 // fastest with that work in passes over the quad that only quads holding a
 // port or a solid node enter (FP16 50.1 us, against 52.3 us inside the loop).
 // kPasses selects the passes (the multi-step kernel takes them for FP32 too:
-// there they keep its registers from spilling).
-template <typename T, bool kPasses = !kStoresF32<T>>
+// there they keep its registers from spilling).  Both forms give the same
+// bits.  kPorts = false leaves the port code out, for tiles whose row
+// segment holds no port node (kPortTile): present in the node loop, it costs
+// the step even where it never runs (a timing copy without it: FP16 44.1 us
+// against 48.0 us on the 4096 x 2048 chip).  The register kernels take the
+// port-free form for those tiles and the pass form for the few others.
+template <typename T, bool kPasses = !kStoresF32<T>, bool kPorts = true>
 __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, int x0, const RowBC& bw,
                                              const RowBC& be, const StepArgs& a, const T* S, long long oC,
                                              float2 omega, QuadAcc& acc)
@@ -868,8 +873,10 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     // a port entry exists on a few rows only (the entries are the same for
     // the whole warp, so the tests below branch uniformly)
     bool open_w = false, open_e = false;
-    if (bw.x >= 0) open_w = valve_open(a, bw.chan_kind);
-    if (be.x >= 0) open_e = valve_open(a, be.chan_kind);
+    if constexpr (kPorts) {
+        if (bw.x >= 0) open_w = valve_open(a, bw.chan_kind);
+        if (be.x >= 0) open_e = valve_open(a, be.chan_kind);
+    }
     const float dfac = a.decay != 0.f ? 1.f - a.decay / omega.y : 1.f;
     // With 16-bit storage the scalar populations stay in their stored form
     // g_i - w_i C_ref here (C_ref = kCRef), as the fluid ones stay f_i - w_i:
@@ -878,7 +885,7 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     constexpr bool kDev = !kStoresF32<T>;
 
     unsigned outlet = 0;  // passes: bit k = node x0 + k is an open outlet (flux diagnostics)
-    if constexpr (kPasses) {
+    if constexpr (kPasses && kPorts) {
         // ---- open valve ports (Zou-He; held concentration / do-nothing):
         //      only the first and last quads of a channel row hold a port
         //      node (ports are fluid, and never on both sides of a row) ----
@@ -922,10 +929,12 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
                 for (int i = 0; i < 5; ++i) g[i] = 0.f;
             }
             // ---- open valve ports ----
-            const int xk = x0 + k;
-            const bool pw = open_w && bw.x == xk;
-            const bool pe = !pw && open_e && be.x == xk;
-            if (pw || pe) outlet_k = port_node(f, g, pw, pw ? bw : be, a, S, oC + k);
+            if constexpr (kPorts) {
+                const int xk = x0 + k;
+                const bool pw = open_w && bw.x == xk;
+                const bool pe = !pw && open_e && be.x == xk;
+                if (pw || pe) outlet_k = port_node(f, g, pw, pw ? bw : be, a, S, oC + k);
+            }
         }
 
         const NodeMoments nm = collide_node<kDev>(f, g, omega, dfac, a);

@@ -38,6 +38,10 @@ constexpr int kMaskWords = 8;              // valve channels per lattice: 32 * k
 
 enum StepVariant { kVariantRegs = 1, kVariantBulk = 2, kVariantPipe = 3, kVariantAsync = 4, kVariantPairs = 5 };
 constexpr int kPairTileNodes = 64;  // nodes per warp tile of variant 5: 32 lanes x 2 nodes
+// Bit of a tile table entry's .y: the tile's row segment holds a port node
+// (of either side; whether its valve is open is decided per step).  Tiles
+// without one run a step without any port code.
+constexpr uint32_t kPortTile = 1u << 16;
 constexpr int kSegBits64 = 13;      // 64-node tile encoding: segment in the low 13 bits
 enum Precision { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 constexpr float kCRef = 0.5f;  // reference concentration of 16-bit scalar storage
@@ -65,8 +69,12 @@ struct StepArgs {
     float* dst;             // post-collision populations at time t + 1
     const uint8_t* links;
     const RowBC* rowbc;
-    const uint2* tiles;
+    const uint2* tiles;     // x = (y << 12) | segment, y = first | (last << 8) lane (quad) holding
+                            // fluid | kPortTile; the n_plain tiles without a port node come first
     int n_tiles;
+    int n_plain;            // 0: every tile is treated as a port tile
+    int port_blocks;        // variants 1, 4: the grid's last port_blocks blocks take the port tiles
+                            // (launch_step sets it from the grid)
     const uint2* tiles64;   // the same lattice in 64-node row segments (variant 5):
                             // x = (y << 13) | segment, y = first | (last << 8) lane (node pair) holding fluid
     int n_tiles64;
@@ -105,8 +113,12 @@ struct AdjointArgs {
     float* adj_mid;         // M(t), written
     const uint8_t* links;
     const RowBC* rowbc;
-    const uint2* tiles;
+    const uint2* tiles;     // x = (y << 12) | segment, y = first | (last << 8) lane (quad) holding
+                            // fluid | kPortTile; the n_plain tiles without a port node come first
     int n_tiles;
+    int n_plain;            // 0: every tile is treated as a port tile
+    int port_blocks;        // variants 1, 4: the grid's last port_blocks blocks take the port tiles
+                            // (launch_step sets it from the grid)
     int ny;
     int pitch;
     long long plane;
@@ -154,8 +166,12 @@ struct ScalarArgs {
     float* dst;             // scalar plane 0 of the destination buffer
     const uint8_t* links;
     const RowBC* rowbc;
-    const uint2* tiles;
+    const uint2* tiles;     // x = (y << 12) | segment, y = first | (last << 8) lane (quad) holding
+                            // fluid | kPortTile; the n_plain tiles without a port node come first
     int n_tiles;
+    int n_plain;            // 0: every tile is treated as a port tile
+    int port_blocks;        // variants 1, 4: the grid's last port_blocks blocks take the port tiles
+                            // (launch_step sets it from the grid)
     int reverse;            // 1: take the tiles from the end of the table (see tile_at)
     int ny;
     int pitch;

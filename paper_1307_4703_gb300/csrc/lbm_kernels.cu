@@ -401,6 +401,27 @@ cudaError_t prepare_step_kernels()
     return e;
 }
 
+// Blocks of a grid that take the port tiles in the register variants, for
+// 16-bit storage: the port tiles' share of the grid with each port tile
+// weighted as kPortTileCost plain ones, rounded up, and at least one block
+// for the tiles without ports.  0 (every block runs every tile through the
+// port loop) when there are no port tiles, for grids of one block, and for
+// FP32 storage, whose step is bound by memory and measured slower split.
+// The weight is measured on the 4096 x 2048 chip, FP16 storage (one port
+// tile in 27): 1 -> 52.1 us, 2 -> 40.3 us, 3 -> 41.0 us, 5 -> 42.6 us per
+// step; FP32 split: 69.8, 66.7, 67.0, 69.5 us against 62.3 us unsplit.  With
+// the weight 1 the few port warps set the step's length.
+constexpr int kPortTileCost = 2;
+
+static int port_blocks(int grid, int n_tiles, int n_plain, int precision)
+{
+    const long long n_port = n_tiles - n_plain;
+    if (precision == kFP32 || n_port <= 0 || n_plain <= 0 || grid < 2) return 0;
+    const long long w = n_port * kPortTileCost;
+    const long long gp = (grid * w + n_plain + w - 1) / (n_plain + w);
+    return int(std::min<long long>(std::max<long long>(gp, 1), grid - 1));
+}
+
 cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -412,7 +433,9 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = l.pdl ? 1 : 0;
-    if (a.wallv) return launch_step_walls(a, l, s);
+    StepArgs b = a;  // the register variants' port blocks for this grid
+    b.port_blocks = port_blocks(l.grid, a.n_tiles, a.n_plain, l.precision);
+    if (a.wallv) return launch_step_walls(b, l, s);
     cudaError_t e;
     if (l.variant == kVariantBulk) {
         const int per = l.stages / (l.block / 32 - 1);
@@ -426,17 +449,17 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
         e = cudaLaunchKernelEx(&cfg, coupled_step_pipe, a, per);
     } else if (l.variant == kVariantAsync) {
         cfg.dynamicSmemBytes = async_smem_bytes(l.block, l.precision);
-        if (l.precision == kFP16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__half, false>, a);
-        else if (l.precision == kBF16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__nv_bfloat16, false>, a);
-        else e = cudaLaunchKernelEx(&cfg, coupled_step_async<float, false>, a);
+        if (l.precision == kFP16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__half, false>, b);
+        else if (l.precision == kBF16) e = cudaLaunchKernelEx(&cfg, coupled_step_async<__nv_bfloat16, false>, b);
+        else e = cudaLaunchKernelEx(&cfg, coupled_step_async<float, false>, b);
     } else if (l.variant == kVariantPairs) {
         e = cudaLaunchKernelEx(&cfg, coupled_step_pairs, a);  // FP32 storage only
     } else if (l.precision == kFP16) {
-        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__half, false>, a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__half, false>, b);
     } else if (l.precision == kBF16) {
-        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__nv_bfloat16, false>, a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<__nv_bfloat16, false>, b);
     } else {
-        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<float, false>, a);
+        e = cudaLaunchKernelEx(&cfg, coupled_step_regs<float, false>, b);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -12,28 +12,64 @@ namespace lbm {
 namespace {
 
 // ---------------------------------------------------------------------------
+// Tiles with and without ports (the register kernels, variants 1 and 4)
+// ---------------------------------------------------------------------------
+// The tile table lists the tiles whose row segment holds no port node first
+// (a.n_plain of them) and the port tiles (kPortTile) after them.  The port
+// code, present in a tile loop, costs that loop time even where it never
+// runs (the 16-bit step on the 4096 x 2048 chip: 48.0 us with it in the
+// loop, 44.0 us when only a separate loop has it), so the register kernels
+// have two loops: the grid's last a.port_blocks blocks take the port tiles
+// with the port code, the other blocks the rest without any (16-bit
+// storage; see port_blocks for the share).  Both collide each node the same
+// way (collide_quad's forms give the same bits).
+//
+// A tile range of one warp: entries t, t + stride, ... below n of tiles.
+struct TileRange {
+    const uint2* tiles;
+    int n, t, stride;
+};
+
+// The warp's range and which loop it runs.  port_blocks = 0 with port tiles
+// present (a grid too small to split) sends every block through the port
+// loop; n_plain = 0 (nothing known about the tiles) does the same.
+__device__ __forceinline__ TileRange warp_tiles(const StepArgs& a, int warp, int wpb, bool& port_loop)
+{
+    const int gp = a.port_blocks;
+    const int n_port = a.n_tiles - a.n_plain;
+    const int first_port_block = int(gridDim.x) - gp;
+    if (n_port > 0 && (gp == 0 || int(blockIdx.x) >= first_port_block)) {
+        port_loop = true;
+        if (gp == 0) return TileRange{a.tiles, a.n_tiles, int(blockIdx.x) * wpb + warp, int(gridDim.x) * wpb};
+        return TileRange{a.tiles + a.n_plain, n_port, (int(blockIdx.x) - first_port_block) * wpb + warp, gp * wpb};
+    }
+    port_loop = false;
+    return TileRange{a.tiles, a.n_plain, int(blockIdx.x) * wpb + warp, first_port_block * wpb};
+}
+
+// ---------------------------------------------------------------------------
 // Variant 1: registers and warp shuffles
 // ---------------------------------------------------------------------------
-template <typename T, bool kWalls>
-__global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
+// kWhole: every tile of the table with the grid's stride, read from the
+// kernel parameters (the FP32 kernel sits at its register limit, where the
+// range held in registers makes it spill).
+template <typename T, bool kWalls, bool kPortCode, bool kWhole = false>
+__device__ __forceinline__ void regs_loop(const StepArgs& a, TileRange r, int lane, LaneDiag& diag, bool& bad)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
+    if constexpr (kWhole) {
+        r.tiles = a.tiles;
+        r.n = a.n_tiles;
+        r.stride = int(gridDim.x) * int(blockDim.x >> 5);
+    }
     const long long P = a.plane;
     const T* __restrict__ S = reinterpret_cast<const T*>(a.src);
     T* __restrict__ D = reinterpret_cast<T*>(a.dst);
-
-    LaneDiag diag;
-    bool bad = false;
-
-    const int stride = gridDim.x * wpb;
-    int t = blockIdx.x * wpb + warp;
-    uint2 next = t < a.n_tiles ? tile_at(a.tiles, a.n_tiles, t, a.reverse) : make_uint2(0u, 0u);
+    int t = r.t;
+    uint2 next = t < r.n ? tile_at(r.tiles, r.n, t, a.reverse) : make_uint2(0u, 0u);
     grid_dependency_sync();
-    for (; t < a.n_tiles; t += stride) {
+    for (; t < r.n; t += r.stride) {
         const uint2 tile = next;  // the following entry is fetched one tile ahead
-        if (t + stride < a.n_tiles) next = tile_at(a.tiles, a.n_tiles, t + stride, a.reverse);
+        if (t + r.stride < r.n) next = tile_at(r.tiles, r.n, t + r.stride, a.reverse);
         const int y = int(tile.x >> kSegBits);
         const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
@@ -59,10 +95,14 @@ __global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
         pull_quad<false>(v, S, P, oC, oS, oN, halo_w, halo_e, act, ld_w, ld_e, lane);
         if (act) {
             bounce_back<T, kWalls>(v, lk, S, P, oC, static_cast<const T*>(a.wallv));
-            const RowBC bw = a.rowbc[y];
-            const RowBC be = a.rowbc[a.ny + y];
             QuadAcc q;
-            collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
+            if constexpr (kPortCode) {
+                const RowBC bw = a.rowbc[y];
+                const RowBC be = a.rowbc[a.ny + y];
+                collide_quad<T, !kStoresF32<T>, true>(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
+            } else {
+                collide_quad<T, !kStoresF32<T>, false>(v, lk, x0, RowBC{}, RowBC{}, a, S, oC, row_rates(a, y), q);
+            }
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p)
                 Codec<T>::st4(D + p * P + oC, v[p], 0.f);
@@ -70,7 +110,24 @@ __global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
             diag.add(q);
         }
     }
+}
 
+template <typename T, bool kWalls>
+__global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    LaneDiag diag;
+    bool bad = false;
+    if constexpr (kStoresF32<T>) {  // one loop over every tile (port_blocks is 0 for FP32)
+        regs_loop<T, kWalls, true, true>(a, TileRange{nullptr, 0, int(blockIdx.x) * wpb + warp, 0}, lane, diag, bad);
+    } else {
+        bool port_loop;
+        const TileRange r = warp_tiles(a, warp, wpb, port_loop);
+        if (port_loop) regs_loop<T, kWalls, true>(a, r, lane, diag, bad);
+        else regs_loop<T, kWalls, false>(a, r, lane, diag, bad);
+    }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
     block_partials(a, diag);
 }
@@ -126,29 +183,20 @@ __device__ __forceinline__ void issue_tile_async(const StepArgs& a, const T* S, 
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-template <typename T, bool kWalls>
-__global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
+template <typename T, bool kWalls, bool kPortCode>
+__device__ __forceinline__ void async_loop(const StepArgs& a, TileRange r, AsyncStage<T>& st, int lane,
+                                           LaneDiag& diag, bool& bad)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
     const long long P = a.plane;
     const T* __restrict__ S = reinterpret_cast<const T*>(a.src);
     T* __restrict__ D = reinterpret_cast<T*>(a.dst);
-    AsyncStage<T>& st = reinterpret_cast<AsyncStage<T>*>(smem)[warp];
-
-    LaneDiag diag;
-    bool bad = false;
-
-    const int stride = gridDim.x * wpb;
-    int t = blockIdx.x * wpb + warp;
+    int t = r.t;
     grid_dependency_sync();
-    uint2 tile = t < a.n_tiles ? tile_at(a.tiles, a.n_tiles, t, a.reverse) : make_uint2(0u, 0u);
-    if (t < a.n_tiles) issue_tile_async(a, S, P, tile, st, lane);
-    for (; t < a.n_tiles; t += stride) {
-        const bool more = t + stride < a.n_tiles;
-        const uint2 next = more ? tile_at(a.tiles, a.n_tiles, t + stride, a.reverse) : make_uint2(0u, 0u);
+    uint2 tile = t < r.n ? tile_at(r.tiles, r.n, t, a.reverse) : make_uint2(0u, 0u);
+    if (t < r.n) issue_tile_async(a, S, P, tile, st, lane);
+    for (; t < r.n; t += r.stride) {
+        const bool more = t + r.stride < r.n;
+        const uint2 next = more ? tile_at(r.tiles, r.n, t + r.stride, a.reverse) : make_uint2(0u, 0u);
         const int y = int(tile.x >> kSegBits);
         const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
@@ -172,10 +220,14 @@ __global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
         if (more) issue_tile_async(a, S, P, next, st, lane);  // the stage is free again
         if (act) {
             bounce_back<T, kWalls>(v, lk, S, P, oC, static_cast<const T*>(a.wallv));
-            const RowBC bw = a.rowbc[y];
-            const RowBC be = a.rowbc[a.ny + y];
             QuadAcc q;
-            collide_quad(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
+            if constexpr (kPortCode) {
+                const RowBC bw = a.rowbc[y];
+                const RowBC be = a.rowbc[a.ny + y];
+                collide_quad<T, !kStoresF32<T>, true>(v, lk, x0, bw, be, a, S, oC, row_rates(a, y), q);
+            } else {
+                collide_quad<T, !kStoresF32<T>, false>(v, lk, x0, RowBC{}, RowBC{}, a, S, oC, row_rates(a, y), q);
+            }
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p)
                 Codec<T>::st4(D + p * P + oC, v[p], 0.f);
@@ -185,7 +237,28 @@ __global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
         tile = next;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");  // nothing in flight at exit
+}
 
+template <typename T, bool kWalls>
+__global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    AsyncStage<T>& st = reinterpret_cast<AsyncStage<T>*>(smem)[warp];
+    LaneDiag diag;
+    bool bad = false;
+    if constexpr (kStoresF32<T>) {  // one loop over every tile (port_blocks is 0 for FP32)
+        async_loop<T, kWalls, true>(a, TileRange{a.tiles, a.n_tiles, int(blockIdx.x) * wpb + warp,
+                                                 int(gridDim.x) * wpb},
+                                    st, lane, diag, bad);
+    } else {
+        bool port_loop;
+        const TileRange r = warp_tiles(a, warp, wpb, port_loop);
+        if (port_loop) async_loop<T, kWalls, true>(a, r, st, lane, diag, bad);
+        else async_loop<T, kWalls, false>(a, r, st, lane, diag, bad);
+    }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
     block_partials(a, diag);
 }

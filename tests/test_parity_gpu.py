@@ -92,11 +92,16 @@ def test_population_parity_random_lattices(nx, ny, seed, variant):
                                   dict(variant=3, pipeline_stages=1, consumer_warps=1, max_blocks=5),
                                   dict(variant=4), dict(variant=4, block_threads=256),
                                   dict(variant=4, block_threads=64, max_blocks=3),
-                                  dict(variant=5), dict(variant=5, block_threads=64, max_blocks=3)])
+                                  dict(variant=5), dict(variant=5, block_threads=64, max_blocks=3),
+                                  dict(variant=1, max_blocks=1), dict(variant=1, max_blocks=2),
+                                  dict(variant=1, block_threads=64, max_blocks=9),
+                                  dict(variant=4, max_blocks=1), dict(variant=4, block_threads=64, max_blocks=2)])
 def test_kernel_variants_are_bit_identical(opts):
     """Both step kernels and any pipeline shape run the same arithmetic on
     the same values: identical bits after 300 steps with valve toggles and
-    a random obstacle field."""
+    a random obstacle field.  The register variants run tiles that hold a
+    port node in their own blocks: one block (every tile through the port
+    loop), two (one block each) and small grids check that split."""
     prob, init = W.random_case(31, 700, 64, solid_frac=0.1)
     prob["states"] = [1, 2, 4, 3, 7, 0]
     ref = lbm.Chip.from_problem(prob)

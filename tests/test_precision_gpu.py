@@ -237,7 +237,9 @@ def test_large_chip_at_benchmark_launch_shape():
                                   dict(variant=2, consumer_warps=1, pipeline_stages=1),
                                   dict(variant=2, consumer_warps=7, pipeline_stages=3),
                                   dict(variant=2, consumer_warps=3, pipeline_stages=2, max_blocks=5),
-                                  dict(variant=4), dict(variant=4, block_threads=64, max_blocks=5)])
+                                  dict(variant=4), dict(variant=4, block_threads=64, max_blocks=5),
+                                  dict(variant=4, max_blocks=1), dict(variant=4, max_blocks=2),
+                                  dict(variant=1, max_blocks=1)])
 def test_16bit_variants_are_bit_identical(prec, opts):
     """Every 16-bit kernel variant and launch shape rounds the same FP32
     values: identical stored bits after 300 steps (a 700-wide lattice whose
