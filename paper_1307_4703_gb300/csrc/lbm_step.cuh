@@ -148,6 +148,7 @@ template <typename T>
 struct AsyncStage {
     static constexpr int kRow = kTileNodes + 8;  // [4 halo | 128 | 4 halo]
     T pl[kPlanes][kRow];
+    unsigned links[32];  // the lanes' wall-link words (lanes q0 .. q1)
 };
 
 template <typename T>
@@ -171,6 +172,10 @@ __device__ __forceinline__ void issue_tile_async(const StepArgs& a, const T* S, 
     const long long rN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + xs;
     const bool own = lane >= q0 && lane <= q1;
     const bool wide = lane >= q0 - 1 && lane <= q1 + 1;
+    if (own)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(&st.links[lane])),
+                     "l"(a.links + rC + 4 * lane)
+                     : "memory");
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         const int sr = src_row(p), sc = src_col(p);
@@ -200,11 +205,14 @@ __device__ __forceinline__ void async_loop(const StepArgs& a, TileRange r, Async
         const int y = int(tile.x >> kSegBits);
         const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
-        const unsigned lk = __ldg(reinterpret_cast<const unsigned*>(a.links + oC));
-        const bool act = lk != 0xFFFFFFFFu;
-        // ---- free flight (pull) from the stage: the current tile's copies ----
+        // ---- free flight (pull) from the stage: the current tile's copies,
+        //      the wall-link words with them (lanes outside the tile's fluid
+        //      range q0 .. q1 hold no fluid) ----
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncwarp();
+        const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
+        const unsigned lk = lane >= q0 && lane <= q1 ? st.links[lane] : 0xFFFFFFFFu;
+        const bool act = lk != 0xFFFFFFFFu;
         float4 v[kPlanes];
         if (act) {
 #pragma unroll
