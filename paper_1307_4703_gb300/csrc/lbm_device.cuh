@@ -678,6 +678,35 @@ __device__ __forceinline__ LoadRange load_range(uint2 tile, int lane)
     return LoadRange{lane >= q0 && lane <= q1, lane >= q0 - 1 && lane <= q1, lane >= q0 && lane <= q1 + 1};
 }
 
+// A warp's share of a tile table: entries t, t + stride, ... below n of
+// tiles.
+struct TileRange {
+    const uint2* tiles;
+    int n, t, stride;
+};
+
+// Tile tables list the tiles whose row segment holds no port node first
+// (n_plain of them) and the port tiles (kPortTile) after them.  The grid's
+// last port_blocks blocks take the port tiles and run them with the port
+// code (port_loop), the other blocks the rest with a loop without any.
+// port_blocks = 0 with port tiles present sends every block through the
+// port loop over every tile; n_plain = 0 (nothing known about the tiles)
+// does the same.
+__device__ __forceinline__ TileRange split_tiles(const uint2* tiles, int n_tiles, int n_plain, int port_blocks,
+                                                 int warp, int wpb, bool& port_loop)
+{
+    const int gp = port_blocks;
+    const int n_port = n_tiles - n_plain;
+    const int first_port_block = int(gridDim.x) - gp;
+    if (n_port > 0 && (gp == 0 || int(blockIdx.x) >= first_port_block)) {
+        port_loop = true;
+        if (gp == 0) return TileRange{tiles, n_tiles, int(blockIdx.x) * wpb + warp, int(gridDim.x) * wpb};
+        return TileRange{tiles + n_plain, n_port, (int(blockIdx.x) - first_port_block) * wpb + warp, gp * wpb};
+    }
+    port_loop = false;
+    return TileRange{tiles, n_plain, int(blockIdx.x) * wpb + warp, first_port_block * wpb};
+}
+
 // Open ports, moments and both collisions for the four nodes x0..x0+3 of a
 // row whose port entries are bw (west) and be (east); v holds the streamed
 // populations on entry and the post-collision populations on exit (fluid

@@ -113,12 +113,8 @@ struct AdjointArgs {
     float* adj_mid;         // M(t), written
     const uint8_t* links;
     const RowBC* rowbc;
-    const uint2* tiles;     // x = (y << 12) | segment, y = first | (last << 8) lane (quad) holding
-                            // fluid | kPortTile; the n_plain tiles without a port node come first
+    const uint2* tiles;
     int n_tiles;
-    int n_plain;            // 0: every tile is treated as a port tile
-    int port_blocks;        // variants 1, 4: the grid's last port_blocks blocks take the port tiles
-                            // (launch_step sets it from the grid)
     int ny;
     int pitch;
     long long plane;
@@ -166,12 +162,8 @@ struct ScalarArgs {
     float* dst;             // scalar plane 0 of the destination buffer
     const uint8_t* links;
     const RowBC* rowbc;
-    const uint2* tiles;     // x = (y << 12) | segment, y = first | (last << 8) lane (quad) holding
-                            // fluid | kPortTile; the n_plain tiles without a port node come first
+    const uint2* tiles;
     int n_tiles;
-    int n_plain;            // 0: every tile is treated as a port tile
-    int port_blocks;        // variants 1, 4: the grid's last port_blocks blocks take the port tiles
-                            // (launch_step sets it from the grid)
     int reverse;            // 1: take the tiles from the end of the table (see tile_at)
     int ny;
     int pitch;

@@ -21,30 +21,11 @@ namespace {
 // loop, 44.0 us when only a separate loop has it), so the register kernels
 // have two loops: the grid's last a.port_blocks blocks take the port tiles
 // with the port code, the other blocks the rest without any (16-bit
-// storage; see port_blocks for the share).  Both collide each node the same
-// way (collide_quad's forms give the same bits).
-//
-// A tile range of one warp: entries t, t + stride, ... below n of tiles.
-struct TileRange {
-    const uint2* tiles;
-    int n, t, stride;
-};
-
-// The warp's range and which loop it runs.  port_blocks = 0 with port tiles
-// present (a grid too small to split) sends every block through the port
-// loop; n_plain = 0 (nothing known about the tiles) does the same.
+// storage; see port_blocks for the share; split_tiles).  Both collide each
+// node the same way (collide_quad's forms give the same bits).
 __device__ __forceinline__ TileRange warp_tiles(const StepArgs& a, int warp, int wpb, bool& port_loop)
 {
-    const int gp = a.port_blocks;
-    const int n_port = a.n_tiles - a.n_plain;
-    const int first_port_block = int(gridDim.x) - gp;
-    if (n_port > 0 && (gp == 0 || int(blockIdx.x) >= first_port_block)) {
-        port_loop = true;
-        if (gp == 0) return TileRange{a.tiles, a.n_tiles, int(blockIdx.x) * wpb + warp, int(gridDim.x) * wpb};
-        return TileRange{a.tiles + a.n_plain, n_port, (int(blockIdx.x) - first_port_block) * wpb + warp, gp * wpb};
-    }
-    port_loop = false;
-    return TileRange{a.tiles, a.n_plain, int(blockIdx.x) * wpb + warp, first_port_block * wpb};
+    return split_tiles(a.tiles, a.n_tiles, a.n_plain, a.port_blocks, warp, wpb, port_loop);
 }
 
 // ---------------------------------------------------------------------------
