@@ -386,7 +386,8 @@ lbm_status lbm_debug_barrier_extra(lbm_handle h, int32_t extra);
 typedef struct {
     int32_t nx, ny;
     int32_t pitch;          /* elements per stored row (multiple of 128) */
-    int32_t n_tiles;        /* 128-node row segments that hold fluid */
+    int32_t n_tiles;        /* 128-node warp tiles: each starts at its row's first fluid node (on a
+                               16-node boundary) not covered by the tile before it */
     int32_t grid, block;    /* step kernel launch shape */
     int32_t variant;        /* 1 registers, 2 bulk-copy pipeline with producer warp, 3 self-refilling warps,
                                4 registers with asynchronous prefetch, 5 registers on 64-node tiles */
@@ -491,8 +492,9 @@ lbm_status lbm_set_instance_schedule(lbm_handle h, int32_t k, int64_t period, in
  *             fluid node (solid, outside the grid, or beyond a port); 0xFF
  *             marks a solid node and every padding column x >= nx.
  *   ports     2 * ny lbm_row_port entries, west side then east side.
- *   tiles     n_tiles lbm_tile entries: every 128-node row segment that
- *             holds fluid, exactly once.
+ *   tiles     n_tiles lbm_tile entries covering every fluid node exactly
+ *             once (disjoint 128-node row windows, e.g. the row segments
+ *             that hold fluid).
  * Malformed tables or buffers that are too small are not detected and lead
  * to out-of-bounds device accesses. */
 #define LBM_NOALLOC_MAX_BLOCKS 2048
@@ -507,7 +509,9 @@ typedef struct {
 } lbm_row_port;
 
 typedef struct {
-    uint32_t row_segment;  /* (y << 12) | s: nodes [128 s, 128 s + 128) of row y */
+    uint32_t row_segment;  /* (y << 15) | (x0 / 16): nodes [x0, x0 + 128) of row y, x0 a multiple of 16
+                              with x0 + 128 <= pitch (lbm_create's tiles start at each row's first
+                              fluid node not yet covered; a segment start x0 = 128 s is one choice) */
     uint32_t quads;        /* q0 | (q1 << 8): first and last 4-node group holding fluid */
 } lbm_tile;
 

@@ -237,8 +237,8 @@ struct QuadPos {
 __device__ __forceinline__ QuadPos quad_pos(const AdjointArgs& A, uint2 tile, int lane)
 {
     QuadPos q;
-    q.y = int(tile.x >> kSegBits);
-    q.x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+    q.y = int(tile.x >> kColBits);
+    q.x0 = tile_x0(tile) + 4 * lane;
     q.oC = (long long)q.y * A.pitch + q.x0;
     q.oS = (long long)(q.y > 0 ? q.y - 1 : q.y) * A.pitch + q.x0;
     q.oN = (long long)(q.y + 1 < A.ny ? q.y + 1 : q.y) * A.pitch + q.x0;

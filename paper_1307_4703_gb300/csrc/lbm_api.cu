@@ -426,7 +426,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     }
     // ---- argument checks (no device call before they pass) ----
     if (nx < 1 || ny < 1) return fail(nullptr, LBM_ERR_ARG, "grid %d x %d is empty", nx, ny);
-    if (ny >= (1 << 19) || nx > (1 << lbm::kSegBits) * lbm::kTileNodes - lbm::kTileNodes)
+    if (ny >= lbm::kMaxRows || nx > lbm::kMaxCols)
         return fail(nullptr, LBM_ERR_ARG, "grid %d x %d is too large", nx, ny);
     if (!mask) return fail(nullptr, LBM_ERR_ARG, "mask is NULL");
     if (!(tau > 0.5) || !std::isfinite(tau))
@@ -563,6 +563,39 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         long long fluid = 0;
         int bad_x = -1, bad_y = -1;
     };
+    // The 128-node tiles of row y from its link bytes L: each tile starts at
+    // the row's first fluid node that no earlier tile covers, on a
+    // kTileStart boundary, and its lanes q0 .. q1 are the quads holding
+    // fluid.  Tiles never overlap (every kernel takes a tile's fluid lanes
+    // from the link bytes alone): a row whose next tile would run past the
+    // padded row end is tiled by 128-node segments instead.
+    auto row_tiles = [&](const uint8_t* L, int y, std::vector<uint2>& tiles) {
+        const size_t first = tiles.size();
+        for (int pass = 0; pass < 2; ++pass) {
+            const int gran = pass == 0 ? lbm::kTileStart : lbm::kTileNodes;
+            bool fits = true;
+            int t0 = -1, q0 = 0, q1 = 0;
+            auto push = [&]() {
+                tiles.push_back(make_uint2((uint32_t(y) << lbm::kColBits) | uint32_t(t0 / lbm::kTileStart),
+                                           uint32_t(q0) | (uint32_t(q1) << 8)));
+            };
+            for (int x = 0; x < nx && fits; ++x) {
+                if (L[x] == lbm::kSolid) continue;
+                if (t0 < 0 || x >= t0 + lbm::kTileNodes) {
+                    if (t0 >= 0) push();
+                    t0 = x / gran * gran;
+                    if (t0 + lbm::kTileNodes > pitch) fits = false;
+                    q0 = (x - t0) / 4;
+                }
+                q1 = (x - t0) / 4;
+            }
+            if (fits) {
+                if (t0 >= 0) push();
+                return;
+            }
+            tiles.resize(first);
+        }
+    };
     auto build_rows = [&](int y0, int y1, RowsOut& out) {
         // a row of solid cells stands for the rows outside the grid, one
         // more solid cell on each side of every row for the columns outside
@@ -585,8 +618,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
             const uint8_t* C = rows[1] + 1;
             const uint8_t* N = rows[2] + 1;
             uint8_t* L = links.data() + size_t(y) * pitch;
-            int s_cur = -1, q0 = -1, q1 = -1;  // segment and its first and last quad holding fluid
-            int h_cur = -1, p0 = -1, p1 = -1;  // the same for 64-node segments and node pairs
+            int h_cur = -1, p0 = -1, p1 = -1;  // 64-node segments, their first and last node pair holding fluid
             for (int x = 0; x < nx; ++x) {
                 if (C[x]) continue;
                 // bit i - 1: the pull source x - e_i is not fluid (directions of Eq. lattice)
@@ -600,15 +632,6 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
                 }
                 L[x] = lb;
                 ++out.fluid;
-                const int sg = x / lbm::kTileNodes, q = (x % lbm::kTileNodes) / 4;
-                if (sg != s_cur) {
-                    if (s_cur >= 0)
-                        out.tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s_cur),
-                                                       uint32_t(q0) | (uint32_t(q1) << 8)));
-                    s_cur = sg;
-                    q0 = q;
-                }
-                q1 = q;
                 const int hg = x / lbm::kPairTileNodes, pr = (x % lbm::kPairTileNodes) / 2;
                 if (hg != h_cur) {
                     if (h_cur >= 0)
@@ -619,9 +642,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
                 }
                 p1 = pr;
             }
-            if (s_cur >= 0)
-                out.tiles.push_back(make_uint2((uint32_t(y) << lbm::kSegBits) | uint32_t(s_cur),
-                                               uint32_t(q0) | (uint32_t(q1) << 8)));
+            row_tiles(L, y, out.tiles);
             if (h_cur >= 0)
                 out.tiles64.push_back(make_uint2((uint32_t(y) << lbm::kSegBits64) | uint32_t(h_cur),
                                                  uint32_t(p0) | (uint32_t(p1) << 8)));
@@ -653,7 +674,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (fluid == 0) return fail(nullptr, LBM_ERR_ARG, "the mask has no fluid node");
     // tiles whose row segment holds a port node, listed after the others
     for (uint2& t : tiles) {
-        const int y = int(t.x >> lbm::kSegBits), x0 = int(t.x & ((1u << lbm::kSegBits) - 1)) * lbm::kTileNodes;
+        const int y = int(t.x >> lbm::kColBits);
+        const int x0 = int(t.x & ((1u << lbm::kColBits) - 1)) * lbm::kTileStart;
         for (int side = 0; side < 2; ++side) {
             const int px = rowbc[size_t(side) * ny + y].x;
             if (px >= x0 && px < x0 + lbm::kTileNodes) t.y |= lbm::kPortTile;

@@ -95,6 +95,13 @@ __device__ __forceinline__ uint2 tile_at(const uint2* tiles, int n, int t, int r
     return tiles[reverse ? n - 1 - t : t];
 }
 
+// First node (column) of a 128-node tile and its row.
+__device__ __forceinline__ int tile_x0(uint2 tile)
+{
+    return int(tile.x & ((1u << kColBits) - 1)) * kTileStart;
+}
+
+
 // Storage of the populations.  FP32 keeps them as they are (fluid planes as
 // f_i - w_i, scalar planes as g_i).  FP16 and BF16 hold deviations from a
 // reference: the fluid planes the same f_i - w_i, the scalar planes

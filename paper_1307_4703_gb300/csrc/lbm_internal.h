@@ -16,9 +16,9 @@
 //                grid, or outside a port).  0xFF marks a solid node.
 //   rowbc        2*ny entries (west side then east side): the port node of
 //                that side and row, if any.
-//   tiles        list of the 128-node row segments that hold fluid:
-//                x = (y << 12) | segment, y = first | (last << 8), the first
-//                and last lane (4-node quad) of the segment holding fluid.
+//   tiles        list of the 128-node warp tiles that hold fluid, disjoint:
+//                x = (y << 15) | (first column / 16), y = first | (last << 8),
+//                the first and last lane (4-node quad) holding fluid.
 #pragma once
 
 #include <cstdint>
@@ -29,7 +29,15 @@ namespace lbm {
 
 constexpr int kTileNodes = 128;  // nodes per warp tile: 32 lanes x 4 nodes
 constexpr int kPlanes = 14;      // f_0..f_8, g_0..g_4
-constexpr int kSegBits = 12;     // tile encoding: segment in the low 12 bits
+// A 128-node tile starts at its row's first fluid node not yet covered, on a
+// kTileStart-node boundary (every staged copy stays 16-byte aligned), rather
+// than at a 128-node segment boundary: x = (y << kColBits) | first column /
+// kTileStart.  Tiles never overlap, so a lane's nodes are its tile's to
+// update exactly when they are fluid.
+constexpr int kColBits = 15;
+constexpr int kTileStart = 16;
+constexpr int kMaxRows = 1 << (32 - kColBits);                         // rows a tile entry can name
+constexpr int kMaxCols = (1 << kColBits) * kTileStart - kTileNodes;    // columns, ditto
 constexpr uint8_t kSolid = 0xFF;
 constexpr int kRowFloats = kTileNodes + 8;  // staged plane row: 4-float halo on each side
 constexpr int kBulkMaxThreads = 256;        // bulk variant: at most 7 consumer warps + 1 producer
@@ -69,7 +77,7 @@ struct StepArgs {
     float* dst;             // post-collision populations at time t + 1
     const uint8_t* links;
     const RowBC* rowbc;
-    const uint2* tiles;     // x = (y << 12) | segment, y = first | (last << 8) lane (quad) holding
+    const uint2* tiles;     // x = (y << 15) | first column / 16, y = first | (last << 8) lane (quad) holding
                             // fluid | kPortTile; the n_plain tiles without a port node come first
     int n_tiles;
     int n_plain;            // 0: every tile is treated as a port tile

@@ -95,8 +95,8 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 // bytes and the two port entries), so one warp instruction starts them all.
 __device__ __forceinline__ void issue_tile(const StepArgs& a, uint2 tile, Stage& sg, uint64_t* bar, int lane)
 {
-    const int y = int(tile.x >> kSegBits);
-    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
+    const int y = int(tile.x >> kColBits);
+    const int x0 = tile_x0(tile);
     const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
     // columns of the lanes that hold fluid, and one quad more on each side
     // for the planes that pull from x -+ 1
@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_pipe(const St
         }
         const Stage& sg = st[s];
         const uint2 tile = sg.tile;
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+        const int y = int(tile.x >> kColBits);
+        const int x0 = tile_x0(tile) + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
         const unsigned lk = sg.links[lane];
         const bool act = lk != 0xFFFFFFFFu;

@@ -91,8 +91,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_noalloc_step* s)
     if (!s) return LBM_ERR_ARG;
     if (s->struct_size != sizeof(lbm_noalloc_step))
         return reject(s, LBM_ERR_ARG, "struct_size is %u, expected %zu", s->struct_size, sizeof(lbm_noalloc_step));
-    if (s->nx < 1 || s->ny < 1 || s->ny >= (1 << 19) ||
-        s->nx > (1 << lbm::kSegBits) * lbm::kTileNodes - lbm::kTileNodes)
+    if (s->nx < 1 || s->ny < 1 || s->ny >= lbm::kMaxRows || s->nx > lbm::kMaxCols)
         return reject(s, LBM_ERR_ARG, "grid %d x %d outside the supported range", s->nx, s->ny);
     if (s->pitch < s->nx || s->pitch % lbm::kTileNodes != 0)
         return reject(s, LBM_ERR_ARG, "pitch %d: use a multiple of %d that is at least nx = %d", s->pitch,

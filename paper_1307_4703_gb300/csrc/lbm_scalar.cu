@@ -192,8 +192,8 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) scalar_frozen_bulk(const S
                 if (batch > 0 && !mbar_wait(&empty[s], uint32_t(batch - 1) & 1u)) {
                     good = false;
                 } else {
-                    const int y = int(tile.x >> kSegBits);
-                    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
+                    const int y = int(tile.x >> kColBits);
+                    const int x0 = tile_x0(tile);
                     const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
                     const int us = x0 + 4 * q0, ue = x0 + 4 * q1 + 4;
                     const int ss = us - 4 > 0 ? us - 4 : 0;
@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) scalar_frozen_bulk(const S
             }
             const ScalarStage& sg = st[s];
             const uint2 tile = sg.tile;
-            const int y = int(tile.x >> kSegBits);
-            const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+            const int y = int(tile.x >> kColBits);
+            const int x0 = tile_x0(tile) + 4 * lane;
             const long long oC = (long long)y * a.pitch + x0;
             const unsigned lk = sg.links[lane];
             const bool act = lk != 0xFFFFFFFFu;
@@ -284,8 +284,8 @@ __global__ void __launch_bounds__(128) scalar_frozen_regs(const ScalarArgs a)
     grid_dependency_sync();
     for (int t = blockIdx.x * wpb + warp; t < a.n_tiles; t += gridDim.x * wpb) {
         const uint2 tile = tile_at(a.tiles, a.n_tiles, t, a.reverse);
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+        const int y = int(tile.x >> kColBits);
+        const int x0 = tile_x0(tile) + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
         const long long oS = (long long)(y > 0 ? y - 1 : y) * a.pitch + x0;
         const long long oN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + x0;

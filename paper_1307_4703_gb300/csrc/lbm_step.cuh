@@ -51,8 +51,8 @@ __device__ __forceinline__ void regs_loop(const StepArgs& a, TileRange r, int la
     for (; t < r.n; t += r.stride) {
         const uint2 tile = next;  // the following entry is fetched one tile ahead
         if (t + r.stride < r.n) next = tile_at(r.tiles, r.n, t + r.stride, a.reverse);
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+        const int y = int(tile.x >> kColBits);
+        const int x0 = tile_x0(tile) + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
         // Rows outside the grid are clamped to a valid row: every link that
         // crosses y = -1/2 or y = ny - 1/2 is a wall link, so the value read
@@ -145,8 +145,8 @@ template <typename T>
 __device__ __forceinline__ void issue_tile_async(const StepArgs& a, const T* S, long long P, uint2 tile,
                                                  AsyncStage<T>& st, int lane)
 {
-    const int y = int(tile.x >> kSegBits);
-    const int xs = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
+    const int y = int(tile.x >> kColBits);
+    const int xs = tile_x0(tile);
     const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
     const long long rC = (long long)y * a.pitch + xs;
     const long long rS = (long long)(y > 0 ? y - 1 : y) * a.pitch + xs;
@@ -183,8 +183,8 @@ __device__ __forceinline__ void async_loop(const StepArgs& a, TileRange r, Async
     for (; t < r.n; t += r.stride) {
         const bool more = t + r.stride < r.n;
         const uint2 next = more ? tile_at(r.tiles, r.n, t + r.stride, a.reverse) : make_uint2(0u, 0u);
-        const int y = int(tile.x >> kSegBits);
-        const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+        const int y = int(tile.x >> kColBits);
+        const int x0 = tile_x0(tile) + 4 * lane;
         const long long oC = (long long)y * a.pitch + x0;
         // ---- free flight (pull) from the stage: the current tile's copies,
         //      the wall-link words with them (lanes outside the tile's fluid
@@ -425,8 +425,8 @@ template <typename T, bool kWalls>
 __device__ __forceinline__ void regs_tile(const StepArgs& a, const T* __restrict__ S, T* __restrict__ D,
                                           long long P, uint2 tile, int lane, LaneDiag& diag, bool& bad)
 {
-    const int y = int(tile.x >> kSegBits);
-    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+    const int y = int(tile.x >> kColBits);
+    const int x0 = tile_x0(tile) + 4 * lane;
     const long long oC = (long long)y * a.pitch + x0;
     const long long oS = (long long)(y > 0 ? y - 1 : y) * a.pitch + x0;
     const long long oN = (long long)(y + 1 < a.ny ? y + 1 : y) * a.pitch + x0;
@@ -539,8 +539,8 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
                 if (batch > 0 && !mbar_wait(&empty[s], uint32_t(batch - 1) & 1u)) {
                     good = false;
                 } else {
-                    const int y = int(tile.x >> kSegBits);
-                    const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes;
+                    const int y = int(tile.x >> kColBits);
+                    const int x0 = tile_x0(tile);
                     const int q0 = int(tile.y & 0xFFu), q1 = int((tile.y >> 8) & 0xFFu);
                     // columns of the lanes that hold fluid (widened to whole
                     // 16-byte units), and one unit more on each side for the
@@ -590,8 +590,8 @@ __global__ void __launch_bounds__(kBulkMaxThreads, 2) coupled_step_bulk(const St
             }
             const StageX& sg = st[s];
             const uint2 tile = sg.tile;
-            const int y = int(tile.x >> kSegBits);
-            const int x0 = int(tile.x & ((1u << kSegBits) - 1)) * kTileNodes + 4 * lane;
+            const int y = int(tile.x >> kColBits);
+            const int x0 = tile_x0(tile) + 4 * lane;
             const long long oC = (long long)y * a.pitch + x0;
             const unsigned lk = sg.links[lane];
             const bool act = lk != 0xFFFFFFFFu;

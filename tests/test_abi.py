@@ -201,9 +201,9 @@ def test_create_reports_the_first_isolated_node_of_a_large_mask(lib):
 
 
 def test_create_rejects_grids_beyond_the_tile_encoding(lib):
-    """Rows are encoded in 19 bits and row segments in 12 (4095 segments of
-    128 nodes); one more row or column than that is rejected before any
-    device call."""
-    for nx, ny in ((4, 1 << 19), (524161, 2)):
+    """Tile entries hold the row in 17 bits and the first column / 16 in 15
+    (a tile ends at most at column 2^19 - 1: 524160 columns); one more row or
+    column than that is rejected before any device call."""
+    for nx, ny in ((4, 1 << 17), (524161, 2)):
         st, msg = _create(lib, nx, ny, np.zeros((ny, nx), np.uint8))
         assert st == lbm.LBM_ERR_ARG and "too large" in msg, (nx, ny, msg)

@@ -423,10 +423,10 @@ def test_zero_steps_change_nothing(opts):
     chip.close()
 
 
-@pytest.mark.parametrize("nx,ny", [(524160, 3), (4, 524287)])
+@pytest.mark.parametrize("nx,ny", [(524160, 3), (4, 131071)])
 def test_largest_width_and_height(nx, ny):
-    """The largest lattices the tile encoding admits (4095 segments of 128
-    nodes in a row; 2^19 - 1 rows): a closed box (every edge a wall) from
+    """The largest lattices the tile encoding admits (524160 columns, the
+    last tile starting at column 524032; 2^17 - 1 rows): a closed box (every edge a wall) from
     random fields near rest, two steps, every population against the
     oracle.  Exercises the last segment index and the last row in the tile
     table, the row clamping at both edges and the halos at the last

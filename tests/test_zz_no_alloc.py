@@ -67,7 +67,7 @@ def _tables(prob, pitch):
         for seg in range(pitch // TILE):
             q = np.nonzero(fl[y, seg * TILE:min(nx, (seg + 1) * TILE)])[0] // 4  # fluid quads
             if len(q):
-                tiles.append(((y << 12) | seg, int(q[0]) | (int(q[-1]) << 8)))
+                tiles.append(((y << 15) | (seg * TILE // 16), int(q[0]) | (int(q[-1]) << 8)))
     return links, ports, np.array(tiles, dtype=np.uint32).reshape(-1, 2)
 
 
