@@ -81,7 +81,11 @@ struct lbm_ctx {
 
     int n_tiles = 0;
     int n_tiles64 = 0;
-    int n_plain = 0;  // tiles without a port node, listed first in the tile table
+    int n_plain = 0;  // 16-bit storage: tiles without a port node, listed first in the tile table
+    // both tile tables in row order (port tiles flagged), from which the
+    // device tables are ordered for the launch shape (arrange_tiles)
+    std::vector<uint2> tiles_rows, tiles64_rows;
+    std::vector<uint2> tiles_order, tiles64_order;  // the orders last copied to the device
     int sms = 0;
     int partials_cap = 0;  // blocks the partials buffer holds (any launch shape fits)
     int diag_grid = 0;     // blocks whose partials the last step wrote
@@ -332,6 +336,73 @@ lbm_status step_graph(lbm_ctx* h, lbm::StepArgs a, cudaGraphExec_t* out)
     h->graphs.push_back(g);
     *out = exec;
     return LBM_OK;
+}
+
+// A tile list ordered for a kernel whose warps take entries w, w + G,
+// w + 2G, ... (counted from either end of the table: the steps alternate).
+// With n tiles the warps w < r = n - (k - 1) G take k = ceil(n / G) tiles
+// and the others k - 1, and the entries of the first group are the same set
+// counted from either end.  The tiles that hold a port node take longer, so
+// they go to entries of the warps with fewer tiles; the other tiles keep
+// their row order in the remaining entries.
+std::vector<uint2> order_for_warps(const std::vector<uint2>& rows, long long G)
+{
+    const long long n = (long long)rows.size();
+    if (G <= 0 || n <= G || n % G == 0) return rows;
+    const long long k = (n + G - 1) / G, r = n - (k - 1) * G;
+    std::vector<char> longer(static_cast<size_t>(n), 0);  // entry of a warp that takes k tiles
+    for (long long w = 0; w < r; ++w)
+        for (long long j = 0; j < k; ++j) longer[size_t(w + j * G)] = 1;
+    std::vector<uint2> out(static_cast<size_t>(n));
+    std::vector<char> used(static_cast<size_t>(n), 0);
+    long long p = 0, placed = 0;  // next entry for a port tile (the short warps' first); port tiles placed
+    for (const uint2& t : rows) {
+        if (!(t.y & lbm::kPortTile)) continue;
+        while (p < n && longer[size_t(p)]) ++p;
+        if (p >= n) break;  // more port tiles than short entries: the rest go with the plain tiles
+        out[size_t(p)] = t;
+        used[size_t(p++)] = 1;
+        ++placed;
+    }
+    long long q = 0, skipped = 0;
+    for (const uint2& t : rows) {
+        if ((t.y & lbm::kPortTile) && skipped < placed) {
+            ++skipped;
+            continue;
+        }
+        while (used[size_t(q)]) ++q;
+        out[size_t(q)] = t;
+        used[size_t(q++)] = 1;
+    }
+    return out;
+}
+
+// Copy both tile tables to the device in the order the launch shape L wants:
+// 16-bit storage lists the port tiles last (the register kernels give them
+// blocks of their own, n_plain); FP32 register kernels (variants 1, 4) and
+// variant 5 put them on the warps with fewer tiles (order_for_warps).
+cudaError_t arrange_tiles(lbm_ctx* h, const lbm::StepLaunch& L)
+{
+    const long long G = (long long)L.grid * (L.block / 32);
+    if (h->precision != LBM_FP32) {
+        h->tiles_order = h->tiles_rows;
+        h->n_plain = int(std::stable_partition(h->tiles_order.begin(), h->tiles_order.end(),
+                                               [](const uint2& t) { return !(t.y & lbm::kPortTile); }) -
+                         h->tiles_order.begin());
+    } else {
+        const bool regs = L.variant == lbm::kVariantRegs || L.variant == lbm::kVariantAsync;
+        h->tiles_order = regs ? order_for_warps(h->tiles_rows, G) : h->tiles_rows;
+        h->n_plain = 0;
+    }
+    h->tiles64_order = L.variant == lbm::kVariantPairs ? order_for_warps(h->tiles64_rows, G) : h->tiles64_rows;
+    cudaError_t e = cudaSuccess;
+    if (!h->tiles_order.empty())
+        e = cudaMemcpyAsync(h->tiles, h->tiles_order.data(), h->tiles_order.size() * sizeof(uint2),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !h->tiles64_order.empty())
+        e = cudaMemcpyAsync(h->tiles64, h->tiles64_order.data(), h->tiles64_order.size() * sizeof(uint2),
+                            cudaMemcpyHostToDevice, h->stream);
+    return e;
 }
 
 // One wave of resident blocks, which then stride over the tile table.
@@ -681,9 +752,6 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
             if (px >= x0 && px < x0 + lbm::kTileNodes) t.y |= lbm::kPortTile;
         }
     }
-    const int n_plain = int(std::stable_partition(tiles.begin(), tiles.end(),
-                                                  [](const uint2& t) { return !(t.y & lbm::kPortTile); }) -
-                            tiles.begin());
     for (uint2& t : tiles64) {
         const int y = int(t.x >> lbm::kSegBits64);
         const int x0 = int(t.x & ((1u << lbm::kSegBits64) - 1)) * lbm::kPairTileNodes;
@@ -715,7 +783,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->alloc_user = opt.alloc_user;
     h->n_tiles = int(tiles.size());
     h->n_tiles64 = int(tiles64.size());
-    h->n_plain = n_plain;
+    h->tiles_rows = std::move(tiles);
+    h->tiles64_rows = std::move(tiles64);
     h->solid.assign(mask, mask + size_t(nx) * ny);
     h->fluid = fluid;
     h->precision = opt.precision;
@@ -792,8 +861,8 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->pop[1] = static_cast<float*>(dev_alloc(h, pop_bytes));
     h->links = static_cast<uint8_t*>(dev_alloc(h, links.size()));
     h->rowbc = static_cast<lbm::RowBC*>(dev_alloc(h, rowbc.size() * sizeof(lbm::RowBC)));
-    h->tiles = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, tiles.size()) * sizeof(uint2)));
-    h->tiles64 = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, tiles64.size()) * sizeof(uint2)));
+    h->tiles = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, h->tiles_rows.size()) * sizeof(uint2)));
+    h->tiles64 = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, h->tiles64_rows.size()) * sizeof(uint2)));
     h->partials_cap = std::max(h->launch.grid, sms * kMaxBlocksPerSM);
     h->diag_grid = h->launch.grid;
     h->partials = static_cast<double*>(dev_alloc(h, size_t(h->partials_cap) * 4 * sizeof(double)));
@@ -830,10 +899,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->rowbc, rowbc.data(), rowbc.size() * sizeof(lbm::RowBC),
                             cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !tiles.empty())
-        e = cudaMemcpyAsync(h->tiles, tiles.data(), tiles.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !tiles64.empty())
-        e = cudaMemcpyAsync(h->tiles64, tiles64.data(), tiles64.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = arrange_tiles(h, h->launch);
     if (e == cudaSuccess && batch)
         e = cudaMemcpyAsync(h->rates, batch->rates.data(), size_t(ny) * sizeof(float4), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !woff.empty())
@@ -2046,6 +2112,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old shape
         h->graphs.clear();
         h->launch = best;
+        LBM_CUDA(h, arrange_tiles(h, best));
     }
     return LBM_OK;
 }
