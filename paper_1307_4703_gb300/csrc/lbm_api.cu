@@ -1559,9 +1559,6 @@ lbm_status lbm_load_state(lbm_handle h, const void* buf, size_t bytes)
     return LBM_OK;
 }
 
-namespace {
-}  // namespace
-
 lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_t K, double* J,
                        double* dJ_dtau_c, double* dJ_du_in, double* dJ_dC_in)
 {
