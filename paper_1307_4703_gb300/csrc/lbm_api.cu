@@ -2082,7 +2082,8 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
             continue;
         }
         L.grid = std::min(wave_grid(h, L, per_sm), h->partials_cap);
-        e = cudaMemsetAsync(err, 0, sizeof(unsigned), h->stream);
+        e = arrange_tiles(h, L);  // each shape is timed with its own tile order
+        if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned), h->stream);
         // the step kernel alone (the wall values, when used, are computed
         // once below from the current state)
         for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = lbm::launch_step(a, L, h->stream);
@@ -2109,8 +2110,8 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old shape
         h->graphs.clear();
         h->launch = best;
-        LBM_CUDA(h, arrange_tiles(h, best));
     }
+    LBM_CUDA(h, arrange_tiles(h, h->launch));  // the order of the shape kept
     return LBM_OK;
 }
 
