@@ -1031,27 +1031,29 @@ __device__ __forceinline__ void finish_partials(const double* partials, int n, d
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 64) {
         double t[4] = {0.0, 0.0, 0.0, 0.0};
-        int b = threadIdx.x;
-        // four blocks' partials in flight at once (16-byte loads), added in
-        // block order
-        for (; b + 3 * 64 < n; b += 4 * 64) {
-            double2 v[4][2];
+        // up to eight blocks' partials in flight at once (16-byte loads; one
+        // round for grids of up to 512 blocks), added in block order
+        constexpr int kFold = 8;
+        for (int b0 = threadIdx.x; b0 < n; b0 += kFold * 64) {
+            double2 v[kFold][2];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                v[j][0] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * (b + 64 * j)));
-                v[j][1] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * (b + 64 * j) + 2));
+            for (int j = 0; j < kFold; ++j) {
+                const int b = b0 + 64 * j;
+                if (b < n) {
+                    v[j][0] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * b));
+                    v[j][1] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * b + 2));
+                }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                t[0] += v[j][0].x;
-                t[1] += v[j][0].y;
-                t[2] += v[j][1].x;
-                t[3] += v[j][1].y;
+            for (int j = 0; j < kFold; ++j) {
+                if (b0 + 64 * j < n) {
+                    t[0] += v[j][0].x;
+                    t[1] += v[j][0].y;
+                    t[2] += v[j][1].x;
+                    t[3] += v[j][1].y;
+                }
             }
         }
-        for (; b < n; b += 64)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) t[q] += __ldcg(partials + 4 * b + q);
 #pragma unroll
         for (int q = 0; q < 4; ++q) t[q] = warp_sum(t[q]);
         if (lane == 0)
