@@ -1222,13 +1222,18 @@ lbm_status lbm_step_diagnostics(lbm_handle h, int64_t n, double* out)
     if (lbm_status js = join_scalar(h)) return js;
     lbm::StepArgs a = step_args(h);
     a.diag_ticket = h->err + 1;
+    // The in-kernel fold adds the partials with 64 threads; blocks of one warp
+    // (variant 3 with a single computing warp) leave it to the reduction
+    // kernel, launched after each step (the same order of additions).
+    const bool fold = h->launch.block >= 64;
     for (int64_t k = 0; k < n; ++k) {
         h->mask_words(h->step, a.open_mask);
         a.src = h->pop[h->cur];
         a.dst = h->pop[1 - h->cur];
         a.reverse = h->cur;
-        a.diag_out = dev + 4 * k;  // the step's last block writes the totals here
+        a.diag_out = fold ? dev + 4 * k : nullptr;  // the step's last block writes the totals here
         cudaError_t e = launch_full_step(h, a, h->launch, h->stream);
+        if (e == cudaSuccess && !fold) e = lbm::launch_diag_finish(h->partials, h->launch.grid, dev + 4 * k, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
         h->gbuf = h->cur;

@@ -338,13 +338,16 @@ def test_async_diagnostics_match_the_synchronous_read():
 
 @pytest.mark.parametrize("opts", [dict(), dict(variant=2, pipeline_stages=2, consumer_warps=3),
                                   dict(variant=4, block_threads=64), dict(variant=5), dict(precision="fp16"),
-                                  dict(precision="bf16", variant=1), dict(wall_scheme=1)])
+                                  dict(precision="bf16", variant=1), dict(wall_scheme=1),
+                                  dict(max_blocks=5), dict(max_blocks=17), dict(variant=3, consumer_warps=1)])
 def test_in_kernel_diagnostics_equal_the_reduction_launch(opts):
     """lbm_step_diagnostics: the step kernel's last block writes the totals
     of every step (into pinned host memory and into device memory); each row
     has the same bits as lbm_get_diagnostics after that step (same order of
     additions), the populations match lbm_step's, and the ticket counter is
-    back at zero after every step (a second run gives the same rows)."""
+    back at zero after every step (a second run gives the same rows).  Grids
+    of 5 and 17 blocks, and blocks of one warp (totals from the reduction
+    kernel launched after each step instead) included."""
     prob, init = W.random_case(41, 300, 48, solid_frac=0.1)
     prob["states"] = [1, 2, 3, 0]
     a = lbm.Chip.from_problem(prob, **opts)
