@@ -247,9 +247,10 @@ lbm_status lbm_get_fields_device(lbm_handle h, float* rho, float* ux, float* uy,
  * out[2] = sum of rho u_x and out[3] = sum of C u_x over the nodes of the
  * PRESSURE ports open during that step.  Each lane of the step kernel sums
  * its nodes in compensated FP32; the lanes of a block are combined as
- * double-float pairs (about 44 significant bits) into one FP64 partial per
- * block, and the blocks' partials in FP64, in a fixed order (run-to-run
- * identical for a given launch shape).  Launches a small reduction kernel
+ * double-float pairs (about 44 significant bits) into one double-float
+ * partial per block, and the blocks' partials as double-float pairs too, in
+ * a fixed order (run-to-run identical for a given launch shape), rounded to
+ * double at the end.  Launches a small reduction kernel
  * and synchronises the stream; returns LBM_ERR_NUMERIC / LBM_ERR_TIMEOUT if
  * the error word is set. */
 lbm_status lbm_get_diagnostics(lbm_handle h, double out[4]);
@@ -472,8 +473,8 @@ lbm_status lbm_set_instance_schedule(lbm_handle h, int32_t k, int64_t period, in
  *
  * The step kernel's only scratch memory, its per-block partial sums of the
  * diagnostics, lives in a fixed array inside the library of
- * LBM_NOALLOC_MAX_BLOCKS x 4 doubles (64 KiB), which every GPU that loads the
- * library holds until the process exits.  The first call on a device sets
+ * LBM_NOALLOC_MAX_BLOCKS x 4 double-float pairs of 8 bytes (64 KiB), which
+ * every GPU that loads the library holds until the process exits.  The first call on a device sets
  * that device up (looks up the array's device address and the launch
  * shape); make that first call before capturing the stream into a CUDA
  * graph.  All calls share the one array: calls whose kernels overlap on the

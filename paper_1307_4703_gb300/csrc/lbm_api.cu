@@ -74,7 +74,7 @@ struct lbm_ctx {
     lbm::RowBC* rowbc = nullptr;
     uint2* tiles = nullptr;
     uint2* tiles64 = nullptr;  // the same row segments in 64-node halves (variant 5)
-    double* partials = nullptr;
+    float2* partials = nullptr;  // per-block diagnostics partials, double-float pairs
     double* diag = nullptr;       // 4 totals formed by lbm_get_diagnostics
     unsigned int* err = nullptr;
     float* fields_tmp = nullptr;  // 4 * nx * ny floats
@@ -865,7 +865,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
     h->tiles64 = static_cast<uint2*>(dev_alloc(h, std::max<size_t>(1, h->tiles64_rows.size()) * sizeof(uint2)));
     h->partials_cap = std::max(h->launch.grid, sms * kMaxBlocksPerSM);
     h->diag_grid = h->launch.grid;
-    h->partials = static_cast<double*>(dev_alloc(h, size_t(h->partials_cap) * 4 * sizeof(double)));
+    h->partials = static_cast<float2*>(dev_alloc(h, size_t(h->partials_cap) * 4 * sizeof(float2)));
     // the error word, then the ticket counter of lbm_step_diagnostics
     h->err = static_cast<unsigned*>(dev_alloc(h, 2 * sizeof(unsigned)));
     if (h->multi_step > 0) {
@@ -906,7 +906,7 @@ lbm_status create_impl(lbm_handle* out, int32_t nx, int32_t ny, const uint8_t* m
         e = cudaMemcpyAsync(h->woff, woff.data(), woff.size() * sizeof(long long), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, 2 * sizeof(unsigned), st);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(h->partials, 0, size_t(h->partials_cap) * 4 * sizeof(double), st);
+        e = cudaMemsetAsync(h->partials, 0, size_t(h->partials_cap) * 4 * sizeof(float2), st);
     if (e == cudaSuccess)
         e = lbm::launch_init_rest(h->pop[0], ny, pitch, float(h->rho0), h->wg0, h->wg1, float(h->C0),
                                   h->precision, h->decay, st);
@@ -1222,10 +1222,10 @@ lbm_status lbm_step_diagnostics(lbm_handle h, int64_t n, double* out)
     if (lbm_status js = join_scalar(h)) return js;
     lbm::StepArgs a = step_args(h);
     a.diag_ticket = h->err + 1;
-    // The in-kernel fold adds the partials with 64 threads; blocks of one warp
-    // (variant 3 with a single computing warp) leave it to the reduction
-    // kernel, launched after each step (the same order of additions).
-    const bool fold = h->launch.block >= 64;
+    // The in-kernel fold adds the partials with lbm::kFoldThreads threads;
+    // smaller blocks leave it to the reduction kernel, launched after each
+    // step (the same order of additions).
+    const bool fold = h->launch.block >= lbm::kFoldThreads;
     for (int64_t k = 0; k < n; ++k) {
         h->mask_words(h->step, a.open_mask);
         a.src = h->pop[h->cur];
@@ -1604,7 +1604,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     double* gu = static_cast<double*>(tmp.get(size_t(2) * h->ny * sizeof(double)));
     double* gc = static_cast<double*>(tmp.get(size_t(2) * h->ny * sizeof(double)));
     double* dJ = static_cast<double*>(tmp.get(2 * sizeof(double)));
-    double* rp = static_cast<double*>(tmp.get(size_t(h->launch.grid) * 4 * sizeof(double)));
+    float2* rp = static_cast<float2*>(tmp.get(size_t(h->launch.grid) * 4 * sizeof(float2)));
     int* ox = static_cast<int*>(tmp.get(size_t(obj->n) * sizeof(int)));
     int* oy = static_cast<int*>(tmp.get(size_t(obj->n) * sizeof(int)));
     float* ot = static_cast<float*>(tmp.get(size_t(obj->n) * sizeof(float)));
@@ -2021,7 +2021,7 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     // trials write to scratch buffers: the state, step count and diagnostics stay as they are
     Scratch sc(h);
     void* dst = sc.get(size_t(h->plane) * lbm::kPlanes * h->elem);
-    double* part = static_cast<double*>(sc.get(size_t(h->partials_cap) * 4 * sizeof(double)));
+    float2* part = static_cast<float2*>(sc.get(size_t(h->partials_cap) * 4 * sizeof(float2)));
     unsigned* err = static_cast<unsigned*>(sc.get(sizeof(unsigned)));
     if (!dst || !part || !err) return fail(h, LBM_ERR_OOM, "no device memory for the trial steps");
     LBM_CUDA(h, lbm::prepare_step_kernels());

@@ -1019,39 +1019,55 @@ __device__ __forceinline__ void collide_quad(float4 (&v)[kPlanes], unsigned lk, 
     }
 }
 
-// Totals of the four diagnostics from the partials of n blocks (4 doubles
-// each), in one fixed order whatever block runs it: the block's first 64
-// threads, thread i adding blocks i, i + 64, ... in turn, then the lanes of
-// each of the two warps by shuffles, then the two warps.  Partials written by
-// other blocks of a running grid are read through L2 (ld.global.cg).  Every
-// thread of the block calls this (it has a barrier).
-__device__ __forceinline__ void finish_partials(const double* partials, int n, double* out)
+// Totals of the four diagnostics from the partials of n blocks (4
+// double-float pairs each), in one fixed order whatever block runs it: the
+// block's first kFoldThreads threads, thread i taking blocks i + kFoldThreads
+// j for j = 0, 1, ... in rounds of eight (one round for grids of up to 1024
+// blocks), the eight of a round added as a pairwise tree (absent blocks count
+// as zero) and the rounds in turn; then the lanes of each warp by shuffles,
+// then the four warps pairwise; one double per diagnostic written.  Every
+// addition is a double-float one on the FP32 pipes, and the loads are one
+// round: it is the tail of the step that forms its own totals, and GB300
+// issues FP64 arithmetic at a small fraction of its FP32 rate.  Partials
+// written by other blocks of a running grid are read through L2
+// (ld.global.cg).  Every thread of the block calls this (it has a barrier);
+// the block has at least kFoldThreads threads.
+__device__ __forceinline__ DF df_tree8(const DF (&x)[8])
 {
-    __shared__ double red[2][4];
+    return df_add(df_add(df_add(x[0], x[1]), df_add(x[2], x[3])), df_add(df_add(x[4], x[5]), df_add(x[6], x[7])));
+}
+
+__device__ __forceinline__ void finish_partials(const float2* partials, int n, double* out)
+{
+    __shared__ DF red[kFoldThreads / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 64) {
-        double t[4] = {0.0, 0.0, 0.0, 0.0};
-        // up to eight blocks' partials in flight at once (16-byte loads; one
-        // round for grids of up to 512 blocks), added in block order
-        constexpr int kFold = 8;
-        for (int b0 = threadIdx.x; b0 < n; b0 += kFold * 64) {
-            double2 v[kFold][2];
+    if (threadIdx.x < kFoldThreads) {
+        DF t[4];
 #pragma unroll
-            for (int j = 0; j < kFold; ++j) {
-                const int b = b0 + 64 * j;
+        for (int q = 0; q < 4; ++q) t[q] = DF{0.f, 0.f};
+        constexpr int kRound = 8;
+        for (int b0 = threadIdx.x; b0 < n; b0 += kRound * kFoldThreads) {
+            float4 v[kRound][2];  // diagnostics 0, 1 and 2, 3 of a block, (hi, lo) each
+#pragma unroll
+            for (int j = 0; j < kRound; ++j) {
+                const int b = b0 + kFoldThreads * j;
                 if (b < n) {
-                    v[j][0] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * b));
-                    v[j][1] = __ldcg(reinterpret_cast<const double2*>(partials + 4 * b + 2));
+                    v[j][0] = __ldcg(reinterpret_cast<const float4*>(partials + 4 * b));
+                    v[j][1] = __ldcg(reinterpret_cast<const float4*>(partials + 4 * b + 2));
+                } else {
+                    v[j][0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < kFold; ++j) {
-                if (b0 + 64 * j < n) {
-                    t[0] += v[j][0].x;
-                    t[1] += v[j][0].y;
-                    t[2] += v[j][1].x;
-                    t[3] += v[j][1].y;
+            for (int q = 0; q < 4; ++q) {
+                DF x[kRound];
+#pragma unroll
+                for (int j = 0; j < kRound; ++j) {
+                    const float4& w = v[j][q >> 1];
+                    x[j] = (q & 1) ? DF{w.z, w.w} : DF{w.x, w.y};
                 }
+                t[q] = df_add(t[q], df_tree8(x));
             }
         }
 #pragma unroll
@@ -1061,7 +1077,10 @@ __device__ __forceinline__ void finish_partials(const double* partials, int n, d
             for (int q = 0; q < 4; ++q) red[warp][q] = t[q];
     }
     __syncthreads();
-    if (threadIdx.x < 4) out[threadIdx.x] = red[0][threadIdx.x] + red[1][threadIdx.x];
+    if (threadIdx.x < 4) {
+        const int q = threadIdx.x;
+        out[q] = df_value(df_add(df_add(red[0][q], red[1][q]), df_add(red[2][q], red[3][q])));
+    }
 }
 
 // The totals of a step formed inside it: the last block to finish adds up
@@ -1069,7 +1088,7 @@ __device__ __forceinline__ void finish_partials(const double* partials, int n, d
 // visible before the ticket is taken, and the block that draws the last
 // ticket reads them all after it).  Out of line, so that the step kernels
 // carry no more than a call when it is not asked for.
-__device__ __noinline__ void fold_totals(const double* partials, unsigned* ticket, double* out)
+__device__ __noinline__ void fold_totals(const float2* partials, unsigned* ticket, double* out)
 {
     __shared__ bool last;
     if (threadIdx.x < 4) __threadfence();
@@ -1083,8 +1102,8 @@ __device__ __noinline__ void fold_totals(const double* partials, unsigned* ticke
 }
 
 // The block's partial sums of the four diagnostics: lanes and warps combined
-// as double-float pairs, the fluid node count as an integer, and one double
-// per diagnostic written.  The cross-block total is formed on demand by
+// as double-float pairs, the fluid node count as an integer (added to the
+// first as an exact pair), and one double-float pair per diagnostic written.  The cross-block total is formed on demand by
 // diag_finish.
 __device__ __forceinline__ void block_partials(const StepArgs& a, const LaneDiag& d)
 {
@@ -1113,7 +1132,11 @@ __device__ __forceinline__ void block_partials(const StepArgs& a, const LaneDiag
             s = df_add(s, red[w][threadIdx.x]);
             nb += red_n[w];
         }
-        a.partials[blockIdx.x * 4 + threadIdx.x] = (threadIdx.x == 0 ? double(nb) : 0.0) + df_value(s);
+        if (threadIdx.x == 0) {
+            const float hi = float(nb);  // nb = hi + lo exactly (|lo| <= 64 for any int)
+            s = df_add(DF{hi, float(static_cast<long long>(nb) - static_cast<long long>(hi))}, s);
+        }
+        a.partials[blockIdx.x * 4 + threadIdx.x] = make_float2(s.hi, s.lo);
     }
     if (a.diag_out != nullptr) fold_totals(a.partials, a.diag_ticket, a.diag_out);
 }

@@ -53,6 +53,7 @@ constexpr uint32_t kPortTile = 1u << 16;
 constexpr int kSegBits64 = 13;      // 64-node tile encoding: segment in the low 13 bits
 enum Precision { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 constexpr float kCRef = 0.5f;  // reference concentration of 16-bit scalar storage
+constexpr int kFoldThreads = 128;  // threads that add up the block partials of the diagnostics
 
 struct StepLaunch {
     int variant;  // kVariantRegs, kVariantBulk, kVariantPipe, kVariantAsync or kVariantPairs
@@ -102,7 +103,7 @@ struct StepArgs {
                             // the wall values launch_wall_values computed for this step; null: halfway
                             // bounce-back
     uint32_t open_mask[kMaskWords];  // valve bits of this step: channel c is bit c % 32 of word c / 32
-    double* partials;       // 4 diagnostics partial sums per block (scratch)
+    float2* partials;       // 4 diagnostics partial sums per block, double-float pairs (hi, lo) (scratch)
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
     float gref0, gref1;     // 16-bit storage: offsets w_0 C_ref and w_1 C_ref of the scalar planes
     unsigned barrier_extra; // multi-step kernel: arrivals its barriers wait for beyond the grid's
@@ -182,7 +183,7 @@ struct ScalarArgs {
     float omega_g, wg0, wg1, inv_cs2g;
     float decay;            // k of the reaction term R = -k C (0: none)
     uint32_t open_mask;
-    double* partials;       // writes slots 1 and 3 of each block's four
+    float2* partials;       // writes slots 1 and 3 of each block's four (double-float pairs)
     int n_partials;         // entries of `partials` (>= grid); those beyond the grid get 0
     int fluid_blocks;       // entries holding the last coupled step's fluid partials (slots 0, 2);
                             // blocks at or beyond it zero their slots 0 and 2
@@ -221,7 +222,7 @@ cudaError_t launch_step_walls(const StepArgs& a, const StepLaunch& l, cudaStream
 cudaError_t step_walls_occupancy(const StepLaunch& l, int* blocks_per_sm);
 cudaError_t prepare_walls_kernels();
 
-cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s);
+cudaError_t launch_diag_finish(const float2* partials, int n_blocks, double* out, cudaStream_t s);
 // n coupled steps (FP32 storage, halfway bounce-back) in one cooperative
 // launch of `grid` blocks of `block` threads, all resident (grid <= the
 // occupancy times the SMs): src holds time t; with seq_stride = 0 the result

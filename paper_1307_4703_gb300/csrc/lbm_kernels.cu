@@ -41,7 +41,7 @@ namespace {
 // Totals of the block partials of the last step (finish_partials: the same
 // order, and so the same bits, as the step kernels' own in-kernel totals).
 // out may be page-locked host memory (written over the interconnect).
-__global__ void diag_finish(const double* partials, int n_blocks, double* out)
+__global__ void diag_finish(const float2* partials, int n_blocks, double* out)
 {
     grid_dependency_sync();  // the step kernel before it has written the partials
     finish_partials(partials, n_blocks, out);
@@ -495,12 +495,12 @@ size_t async_smem_bytes(int block, int precision)
     return per_warp * size_t(block / 32);
 }
 
-cudaError_t launch_diag_finish(const double* partials, int n_blocks, double* out, cudaStream_t s)
+cudaError_t launch_diag_finish(const float2* partials, int n_blocks, double* out, cudaStream_t s)
 {
     // a programmatic dependent of the step before it, like the steps
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1);
-    cfg.blockDim = dim3(64);
+    cfg.blockDim = dim3(kFoldThreads);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

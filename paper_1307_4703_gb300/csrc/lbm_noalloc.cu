@@ -21,15 +21,15 @@ constexpr int kMaxDevices = 64;
 constexpr int kConsumers = 3;
 constexpr int kStagesPerConsumer = 1;
 
-// Per-block partial sums of the four diagnostics, 4 doubles per block of the
-// step kernel.  A fixed 64 KiB that every GPU loading the library keeps until
+// Per-block partial sums of the four diagnostics, 4 double-float pairs (8
+// bytes each) per block of the step kernel.  A fixed 64 KiB that every GPU loading the library keeps until
 // the process exits; host code reaches it only through the address returned
 // by cudaGetSymbolAddress for the current device.
-static __device__ __align__(256) double g_step_scratch[LBM_NOALLOC_MAX_BLOCKS * 4];
+static __device__ __align__(256) float2 g_step_scratch[LBM_NOALLOC_MAX_BLOCKS * 4];
 
 struct DeviceSetup {
     bool ready;
-    double* scratch;  // device address of g_step_scratch on this device
+    float2* scratch;  // device address of g_step_scratch on this device
     int grid_cap;     // one wave of resident blocks, at most LBM_NOALLOC_MAX_BLOCKS
 };
 DeviceSetup g_setup[kMaxDevices];
@@ -62,7 +62,7 @@ lbm_status setup_device(const lbm_noalloc_step* s, int dev, DeviceSetup* out)
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup& d = g_setup[dev];
     if (!d.ready) {
-        double* ptr = nullptr;
+        float2* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_step_scratch);
         if (e != cudaSuccess)
             return reject(s, LBM_ERR_CUDA, "cudaGetSymbolAddress of the step scratch: %s", cudaGetErrorString(e));

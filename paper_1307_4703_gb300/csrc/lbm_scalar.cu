@@ -125,11 +125,11 @@ __device__ __forceinline__ void scalar_partials(const ScalarArgs& a, const Kahan
     if (threadIdx.x < 2) {
         DF sum = red[0][threadIdx.x];
         for (int w = 1; w < int(blockDim.x >> 5); ++w) sum = df_add(sum, red[w][threadIdx.x]);
-        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = df_value(sum);
+        a.partials[blockIdx.x * 4 + 1 + 2 * threadIdx.x] = make_float2(sum.hi, sum.lo);
         for (int b = blockIdx.x + gridDim.x; b < a.n_partials; b += gridDim.x)
-            a.partials[b * 4 + 1 + 2 * threadIdx.x] = 0.0;
+            a.partials[b * 4 + 1 + 2 * threadIdx.x] = make_float2(0.f, 0.f);
         // blocks beyond the last coupled step's grid hold no fluid partial
-        if (int(blockIdx.x) >= a.fluid_blocks) a.partials[blockIdx.x * 4 + 2 * threadIdx.x] = 0.0;
+        if (int(blockIdx.x) >= a.fluid_blocks) a.partials[blockIdx.x * 4 + 2 * threadIdx.x] = make_float2(0.f, 0.f);
     }
 }
 
