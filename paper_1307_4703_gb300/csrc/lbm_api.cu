@@ -1604,7 +1604,6 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     double* gu = static_cast<double*>(tmp.get(size_t(2) * h->ny * sizeof(double)));
     double* gc = static_cast<double*>(tmp.get(size_t(2) * h->ny * sizeof(double)));
     double* dJ = static_cast<double*>(tmp.get(2 * sizeof(double)));
-    float2* rp = static_cast<float2*>(tmp.get(size_t(h->launch.grid) * 4 * sizeof(float2)));
     int* ox = static_cast<int*>(tmp.get(size_t(obj->n) * sizeof(int)));
     int* oy = static_cast<int*>(tmp.get(size_t(obj->n) * sizeof(int)));
     float* ot = static_cast<float*>(tmp.get(size_t(obj->n) * sizeof(float)));
@@ -1619,7 +1618,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         coop_grid = std::max(1, std::min(agrid, std::max(1, cps) * sms));
     }
     if (!ckpt || (seg_slots > 0 && !seg) || !adj[0] || !adj[1] || !adj[2] || !dn || !gw || !gu || !gc || !dJ ||
-        !rp || !ox || !oy || !ot || !ow || (coop && !masks_d))
+        !ox || !oy || !ot || !ow || (coop && !masks_d))
         return fail(h, LBM_ERR_OOM, "adjoint: device memory for %lld checkpoints and %d recomputed states not available",
                     n_ck, seg_slots);
 
@@ -1641,7 +1640,9 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     a.wg0 = h->wg0;
     a.wg1 = h->wg1;
     a.inv_cs2g = h->inv_cs2g;
-    a.partials = h->partials;
+    // Only the sweep's last step forms diagnostics: the call leaves those of
+    // its final state, and nothing reads the others.
+    a.partials = nullptr;
     a.err = h->err;
     const int64_t t0 = h->step;
     if (lbm_status js = join_scalar(h)) return js;
@@ -1678,6 +1679,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         a.dst = h->pop[1 - h->cur];
         a.reverse = int((n - 1) & 1);
         a.open_mask[0] = h->mask_at(t0 + n - 1);
+        a.partials = h->partials;
         cudaError_t e = lbm::launch_step(a, h->launch, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
@@ -1693,6 +1695,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
             a.dst = t + 1 < n ? reinterpret_cast<float*>(ckpt + size_t(t + 1) * S) : h->pop[1 - h->cur];
             a.reverse = int(t & 1);
             a.open_mask[0] = h->mask_at(t0 + t);
+            a.partials = t + 1 < n ? nullptr : h->partials;
             cudaError_t e = lbm::launch_step(a, h->launch, st);
             if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         }
@@ -1738,6 +1741,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
         a.dst = h->pop[1 - h->cur];
         a.reverse = int((h->cur + len - 1) & 1);
         a.open_mask[0] = h->mask_at(t0 + n - 1);
+        a.partials = h->partials;
         cudaError_t e = lbm::launch_step(a, h->launch, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "coupled step launch");
         h->cur = 1 - h->cur;
@@ -1793,7 +1797,7 @@ lbm_status lbm_adjoint(lbm_handle h, const lbm_objective* obj, int64_t n, int32_
     A.err = h->err;
     A.barrier_extra = h->barrier_extra;
     lbm::StepArgs r = a;
-    r.partials = rp;  // keep the diagnostics of the last forward step
+    r.partials = nullptr;  // recomputed states only: the diagnostics stay those of the last forward step
     // adj[0] holds A(n); M(t) alternates between adj[1] and adj[2]
     int mid = 0;  // 0 before the first reverse step, else adj[mid] holds M(t+1)
     // One reverse step t (state `state`): the first one reads A(n), the

@@ -1103,10 +1103,13 @@ __device__ __noinline__ void fold_totals(const float2* partials, unsigned* ticke
 
 // The block's partial sums of the four diagnostics: lanes and warps combined
 // as double-float pairs, the fluid node count as an integer (added to the
-// first as an exact pair), and one double-float pair per diagnostic written.  The cross-block total is formed on demand by
+// first as an exact pair), and one double-float pair per diagnostic written.
+// Null partials: a step whose diagnostics nothing reads (the forward steps
+// inside the adjoint but the last) forms none.  The cross-block total is formed on demand by
 // diag_finish.
 __device__ __forceinline__ void block_partials(const StepArgs& a, const LaneDiag& d)
 {
+    if (a.partials == nullptr) return;  // uniform over the grid
     __shared__ DF red[32][4];
     __shared__ int red_n[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;

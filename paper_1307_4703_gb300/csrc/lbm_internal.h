@@ -103,7 +103,8 @@ struct StepArgs {
                             // the wall values launch_wall_values computed for this step; null: halfway
                             // bounce-back
     uint32_t open_mask[kMaskWords];  // valve bits of this step: channel c is bit c % 32 of word c / 32
-    float2* partials;       // 4 diagnostics partial sums per block, double-float pairs (hi, lo) (scratch)
+    float2* partials;       // 4 diagnostics partial sums per block, double-float pairs (hi, lo) (scratch);
+                            // null: the step forms no diagnostics
     unsigned int* err;      // sticky error word: bit 0 numeric, bit 1 timeout
     float gref0, gref1;     // 16-bit storage: offsets w_0 C_ref and w_1 C_ref of the scalar planes
     unsigned barrier_extra; // multi-step kernel: arrivals its barriers wait for beyond the grid's

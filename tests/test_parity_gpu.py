@@ -387,6 +387,40 @@ def test_in_kernel_diagnostics_equal_the_reduction_launch(opts):
     b.close()
 
 
+def test_diagnostics_over_more_than_1024_block_partials():
+    """Blocks of two warps on a 512 x 600 lattice of about 2400 tiles: a grid
+    of more than 1024 blocks, whose partials the reduction adds in two rounds
+    per thread.  The totals after three steps agree with the oracle's
+    diagnostics, and the rows of lbm_step_diagnostics (the reduction kernel
+    after each step, for blocks of fewer than 128 threads) have the bits of
+    lbm_get_diagnostics."""
+    prob, init = W.random_case(43, 512, 600, solid_frac=0.05)
+    a = lbm.Chip.from_problem(prob, variant=1, block_threads=64)
+    assert a.info()["grid"] > 1024
+    b = lbm.Chip.from_problem(prob, variant=1, block_threads=64)
+    ref = oracle.from_problem(prob)
+    states = prob["states"]
+    for c in (a, b, ref):
+        c.init_equilibrium(**init)
+    for c in (a, b):
+        c.set_valve_schedule(1, states)
+    rows = torch.zeros((3, 4), dtype=torch.float64, device="cuda")
+    a.step_diagnostics(3, rows.data_ptr())
+    want = []
+    for t in range(3):
+        b.step(1)
+        want.append(b.diagnostics())
+        ref.step(states[t])
+    a.synchronize()
+    assert np.array_equal(rows.cpu().numpy(), np.array(want))
+    d, rd = want[-1], ref.diagnostics(states[2])
+    assert abs(d[0] - rd[0]) / rd[0] < 1e-6
+    assert abs(d[1] - rd[1]) <= 1e-5 * max(1.0, abs(rd[1]))
+    assert abs(d[2] - rd[2]) <= 1e-5 and abs(d[3] - rd[3]) <= 1e-5
+    a.close()
+    b.close()
+
+
 def test_misaligned_allocator_memory_is_refused(monkeypatch):
     """A caller's allocator that returns memory off the 256-byte boundary:
     lbm_create hands every such pointer straight back and fails with

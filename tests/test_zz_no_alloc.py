@@ -90,7 +90,7 @@ def _case(name):
     if name == "random-300x40":  # about 120 tiles: at most one per block
         return W.random_case(41, 300, 40, solid_frac=0.15)
     # 1100 x 280: 9 segments x 280 rows = 2520 tiles, more than the 2048-block cap;
-    # the grid is one wave of resident blocks, so the reduction reads over 256 partials
+    # the grid is one wave of resident blocks (several hundred partials to add)
     return W.random_case(43, 1100, 280, solid_frac=0.1)
 
 
