@@ -1105,8 +1105,8 @@ __device__ __noinline__ void fold_totals(const float2* partials, unsigned* ticke
 // as double-float pairs, the fluid node count as an integer (added to the
 // first as an exact pair), and one double-float pair per diagnostic written.
 // Null partials: a step whose diagnostics nothing reads (the forward steps
-// inside the adjoint but the last) forms none.  The cross-block total is formed on demand by
-// diag_finish.
+// inside the adjoint but the last) forms none.  The cross-block total is
+// formed on demand by diag_finish.
 __device__ __forceinline__ void block_partials(const StepArgs& a, const LaneDiag& d)
 {
     if (a.partials == nullptr) return;  // uniform over the grid
