@@ -272,7 +272,9 @@ lbm_status lbm_get_diagnostics_async(lbm_handle h, double* out);
  * (the four values of lbm_get_diagnostics) written to out[4k .. 4k+3] for
  * the k-th of these steps by the step kernel itself: the last of its blocks
  * to finish adds up the blocks' partials, in the same order as
- * lbm_get_diagnostics, so no reduction launch follows the step.  out: 4 n
+ * lbm_get_diagnostics, so no reduction launch follows the step (variants 1
+ * and 4 with halfway bounce-back and blocks of at least 128 threads; other
+ * launch shapes run the reduction kernel after each step, same bits).  out: 4 n
  * doubles of device memory, or of page-locked host memory that the device
  * can address (cudaHostAlloc / cudaMallocHost), owned by the caller and
  * valid after the stream is synchronised.  LBM_ERR_ARG for NULL or any

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
-SOURCES = ["lbm_kernels.cu", "lbm_walls.cu", "lbm_adjoint.cu", "lbm_scalar.cu", "lbm_api.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_fold_steps.cu", "lbm_walls.cu", "lbm_adjoint.cu", "lbm_scalar.cu", "lbm_api.cu",
+           "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1222,10 +1222,11 @@ lbm_status lbm_step_diagnostics(lbm_handle h, int64_t n, double* out)
     if (lbm_status js = join_scalar(h)) return js;
     lbm::StepArgs a = step_args(h);
     a.diag_ticket = h->err + 1;
-    // The in-kernel fold adds the partials with lbm::kFoldThreads threads;
-    // smaller blocks leave it to the reduction kernel, launched after each
-    // step (the same order of additions).
-    const bool fold = h->launch.block >= lbm::kFoldThreads;
+    // The in-kernel fold: variants 1 and 4 with blocks of at least
+    // lbm::kFoldThreads threads and halfway bounce-back; other launch shapes
+    // leave it to the reduction kernel, launched after each step (the same
+    // order of additions, the same bits).
+    const bool fold = lbm::step_folds_totals(h->launch);
     for (int64_t k = 0; k < n; ++k) {
         h->mask_words(h->step, a.open_mask);
         a.src = h->pop[h->cur];

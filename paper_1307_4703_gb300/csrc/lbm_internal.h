@@ -110,7 +110,8 @@ struct StepArgs {
     unsigned barrier_extra; // multi-step kernel: arrivals its barriers wait for beyond the grid's
                             // (0; a test hook sets 1 so that the bounded wait runs out)
     double* diag_out;       // non-null: the step's last block to finish also forms the four
-                            // totals of the partials and writes them here (device-addressable)
+                            // totals of the partials and writes them here (device-addressable;
+                            // the kernels of launch_step_fold)
     unsigned int* diag_ticket;  // blocks of the step that have written their partials (zero
                                 // between steps: the last block resets it)
 };
@@ -224,6 +225,13 @@ cudaError_t step_walls_occupancy(const StepLaunch& l, int* blocks_per_sm);
 cudaError_t prepare_walls_kernels();
 
 cudaError_t launch_diag_finish(const float2* partials, int n_blocks, double* out, cudaStream_t s);
+// A step that also forms its totals in its last block (a.diag_out set):
+// variants 1 and 4 without the paper's walls (lbm_fold_steps.cu); cfg is the
+// step's launch configuration.  Other launch shapes return
+// cudaErrorNotSupported.
+bool step_folds_totals(const StepLaunch& l);
+cudaError_t launch_step_fold(const StepArgs& a, const StepLaunch& l, cudaLaunchConfig_t cfg);
+cudaError_t prepare_fold_kernels();
 // n coupled steps (FP32 storage, halfway bounce-back) in one cooperative
 // launch of `grid` blocks of `block` threads, all resident (grid <= the
 // occupancy times the SMs): src holds time t; with seq_stride = 0 the result

@@ -398,6 +398,7 @@ cudaError_t prepare_step_kernels()
         e = cudaFuncSetAttribute(coupled_step_async<__nv_bfloat16, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, async_max);
     if (e == cudaSuccess) e = prepare_walls_kernels();
+    if (e == cudaSuccess) e = prepare_fold_kernels();
     return e;
 }
 
@@ -436,6 +437,7 @@ cudaError_t launch_step(const StepArgs& a, const StepLaunch& l, cudaStream_t s)
     StepArgs b = a;  // the register variants' port blocks for this grid
     b.port_blocks = port_blocks(l.grid, a.n_tiles, a.n_plain, l.precision);
     if (a.wallv) return launch_step_walls(b, l, s);
+    if (a.diag_out != nullptr) return launch_step_fold(b, l, cfg);
     cudaError_t e;
     if (l.variant == kVariantBulk) {
         const int per = l.stages / (l.block / 32 - 1);

@@ -93,7 +93,7 @@ __device__ __forceinline__ void regs_loop(const StepArgs& a, TileRange r, int la
     }
 }
 
-template <typename T, bool kWalls>
+template <typename T, bool kWalls, bool kFold = false>
 __global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256, 2) coupled_step_regs(const StepArgs a)
         else regs_loop<T, kWalls, false>(a, r, lane, diag, bad);
     }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
-    block_partials(a, diag);
+    block_partials<kFold>(a, diag);
 }
 
 // ---------------------------------------------------------------------------
@@ -228,7 +228,7 @@ __device__ __forceinline__ void async_loop(const StepArgs& a, TileRange r, Async
     asm volatile("cp.async.wait_group 0;" ::: "memory");  // nothing in flight at exit
 }
 
-template <typename T, bool kWalls>
+template <typename T, bool kWalls, bool kFold = false>
 __global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
         else async_loop<T, kWalls, false>(a, r, st, lane, diag, bad);
     }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(a.err, 1u);
-    block_partials(a, diag);
+    block_partials<kFold>(a, diag);
 }
 
 // ---------------------------------------------------------------------------

@@ -345,9 +345,11 @@ def test_in_kernel_diagnostics_equal_the_reduction_launch(opts):
     of every step (into pinned host memory and into device memory); each row
     has the same bits as lbm_get_diagnostics after that step (same order of
     additions), the populations match lbm_step's, and the ticket counter is
-    back at zero after every step (a second run gives the same rows).  Grids
-    of 5 and 17 blocks, and blocks of fewer than 128 threads (totals from the
-    reduction kernel launched after each step instead) included."""
+    back at zero after every step (a second run gives the same rows).  The
+    register and asynchronous-copy variants fold in the kernel (grids of 5
+    and 17 blocks included); the bulk-copy, pipeline and pair variants, the
+    paper's walls and blocks of fewer than 128 threads take the totals from
+    the reduction kernel launched after each step instead."""
     prob, init = W.random_case(41, 300, 48, solid_frac=0.1)
     prob["states"] = [1, 2, 3, 0]
     a = lbm.Chip.from_problem(prob, **opts)
