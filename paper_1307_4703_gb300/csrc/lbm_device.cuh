@@ -1039,6 +1039,7 @@ __device__ __forceinline__ DF df_tree8(const DF (&x)[8])
 
 __device__ __forceinline__ void finish_partials(const float2* partials, int n, double* out)
 {
+    static_assert(kFoldThreads == 128, "the final combination below adds four warps' sums");
     __shared__ DF red[kFoldThreads / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < kFoldThreads) {

@@ -231,11 +231,12 @@ __device__ __forceinline__ void async_loop(const StepArgs& a, TileRange r, Async
 template <typename T, bool kWalls, bool kFold = false>
 __global__ void __launch_bounds__(256, 2) coupled_step_async(const StepArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    // named apart from the bulk kernels' 128-byte aligned smem (one symbol per name)
+    extern __shared__ __align__(16) unsigned char stage_smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    AsyncStage<T>& st = reinterpret_cast<AsyncStage<T>*>(smem)[warp];
+    AsyncStage<T>& st = reinterpret_cast<AsyncStage<T>*>(stage_smem)[warp];
     LaneDiag diag;
     bool bad = false;
     if constexpr (kStoresF32<T>) {  // one loop over every tile (port_blocks is 0 for FP32)
