@@ -407,11 +407,16 @@ lbm_status lbm_get_info(lbm_handle h, lbm_info* info);
 
 /* Time the step kernel's launch shapes on this chip and keep the fastest
  * (the paper has no counterpart; launch shapes are a property of the GPU).
- * Candidates: the register variant with 128 and 256 threads, the bulk-copy
+ * Candidates: the register variant with 128 and 256 threads, variant 4
+ * with 64 and 128 threads (not with the paper's walls), the bulk-copy
  * variant with 2..4 computing warps and 1..2 (16-bit: up to 3) stages each,
- * and variant 3 (FP32).  Each runs 3 + trial_steps (0 = 20) launches from the
- * current state into scratch buffers, so the state, the step count and the
- * diagnostics do not change; every shape gives identical populations.
+ * variant 3 (FP32, not with the paper's walls) and variant 5 (FP32 with
+ * halfway bounce-back).  Each runs 3 launches and then two timed trials of
+ * trial_steps launches (the better one counts), stepping between two
+ * scratch copies of the current state with the tile order alternating as in
+ * lbm_step, so the state, the step count and the diagnostics do not change;
+ * every shape gives identical populations.  trial_steps = 0: a trial
+ * lasts about 2 ms (20 to 2000 launches, from a first timing of 20).
  * lbm_get_info reports the shape kept.  Synchronises the stream. */
 lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps);
 

@@ -2014,7 +2014,12 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     Range range("lbm_autotune");
     if (check_ctx(h)) return LBM_ERR_ARG;
     if (trial_steps < 0 || trial_steps > 10000) return fail(h, LBM_ERR_ARG, "trial_steps = %d outside [0, 10000]", trial_steps);
-    if (trial_steps == 0) trial_steps = 20;
+    // 0: a first timing of 20 steps of the first shape sets a count for
+    // which a trial lasts about 2 ms (between 20 and 2000 steps): 20 steps
+    // of a chip of a few microseconds per step are too short to tell
+    // shapes a few percent apart
+    bool size_trials = trial_steps == 0;
+    if (size_trials) trial_steps = 20;
     if (lbm_status js = join_scalar(h)) return js;
     // candidate shapes: {variant, block (variant 1) or computing warps, stages per computing warp}
     struct Cand { int variant, warps, per; };
@@ -2023,16 +2028,22 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
     if (h->precision == LBM_FP32) cands.push_back({3, 4, 1});
     else cands.push_back({2, 3, 3});
     if (h->precision == LBM_FP32 && !h->wallv) cands.push_back({5, 4, 0});
-    // trials write to scratch buffers: the state, step count and diagnostics stay as they are
+    // trials step between two scratch copies of the state, alternating the
+    // tile order like lbm_step (the L2 reuse of consecutive steps is part of
+    // what is timed): the state, step count and diagnostics stay as they are
     Scratch sc(h);
-    void* dst = sc.get(size_t(h->plane) * lbm::kPlanes * h->elem);
+    const size_t state_bytes = size_t(h->plane) * lbm::kPlanes * h->elem;
+    void* buf0 = sc.get(state_bytes);
+    void* buf1 = sc.get(state_bytes);
     float2* part = static_cast<float2*>(sc.get(size_t(h->partials_cap) * 4 * sizeof(float2)));
     unsigned* err = static_cast<unsigned*>(sc.get(sizeof(unsigned)));
-    if (!dst || !part || !err) return fail(h, LBM_ERR_OOM, "no device memory for the trial steps");
+    if (!buf0 || !buf1 || !part || !err) return fail(h, LBM_ERR_OOM, "no device memory for the trial steps");
     LBM_CUDA(h, lbm::prepare_step_kernels());
+    LBM_CUDA(h, cudaMemcpyAsync(buf0, h->pop[h->cur], state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    float* const bufs[2] = {static_cast<float*>(buf0), static_cast<float*>(buf1)};
     lbm::StepArgs a{};
-    a.src = h->pop[h->cur];
-    a.dst = static_cast<float*>(dst);
+    a.src = bufs[0];
+    a.dst = bufs[1];
     a.links = h->links;
     a.rowbc = h->rowbc;
     a.tiles = h->tiles;
@@ -2095,14 +2106,34 @@ lbm_status lbm_autotune(lbm_handle h, int32_t trial_steps)
         e = arrange_tiles(h, L);  // each shape is timed with its own tile order
         if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned), h->stream);
         // the step kernel alone (the wall values, when used, are computed
-        // once below from the current state)
-        for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = lbm::launch_step(a, L, h->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-        for (int j = 0; j < trial_steps && e == cudaSuccess; ++j) e = lbm::launch_step(a, L, h->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        // once above from the current state); the better of two trials
+        int64_t k = 0;  // launches of this shape so far: buffers and tile order alternate
+        auto trial_step = [&]() {
+            a.src = bufs[k & 1];
+            a.dst = bufs[1 - (k & 1)];
+            a.reverse = int(k & 1);
+            ++k;
+            return lbm::launch_step(a, L, h->stream);
+        };
+        for (int j = 0; j < 3 && e == cudaSuccess; ++j) e = trial_step();
         float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            for (int j = 0; j < trial_steps && e == cudaSuccess; ++j) e = trial_step();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && size_trials) {
+                // once, before any comparison: resize and time this shape again
+                const double want = std::ceil(2.0 * trial_steps / std::max(double(t), 1e-3));
+                trial_steps = int(std::min(2000.0, std::max(double(trial_steps), want)));
+                size_trials = false;
+                --rep;
+                continue;
+            }
+            if (rep == 0 || t < ms) ms = t;
+        }
         unsigned ew = 0;
         if (e == cudaSuccess) e = cudaMemcpy(&ew, err, sizeof(unsigned), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && (ew & 2u) == 0 && (best.grid == 0 || ms < best_ms)) {
